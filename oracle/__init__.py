@@ -1,0 +1,383 @@
+"""CPU oracle of the DRGraph layout path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The
+product library (``paper_2008_07799_gb300``) never imports it and shares no
+code with it.
+
+The arithmetic lives in ``drg_oracle.c`` (plain C, FP64 layout math, exact
+integer graph and index work, its own Philox4x32-10); this module only
+marshals numpy arrays and runs the multilevel loop of Sec. 3.2.3 step by step:
+canonical graph -> sparse distance matrix (Sec. 3.2.1) -> similarity and
+quantised sampling weights -> alias tables (Sec. 3.2.2) -> hierarchy by
+heavy-edge matching (Sec. 3.2.3) -> coarsest random layout -> for each level,
+coarse to fine: epochs of negative-sampling SGD (Eqs. 11-12), then refinement.
+
+Parity status: every stage is pinned by ``tests/test_oracle_*.py`` against
+closed forms, brute force, library routines or invariants.  Whole-run layout
+quality against the paper's printed numbers is "parity unpinned" (the paper
+states neither its random generator, sigma nor learning rate); only a loose
+sanity range on a 17x17 grid is checked.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+import sysconfig
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drg_oracle.c")
+_LIB = os.path.join(_HERE, "_drg_oracle.so")
+_lib = None
+
+U32P = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+U64P = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+U8P = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+F64P = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add: -ffp-contract=off)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    L = C.CDLL(build())
+    L.orc_philox4x32_10.argtypes = [U32P, U32P, U32P]
+    L.orc_tag.argtypes = [C.c_uint32] * 3
+    L.orc_tag.restype = C.c_uint32
+    L.orc_korder_counts.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, U64P]
+    L.orc_korder_fill.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, U64P, U32P, U8P]
+    L.orc_similarity.argtypes = [C.c_uint32, U64P, U32P, U8P, C.c_uint32, C.c_double,
+                                 F32P, F32P, U32P, U64P, F64P]
+    L.orc_node_weights_u32.argtypes = [C.c_uint32, U64P, U32P]
+    L.orc_node_weights_u32.restype = C.c_uint32
+    L.orc_alias_build.argtypes = [C.c_uint64, U32P, U32P, U32P, U64P]
+    L.orc_alias_draw.argtypes = [C.c_uint64, U32P, U32P, C.c_uint64, C.c_uint32]
+    L.orc_alias_draw.restype = C.c_uint64
+    L.orc_sample_draws.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                   C.c_uint64, U32P, U32P, U32P, U32P, C.c_uint32, U32P, U32P,
+                                   C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), U32P]
+    L.orc_pair_force.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.orc_sample_objective.argtypes = [F64P, F64P, F64P, C.c_uint32, C.c_double, C.c_double]
+    L.orc_sample_objective.restype = C.c_double
+    L.orc_layout_level.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32,
+                                   C.c_uint64, U32P, U32P, U32P, U32P,
+                                   C.c_uint32, U32P, U32P,
+                                   C.c_uint32, C.c_void_p, F64P,
+                                   C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                   C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_uint32]
+    L.orc_init_positions.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_float, F64P]
+    L.orc_interpolate.argtypes = [C.c_uint32, U32P, F64P, F64P]
+    L.orc_hem_match.argtypes = [C.c_uint32, U64P, U32P, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                C.c_uint32, U32P]
+    L.orc_cluster_ids.argtypes = [C.c_uint32, U32P, U32P]
+    L.orc_cluster_ids.restype = C.c_uint32
+    L.orc_contract.argtypes = [C.c_uint32, U64P, U32P, C.c_void_p, U32P, C.c_uint32, U64P, C.c_void_p, C.c_void_p]
+    L.orc_contract.restype = C.c_int64
+    L.orc_neighbourhood_preservation.argtypes = [C.c_uint32, U64P, U32P, F64P, C.c_uint32, C.c_uint32,
+                                                 C.c_void_p, C.POINTER(C.c_uint32)]
+    L.orc_neighbourhood_preservation.restype = C.c_double
+    L.orc_stress.argtypes = [C.c_uint32, U64P, U32P, F64P, C.c_uint32, C.c_void_p]
+    L.orc_stress.restype = C.c_double
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- parameters
+@dataclasses.dataclass
+class Params:
+    """Layout parameters (Sec. 4 "Parameters"; Sec. 4.2; supplement on b)."""
+    k: int = 1                 # order of the sparse distance matrix (Sec. 3.2.1)
+    M: int = 5                 # negative samples per positive sample (Sec. 3.2.2)
+    epochs: int = 400          # epochs per level
+    gamma: float = 0.1         # negative-sample weight (Eq. 10)
+    gamma_coarsest: float = 0.01   # early exaggeration on the coarsest level (Sec. 4.2)
+    b: float = 1.0             # shape of the layout proximity kernel (Eq. 5)
+    lr0: float = 1.0           # learning rate at epoch 0, linearly decayed to 0
+    sigma: float = 1.0         # Gaussian width of the node similarity (Eq. 9)
+    clip: float = 5.0          # per-component clip of each pair force
+    seed: int = 0
+    gid: int = 0               # graph id in the random stream
+    mode: int = 0              # 0 synchronous, 1 sequential (asynchronous reference)
+    substeps: int = 16         # synchronous sub-steps per epoch
+    stop_nodes: int = 1000     # coarsen while the level has at least this many nodes
+    rho: float = 0.8           # stop when a coarser level keeps more than rho of the nodes
+    match_rounds: int = 8      # handshake rounds of heavy-edge matching
+    max_levels: int = 32
+    init_scale: float = 1e-4   # coarsest positions uniform in [-s, s]^2
+    multilevel: bool = True
+
+
+# ---------------------------------------------------------------- primitives
+def philox(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def canonical_graph(n, src, dst):
+    """Sec. 3.1: undirected unweighted G = (V, E) -- drop self-loops, make
+    every edge symmetric, remove duplicates; CSR rows sorted by column."""
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    keep = src != dst
+    a = np.r_[src[keep], dst[keep]]
+    b = np.r_[dst[keep], src[keep]]
+    key = np.unique(a * np.int64(n) + b)
+    rows = key // n
+    cols = key % n
+    rp = np.zeros(n + 1, np.uint64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    return rp, cols.astype(np.uint32)
+
+
+def korder(rp, col, k):
+    n = len(rp) - 1
+    counts = np.zeros(max(n, 1), np.uint64)
+    L = lib()
+    assert L.orc_korder_counts(n, rp, col, k, counts) == 0
+    gd_rp = np.zeros(n + 1, np.uint64)
+    np.cumsum(counts[:n], out=gd_rp[1:])
+    nnz = int(gd_rp[-1])
+    gd_col = np.zeros(max(nnz, 1), np.uint32)
+    gd_dist = np.zeros(max(nnz, 1), np.uint8)
+    assert L.orc_korder_fill(n, rp, col, k, gd_rp, gd_col, gd_dist) == 0
+    return gd_rp, gd_col[:nnz], gd_dist[:nnz]
+
+
+def similarity(gd_rp, gd_col, gd_dist, k, sigma=1.0):
+    n = len(gd_rp) - 1
+    nnz = int(gd_rp[-1])
+    g = np.zeros(k, np.float32)
+    Z = np.zeros(max(n, 1), np.float32)
+    q = np.zeros(max(nnz, 1), np.uint32)
+    r = np.zeros(max(n, 1), np.uint64)
+    ns = np.zeros(max(nnz, 1), np.float64)
+    col = gd_col if nnz else np.zeros(1, np.uint32)
+    dist = gd_dist if nnz else np.zeros(1, np.uint8)
+    assert lib().orc_similarity(n, gd_rp, col, dist, k, sigma, g, Z, q, r, ns) == 0
+    return dict(g=g, Z=Z[:n], q=q[:nnz], r=r[:n], ns=ns[:nnz])
+
+
+def node_weights_u32(r):
+    r = np.ascontiguousarray(r, np.uint64)
+    out = np.zeros(max(len(r), 1), np.uint32)
+    s = lib().orc_node_weights_u32(len(r), r if len(r) else np.zeros(1, np.uint64), out)
+    return out[:len(r)], int(s)
+
+
+def alias_build(q):
+    q = np.ascontiguousarray(q, np.uint32)
+    N = len(q)
+    th = np.zeros(max(N, 1), np.uint32)
+    al = np.zeros(max(N, 1), np.uint32)
+    own = np.zeros(max(N, 1), np.uint64)
+    rc = lib().orc_alias_build(N, q if N else np.zeros(1, np.uint32), th, al, own)
+    if rc != 0:
+        return None
+    return th[:N], al[:N], own[:N]
+
+
+def alias_draw(thresh, alias, R, U):
+    return int(lib().orc_alias_draw(len(thresh), thresh, alias, int(R), int(U)))
+
+
+def edge_endpoints(gd_rp, gd_col):
+    """Entry e of the distance matrix -> (source row, column)."""
+    n = len(gd_rp) - 1
+    src = np.repeat(np.arange(n, dtype=np.uint32), np.diff(gd_rp).astype(np.int64))
+    return src, np.ascontiguousarray(gd_col, np.uint32)
+
+
+@dataclasses.dataclass
+class Tables:
+    """Level-0 sampling state: edge table over distance-matrix entries and
+    node table over nodes (Sec. 3.2.2)."""
+    n0: int
+    e_src: np.ndarray
+    e_dst: np.ndarray
+    e_thresh: np.ndarray
+    e_alias: np.ndarray
+    v_thresh: np.ndarray
+    v_alias: np.ndarray
+    q: np.ndarray
+    r32: np.ndarray
+    shift: int
+
+
+def sampling_tables(gd_rp, gd_col, gd_dist, k, sigma=1.0):
+    sim = similarity(gd_rp, gd_col, gd_dist, k, sigma)
+    e_src, e_dst = edge_endpoints(gd_rp, gd_col)
+    et = alias_build(sim["q"])
+    r32, shift = node_weights_u32(sim["r"])
+    vt = alias_build(r32)
+    if et is None or vt is None:
+        raise ValueError("graph has no edges: nothing to sample")
+    return Tables(len(gd_rp) - 1, e_src, e_dst, et[0], et[1], vt[0], vt[1], sim["q"], r32, shift), sim
+
+
+def sample_draws(tab: Tables, seed, gid, level, t, s, M):
+    i = C.c_uint32()
+    j = C.c_uint32()
+    neg = np.zeros(max(M, 1), np.uint32)
+    lib().orc_sample_draws(seed, gid, level, t, s, M, len(tab.e_thresh), tab.e_src, tab.e_dst,
+                           tab.e_thresh, tab.e_alias, tab.n0, tab.v_thresh, tab.v_alias,
+                           C.byref(i), C.byref(j), neg)
+    return i.value, j.value, neg[:M].copy()
+
+
+def pair_force(dx, dy, repulsive, gamma, b, clip):
+    fx = C.c_double()
+    fy = C.c_double()
+    lib().orc_pair_force(dx, dy, int(repulsive), gamma, b, clip, C.byref(fx), C.byref(fy))
+    return fx.value, fy.value
+
+
+def sample_objective(yi, yj, yneg, gamma, b):
+    yneg = np.ascontiguousarray(yneg, np.float64).reshape(-1)
+    return lib().orc_sample_objective(np.ascontiguousarray(yi, np.float64), np.ascontiguousarray(yj, np.float64),
+                                      yneg if len(yneg) else np.zeros(2), len(yneg) // 2, gamma, b)
+
+
+def layout_level(tab: Tables, Y, level, anc, p: Params, gamma, t_begin=0, t_end=None):
+    """Run epochs [t_begin, t_end) of one level in place on Y (n_l x 2 FP64)."""
+    Y = np.ascontiguousarray(Y, np.float64)
+    t_end = p.epochs if t_end is None else t_end
+    anc_arr = None if anc is None else np.ascontiguousarray(anc, np.uint32)
+    rc = lib().orc_layout_level(p.seed, p.gid, level, len(tab.e_thresh), tab.e_src, tab.e_dst,
+                                tab.e_thresh, tab.e_alias, tab.n0, tab.v_thresh, tab.v_alias,
+                                Y.shape[0], _ptr(anc_arr), Y.reshape(-1),
+                                p.epochs, t_begin, t_end, p.M, gamma, p.b, p.lr0, p.clip, p.mode, p.substeps)
+    assert rc == 0
+    return Y
+
+
+def init_positions(p: Params, level, n):
+    Y = np.zeros((n, 2), np.float64)
+    lib().orc_init_positions(p.seed, p.gid, level, n, p.init_scale, Y.reshape(-1))
+    return Y
+
+
+def interpolate(parent, Yc):
+    parent = np.ascontiguousarray(parent, np.uint32)
+    Yf = np.zeros((len(parent), 2), np.float64)
+    lib().orc_interpolate(len(parent), parent, np.ascontiguousarray(Yc, np.float64).reshape(-1), Yf.reshape(-1))
+    return Yf
+
+
+# ---------------------------------------------------------------- hierarchy
+def hem_match(rp, col, w, p: Params, level):
+    n = len(rp) - 1
+    match = np.zeros(max(n, 1), np.uint32)
+    w_arr = None if w is None else np.ascontiguousarray(w, np.uint32)
+    assert lib().orc_hem_match(n, rp, col if len(col) else np.zeros(1, np.uint32), _ptr(w_arr),
+                               p.seed, p.gid, level, p.match_rounds, match) == 0
+    return match[:n]
+
+
+def cluster_ids(match):
+    cid = np.zeros(max(len(match), 1), np.uint32)
+    nc = lib().orc_cluster_ids(len(match), np.ascontiguousarray(match, np.uint32), cid)
+    return cid[:len(match)], int(nc)
+
+
+def contract(rp, col, w, cid, nc):
+    n = len(rp) - 1
+    L = lib()
+    colx = col if len(col) else np.zeros(1, np.uint32)
+    w_arr = None if w is None else np.ascontiguousarray(w, np.uint32)
+    out_rp = np.zeros(nc + 1, np.uint64)
+    m = L.orc_contract(n, rp, colx, _ptr(w_arr), np.ascontiguousarray(cid, np.uint32), nc, out_rp, None, None)
+    assert m >= 0
+    out_col = np.zeros(max(m, 1), np.uint32)
+    out_w = np.zeros(max(m, 1), np.uint32)
+    L.orc_contract(n, rp, colx, _ptr(w_arr), np.ascontiguousarray(cid, np.uint32), nc, out_rp,
+                   _ptr(out_col), _ptr(out_w))
+    return out_rp, out_col[:m], out_w[:m]
+
+
+@dataclasses.dataclass
+class Level:
+    rp: np.ndarray
+    col: np.ndarray
+    w: np.ndarray | None
+    parent: np.ndarray | None = None   # this level -> next coarser level
+    anc: np.ndarray | None = None      # level-0 node -> this level (None at level 0)
+
+    @property
+    def n(self):
+        return len(self.rp) - 1
+
+
+def hierarchy(rp, col, p: Params):
+    """Sec. 3.2.3 coarsening: repeat while the level has >= stop_nodes nodes;
+    stop (discarding the candidate) when it keeps more than rho of the nodes."""
+    levels = [Level(rp, col, None)]
+    while p.multilevel and len(levels) < p.max_levels and levels[-1].n >= p.stop_nodes:
+        cur = levels[-1]
+        lvl = len(levels) - 1
+        match = hem_match(cur.rp, cur.col, cur.w, p, lvl)
+        cid, nc = cluster_ids(match)
+        if nc > p.rho * cur.n:
+            break
+        crp, ccol, cw = contract(cur.rp, cur.col, cur.w, cid, nc)
+        cur.parent = cid
+        anc = cid.copy() if cur.anc is None else cid[cur.anc]
+        levels.append(Level(crp, ccol, cw, None, anc))
+    return levels
+
+
+def run(n, src, dst, p: Params, return_state=False):
+    """The whole layout path, coarse to fine (Sec. 3.2, Fig. 1 pipeline)."""
+    rp, col = canonical_graph(n, src, dst)
+    gd_rp, gd_col, gd_dist = korder(rp, col, p.k)
+    tab, sim = sampling_tables(gd_rp, gd_col, gd_dist, p.k, p.sigma)
+    levels = hierarchy(rp, col, p)
+    L = len(levels) - 1
+    Y = init_positions(p, L, levels[L].n)
+    for lvl in range(L, -1, -1):
+        gamma = p.gamma_coarsest if (lvl == L and L > 0) else p.gamma
+        Y = layout_level(tab, Y, lvl, levels[lvl].anc, p, gamma)
+        if lvl > 0:
+            Y = interpolate(levels[lvl - 1].parent, Y)
+    if return_state:
+        return Y, dict(rp=rp, col=col, gd=(gd_rp, gd_col, gd_dist), tab=tab, sim=sim, levels=levels)
+    return Y
+
+
+# ---------------------------------------------------------------- metrics
+def neighbourhood_preservation(rp, col, Y, k_eval=2, nodes=None):
+    n = len(rp) - 1
+    sel = None if nodes is None else np.ascontiguousarray(nodes, np.uint32)
+    cnt = C.c_uint32()
+    v = lib().orc_neighbourhood_preservation(n, rp, col if len(col) else np.zeros(1, np.uint32),
+                                             np.ascontiguousarray(Y, np.float64).reshape(-1), k_eval,
+                                             n if sel is None else len(sel), _ptr(sel), C.byref(cnt))
+    return v
+
+
+def stress(rp, col, Y, sources=None):
+    n = len(rp) - 1
+    sel = None if sources is None else np.ascontiguousarray(sources, np.uint32)
+    return lib().orc_stress(n, rp, col if len(col) else np.zeros(1, np.uint32),
+                            np.ascontiguousarray(Y, np.float64).reshape(-1),
+                            n if sel is None else len(sel), _ptr(sel))

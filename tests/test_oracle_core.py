@@ -1,0 +1,274 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Philox against the published known-answer vectors; the k-order distance
+matrix against closed forms and scipy's all-pairs shortest paths; the
+similarity against its normalisation identities; the alias tables against
+exact mass conservation, brute-force enumeration and a chi-square test.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+from scipy import stats
+
+import graphgen as gg
+from conftest import golden
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers(orc):
+    rows = [l.split() for l in open(golden("philox_kat.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = orc.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_philox_counter_sensitivity(orc):
+    base = orc.philox([1, 2, 3, 4], [5, 6])
+    for lane in range(4):
+        c = [1, 2, 3, 4]
+        c[lane] ^= 1
+        assert not np.array_equal(orc.philox(c, [5, 6]), base)
+    assert not np.array_equal(orc.philox([1, 2, 3, 4], [5, 7]), base)
+
+
+# ---------------------------------------------------------------- distance matrix
+def _dense_from_gd(gd, n):
+    rp, col, dist = gd
+    D = np.zeros((n, n), np.int64)
+    rows = np.repeat(np.arange(n), np.diff(rp).astype(np.int64))
+    D[rows, col.astype(np.int64)] = dist
+    return D
+
+
+def _expected_dense(spd, k):
+    n = spd.shape[0]
+    E = np.where((spd <= k) & (spd > 0), spd, 0)
+    E[np.arange(n), np.arange(n)] = 0
+    return E.astype(np.int64)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_korder_path_cycle_grid_closed_forms(orc, k):
+    n = 23
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    cases = [
+        (gg.path(n), np.abs(ii - jj)),
+        (gg.cycle(n), np.minimum(np.abs(ii - jj), n - np.abs(ii - jj))),
+    ]
+    R, Cc = 5, 7
+    r, c = np.divmod(np.arange(R * Cc), Cc)
+    cases.append((gg.grid(R, Cc), np.abs(r[:, None] - r[None, :]) + np.abs(c[:, None] - c[None, :])))
+    for (nn, s, d), spd in cases:
+        rp, col = orc.canonical_graph(nn, s, d)
+        gd = orc.korder(rp, col, k)
+        assert np.array_equal(_dense_from_gd(gd, nn), _expected_dense(spd, k))
+        # rows sorted strictly ascending
+        for i in range(nn):
+            row = gd[1][gd[0][i]:gd[0][i + 1]]
+            assert np.all(np.diff(row.astype(np.int64)) > 0)
+
+
+def _grid_count(R, Cc, k):
+    """Number of ordered pairs of distinct grid points at Manhattan distance <= k."""
+    r, c = np.divmod(np.arange(R * Cc), Cc)
+    tot = 0
+    for i in range(R * Cc):
+        d = np.abs(r - r[i]) + np.abs(c - c[i])
+        tot += int(((d > 0) & (d <= k)).sum())
+    return tot
+
+
+def test_korder_grid32_counts(orc):
+    n, s, d = gg.grid(32, 32)
+    rp, col = orc.canonical_graph(n, s, d)
+    assert len(col) == 2 * 1984
+    for k, expect in [(1, 3968), (2, 11652), (3, 22804)]:
+        gd = orc.korder(rp, col, k)
+        assert len(gd[1]) == expect == _grid_count(32, 32, k)
+        interior = 5 * 32 + 5
+        assert gd[0][interior + 1] - gd[0][interior] == 2 * k * (k + 1)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_korder_vs_scipy_shortest_path(orc, seed):
+    n, s, d = gg.erdos_renyi(60, 90, seed)
+    rp, col = orc.canonical_graph(n, s, d)
+    A = sp.csr_matrix((np.ones(len(col)), col.astype(np.int64), rp.astype(np.int64)), shape=(n, n))
+    spd = csg.shortest_path(A, unweighted=True, directed=False)
+    spd[np.isinf(spd)] = 10 ** 6
+    for k in (1, 2, 3, 4):
+        gd = orc.korder(rp, col, k)
+        D = _dense_from_gd(gd, n)
+        assert np.array_equal(D, _expected_dense(spd.astype(np.int64), k))
+        assert np.array_equal(D, D.T)  # GD is symmetric
+
+
+def test_canonical_graph_drops_loops_and_duplicates(orc):
+    rp, col = orc.canonical_graph(4, np.array([0, 1, 1, 2, 3, 3]), np.array([1, 0, 1, 3, 2, 2]))
+    assert rp.tolist() == [0, 1, 2, 3, 4]
+    assert col.tolist() == [1, 0, 3, 2]
+
+
+# ---------------------------------------------------------------- similarity
+def _sim_for(orc, g, k, sigma=1.0):
+    n, s, d = g
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, k)
+    return n, rp, col, gd, orc.similarity(*gd, k, sigma)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_similarity_normalisation(orc, k):
+    n, rp, col, gd, sim = _sim_for(orc, gg.barabasi_albert(300, 2, 7), k, sigma=1.3)
+    g64 = np.exp(-np.arange(1, k + 1) ** 2 / (2 * 1.3 ** 2))
+    assert np.allclose(sim["g"], g64.astype(np.float32), rtol=0, atol=0)
+    rows = np.repeat(np.arange(n), np.diff(gd[0]).astype(np.int64))
+    dist = gd[2].astype(np.int64)
+    # conditional similarities of every row sum to one (Eq. 9)
+    Zrow = np.zeros(n)
+    np.add.at(Zrow, rows, g64[dist - 1])
+    cond = g64[dist - 1] / Zrow[rows]
+    sums = np.zeros(n)
+    np.add.at(sums, rows, cond)
+    assert np.allclose(sums, 1.0)
+    assert np.allclose(sim["Z"], Zrow.astype(np.float32), rtol=1e-6)
+    # symmetric joint similarity summing to one (Eq. 4)
+    ns = sim["ns"]
+    key = rows * n + gd[1].astype(np.int64)
+    tkey = gd[1].astype(np.int64) * n + rows
+    order = np.argsort(key)
+    pos = np.searchsorted(key[order], tkey)
+    assert np.allclose(ns, ns[order][pos], rtol=1e-14)
+    assert math.isclose(ns.sum(), 1.0, rel_tol=1e-12)
+    # quantised weights: floor of an FP32 rounding of (p_j|i + p_i|j) * 2^30
+    exact = (cond + g64[dist - 1] / Zrow[gd[1].astype(np.int64)]) * 2.0 ** 30
+    q = sim["q"].astype(np.float64)
+    assert np.all(q <= exact * (1 + 4e-7) + 1e-9)
+    assert np.all(q >= exact * (1 - 4e-7) - 1.0)
+    assert np.array_equal(sim["r"], np.bincount(rows, weights=sim["q"], minlength=n).astype(np.uint64))
+
+
+def test_similarity_k1_is_inverse_degree(orc):
+    n, rp, col, gd, sim = _sim_for(orc, gg.random_binary_tree(200, 3), 1)
+    deg = np.diff(rp).astype(np.float64)
+    rows = np.repeat(np.arange(n), np.diff(rp).astype(np.int64))
+    j = col.astype(np.int64)
+    assert np.allclose(sim["ns"], (1 / deg[rows] + 1 / deg[j]) / (2 * n), rtol=1e-14)
+
+
+def test_node_weight_shift(orc):
+    r = np.array([0, 5, 2 ** 40 + 7, 2 ** 33], np.uint64)
+    r32, s = orc.node_weights_u32(r)
+    assert s == 9
+    assert r32.tolist() == [0, 0, (2 ** 40 + 7) >> 9, 2 ** 24]
+    r32, s = orc.node_weights_u32(np.array([3, 4], np.uint64))
+    assert s == 0 and r32.tolist() == [3, 4]
+
+
+# ---------------------------------------------------------------- alias tables
+def _mass_per_item(q, th, al, own):
+    N = len(q)
+    W = int(np.sum(q.astype(object)))
+    got = [0] * N
+    for b in range(N):
+        o = int(own[b])
+        got[b] += o
+        if int(al[b]) != b:
+            got[int(al[b])] += W - o
+        else:
+            assert o == W
+    return got, W
+
+
+def _draw_prob(th, al):
+    N = len(th)
+    P = np.zeros(N)
+    for b in range(N):
+        keep = int(th[b]) / 2.0 ** 32
+        P[b] += keep / N
+        P[int(al[b])] += (1 - keep) / N
+    return P
+
+
+CASES = [
+    np.array([1], np.uint32),
+    np.array([3, 3, 3, 3], np.uint32),
+    np.array([0, 0, 9, 0], np.uint32),
+    np.array([1, 2, 3, 4, 5, 6, 7, 8], np.uint32),
+    np.array([2 ** 31, 1, 1, 1, 2 ** 30, 0, 7], np.uint32),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)) )
+def test_alias_exact_mass_and_probability(orc, case):
+    q = CASES[case]
+    th, al, own = orc.alias_build(q)
+    got, W = _mass_per_item(q, th, al, own)
+    N = len(q)
+    assert got == [int(x) * N for x in q]
+    P = _draw_prob(th, al)
+    assert np.allclose(P, q.astype(np.float64) / W, atol=2.0 ** -31, rtol=0)
+
+
+def test_alias_random_weights_and_sweep_closed_form(orc):
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        N = int(rng.integers(1, 400))
+        q = rng.integers(0, 2 ** int(rng.integers(1, 32)), size=N).astype(np.uint32)
+        if q.sum() == 0:
+            q[0] = 1
+        th, al, own = orc.alias_build(q)
+        got, W = _mass_per_item(q, th, al, own)
+        assert got == [int(x) * N for x in q]
+        # the sweep equals its merge-rank closed form (Huebschle-Schneider &
+        # Sanders): light x goes to the first heavy whose cumulative excess
+        # exceeds the lights' cumulative deficit before x.
+        a = [int(x) * N for x in q]
+        L = [i for i in range(N) if a[i] < W]
+        H = [i for i in range(N) if a[i] >= W]
+        Dl = [0]
+        for i in L:
+            Dl.append(Dl[-1] + W - a[i])
+        S = []
+        acc = 0
+        for h in H:
+            acc += a[h] - W
+            S.append(acc)
+        for x, i in enumerate(L):
+            y = sum(1 for v in S if v <= Dl[x])
+            assert int(al[i]) == H[y] and int(own[i]) == a[i]
+        for y, h in enumerate(H):
+            xs = sum(1 for v in Dl if v < S[y])
+            mass = S[y] + W - Dl[xs]
+            assert int(own[h]) == mass
+            exp_alias = h if mass == W else H[y + 1]
+            assert int(al[h]) == exp_alias
+        for b in range(N):
+            t = (int(own[b]) << 32) // W
+            assert int(th[b]) == min(t, 2 ** 32 - 1)
+
+
+def test_alias_zero_total_is_error(orc):
+    assert orc.alias_build(np.zeros(5, np.uint32)) is None
+    assert orc.alias_build(np.zeros(0, np.uint32)) is None
+
+
+def test_alias_draw_chi_square(orc):
+    q = np.array([5, 1, 0, 20, 3, 3, 11, 2, 9, 1], np.uint32)
+    th, al, own = orc.alias_build(q)
+    rng = np.random.default_rng(5)
+    R = rng.integers(0, 2 ** 63, size=60000, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=60000, dtype=np.uint64)
+    U = rng.integers(0, 2 ** 32, size=60000, dtype=np.uint64)
+    counts = np.zeros(len(q))
+    for r, u in zip(R.tolist(), U.tolist()):
+        counts[orc.alias_draw(th, al, r, u)] += 1
+    expect = q / q.sum() * len(R)
+    assert counts[2] == 0
+    m = expect > 0
+    chi2 = ((counts[m] - expect[m]) ** 2 / expect[m]).sum()
+    assert chi2 < stats.chi2.ppf(0.999, m.sum() - 1)

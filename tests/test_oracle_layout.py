@@ -1,0 +1,305 @@
+"""Pins of the oracle's layout arithmetic, hierarchy and metrics (CPU only).
+
+The gradient is pinned by finite differences of the sampled objective
+(Eq. 11) and by its equilibrium distance; the epoch loop by exact symmetry
+and reduction identities and by a brute-force expectation; the hierarchy by
+scipy's sparse products and matching invariants; the metrics by closed-form
+layouts and a brute-force kNN; whole runs by a loose range around the paper's
+grid17 numbers.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+from scipy.optimize import minimize_scalar
+
+import graphgen as gg
+from conftest import golden
+
+
+# ---------------------------------------------------------------- gradient
+@pytest.mark.parametrize("b", [1.0, 2.0, 3.0, 1.5])
+def test_pair_forces_are_objective_gradient(orc, b):
+    rng = np.random.default_rng(int(b * 10))
+    gamma, M = 0.1, 4
+    for _ in range(20):
+        yi = rng.normal(size=2)
+        yj = yi + rng.normal(size=2) * 0.8
+        yneg = yi + rng.normal(size=(M, 2)) * 1.5
+        fx, fy = orc.pair_force(*(yi - yj), False, gamma, b, 1e300)
+        F = np.array([fx, fy])
+        for m in range(M):
+            F += orc.pair_force(*(yi - yneg[m]), True, gamma, b, 1e300)
+        h = 1e-6
+        num = np.zeros(2)
+        for c in range(2):
+            e = np.zeros(2)
+            e[c] = h
+            num[c] = (orc.sample_objective(yi + e, yj, yneg, gamma, b)
+                      - orc.sample_objective(yi - e, yj, yneg, gamma, b)) / (2 * h)
+        assert np.allclose(F, num, rtol=1e-6, atol=1e-8)
+        # the gradient with respect to the positive target is minus the attraction
+        numj = np.zeros(2)
+        for c in range(2):
+            e = np.zeros(2)
+            e[c] = h
+            numj[c] = (orc.sample_objective(yi, yj + e, yneg, gamma, b)
+                       - orc.sample_objective(yi, yj - e, yneg, gamma, b)) / (2 * h)
+        assert np.allclose(-np.array(orc.pair_force(*(yi - yj), False, gamma, b, 1e300)), numj, rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("b,M,gamma", [(1.0, 5, 0.1), (3.0, 5, 0.1), (2.0, 3, 0.2)])
+def test_equilibrium_distance(orc, b, M, gamma):
+    # With all M negatives at the positive target, the net force vanishes where
+    # d^{2b} = M gamma (derived from Eq. 12).
+    d_star = (M * gamma) ** (1 / (2 * b))
+
+    def net(d):
+        fa = orc.pair_force(d, 0.0, False, gamma, b, 1e300)[0]
+        fr = orc.pair_force(d, 0.0, True, gamma, b, 1e300)[0]
+        return fa + M * fr
+
+    assert abs(net(d_star)) < 1e-12
+    assert net(0.9 * d_star) > 0 and net(1.1 * d_star) < 0
+
+
+def test_pair_force_zero_distance_and_clip(orc):
+    assert orc.pair_force(0.0, 0.0, False, 0.1, 1.0, 5.0) == (0.0, 0.0)
+    assert orc.pair_force(0.0, 0.0, True, 0.1, 1.0, 5.0) == (0.0, 0.0)
+    fx, fy = orc.pair_force(1e-6, -1e-6, True, 0.1, 1.0, 5.0)
+    assert fx == 5.0 and fy == -5.0
+    fx, fy = orc.pair_force(1.3, 0.0, False, 0.1, 3.0, 1.0)   # |attraction| ~ 3.8 before the clip
+    assert fx == -1.0 and fy == 0.0
+    fx, fy = orc.pair_force(10.0, 0.0, False, 0.1, 3.0, 1.0)  # ~ 6 / d, below the clip
+    assert -1.0 < fx < -0.5 and fy == 0.0
+
+
+# ---------------------------------------------------------------- epoch loop
+def _setup(orc, g, k, sigma=1.0):
+    n, s, d = g
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, k)
+    tab, sim = orc.sampling_tables(*gd, k, sigma)
+    return n, rp, col, gd, tab, sim
+
+
+def test_rotation_by_quarter_turn_is_exact(orc):
+    n, rp, col, gd, tab, sim = _setup(orc, gg.grid(6, 5), 2)
+    rng = np.random.default_rng(3)
+    Y = rng.normal(size=(n, 2))
+    R = np.stack([-Y[:, 1], Y[:, 0]], axis=1)
+    for mode in (0, 1):
+        p = orc.Params(k=2, M=5, epochs=7, b=2.0, mode=mode, substeps=3)
+        A = orc.layout_level(tab, Y.copy(), 0, None, p, 0.1)
+        B = orc.layout_level(tab, R.copy(), 0, None, p, 0.1)
+        assert np.array_equal(B, np.stack([-A[:, 1], A[:, 0]], axis=1))
+
+
+def test_translation_equivariance(orc):
+    n, rp, col, gd, tab, sim = _setup(orc, gg.barabasi_albert(80, 2, 4), 1)
+    Y = np.random.default_rng(1).normal(size=(n, 2))
+    p = orc.Params(k=1, M=5, epochs=5, b=1.0, mode=0)
+    A = orc.layout_level(tab, Y.copy(), 0, None, p, 0.1)
+    B = orc.layout_level(tab, Y.copy() + [3.0, -2.0], 0, None, p, 0.1)
+    assert np.allclose(B - [3.0, -2.0], A, atol=1e-9)
+
+
+def test_gamma_zero_equals_no_negatives(orc):
+    n, rp, col, gd, tab, sim = _setup(orc, gg.grid(7, 7), 1)
+    Y = np.random.default_rng(2).normal(size=(n, 2))
+    for mode in (0, 1):
+        a = orc.layout_level(tab, Y.copy(), 0, None, orc.Params(M=5, epochs=4, b=3.0, mode=mode), 0.0)
+        b = orc.layout_level(tab, Y.copy(), 0, None, orc.Params(M=0, epochs=4, b=3.0, mode=mode), 0.1)
+        assert np.array_equal(a, b)
+
+
+def test_sync_with_single_sample_substeps_is_sequential(orc):
+    n, rp, col, gd, tab, sim = _setup(orc, gg.cycle(30), 2)
+    Y = np.random.default_rng(4).normal(size=(n, 2)) * 3
+    seq = orc.layout_level(tab, Y.copy(), 0, None, orc.Params(M=5, epochs=6, b=1.0, mode=1), 0.1)
+    syn = orc.layout_level(tab, Y.copy(), 0, None, orc.Params(M=5, epochs=6, b=1.0, mode=0, substeps=n), 0.1)
+    assert np.allclose(seq, syn, rtol=1e-12, atol=1e-12)
+
+
+def test_epoch_gradient_matches_brute_force_expectation(orc):
+    # Tiny graph: the mean synchronous update over many epochs against the
+    # exact expectation over every edge entry and every negative node.
+    n, rp, col, gd, tab, sim = _setup(orc, gg.erdos_renyi(7, 12, 9), 2)
+    rng = np.random.default_rng(8)
+    Y0 = rng.normal(size=(n, 2)) * 1.5
+    gamma, b, M = 0.3, 1.0, 3
+    lr = 1e-9
+    E = 6000
+    p = orc.Params(M=M, epochs=10 ** 9, b=b, lr0=lr, mode=0, substeps=1, clip=1e300)
+    acc = np.zeros((n, 2))
+    acc2 = np.zeros((n, 2))
+    for t in range(E):
+        Y = orc.layout_level(tab, Y0.copy(), 0, None, p, gamma, t_begin=t, t_end=t + 1)
+        G = (Y - Y0) / (lr * (1 - t / 1e9))
+        acc += G
+        acc2 += G * G
+    mean = acc / E
+    sd = np.sqrt(np.maximum(acc2 / E - mean ** 2, 0) / E)
+    # exact expectation of one epoch (n samples)
+    Pe = tab.q.astype(np.float64) / tab.q.astype(np.float64).sum()
+    Pv = tab.r32.astype(np.float64) / tab.r32.astype(np.float64).sum()
+    EG = np.zeros((n, 2))
+    for e in range(len(Pe)):
+        i, j = int(tab.e_src[e]), int(tab.e_dst[e])
+        fa = np.array(orc.pair_force(*(Y0[i] - Y0[j]), False, gamma, b, 1e300))
+        EG[i] += Pe[e] * fa
+        EG[j] -= Pe[e] * fa
+        for c in range(n):
+            if c in (i, j) or Pv[c] == 0:
+                continue
+            fr = np.array(orc.pair_force(*(Y0[i] - Y0[c]), True, gamma, b, 1e300))
+            EG[i] += Pe[e] * M * Pv[c] * fr
+            EG[c] -= Pe[e] * M * Pv[c] * fr
+    EG *= n
+    assert np.all(np.abs(mean - EG) <= 5 * sd + 1e-9), (mean, EG, sd)
+
+
+def test_coarse_level_maps_through_ancestors(orc):
+    # At a coarse level with anc = identity the level behaves like level 0
+    # with the same random stream; with two fine nodes in one cluster the
+    # cluster never pulls on itself.
+    n, rp, col, gd, tab, sim = _setup(orc, gg.path(6), 1)
+    Y = np.random.default_rng(3).normal(size=(n, 2))
+    p = orc.Params(M=2, epochs=3, b=1.0, mode=0)
+    a = orc.layout_level(tab, Y.copy(), 2, None, p, 0.1)
+    b = orc.layout_level(tab, Y.copy(), 2, np.arange(n, dtype=np.uint32), p, 0.1)
+    assert np.array_equal(a, b)
+    anc = np.zeros(n, np.uint32)  # every node in one cluster: nothing moves
+    Yc = np.array([[0.5, -0.25]])
+    out = orc.layout_level(tab, Yc.copy(), 1, anc, p, 0.1)
+    assert np.array_equal(out, Yc)
+
+
+def test_init_positions_range_and_stream(orc):
+    p = orc.Params(seed=0, init_scale=1e-4)
+    Y = orc.init_positions(p, 0, 5000)
+    assert np.all(np.abs(Y) <= 1e-4)
+    assert abs(Y.mean()) < 5e-6 and abs(Y.std() - 1e-4 / math.sqrt(3)) < 3e-6
+    assert np.all(Y.astype(np.float32).astype(np.float64) == Y)
+    assert not np.array_equal(Y, orc.init_positions(p, 1, 5000))
+
+
+def test_interpolate_takes_parent_position(orc):
+    Yc = np.array([[1.0, 2.0], [3.0, 4.0]])
+    Yf = orc.interpolate(np.array([1, 0, 1], np.uint32), Yc)
+    assert Yf.tolist() == [[3.0, 4.0], [1.0, 2.0], [3.0, 4.0]]
+
+
+# ---------------------------------------------------------------- hierarchy
+def test_hem_prefers_heavy_edges(orc):
+    rp = np.array([0, 1, 3, 4], np.uint64)
+    col = np.array([1, 0, 2, 1], np.uint32)
+    w = np.array([5, 5, 1, 1], np.uint32)
+    m = orc.hem_match(rp, col, w, orc.Params(match_rounds=3), 0)
+    assert m.tolist() == [1, 0, 2]
+
+
+@pytest.mark.parametrize("gen", [lambda: gg.grid(20, 17), lambda: gg.barabasi_albert(500, 3, 2),
+                                 lambda: gg.random_binary_tree(300, 1), lambda: gg.erdos_renyi(200, 150, 3)])
+def test_hem_matching_and_contraction(orc, gen):
+    n, s, d = gen()
+    rp, col = orc.canonical_graph(n, s, d)
+    A = sp.csr_matrix((np.ones(len(col)), col.astype(np.int64), rp.astype(np.int64)), shape=(n, n))
+    m = orc.hem_match(rp, col, None, orc.Params(), 0).astype(np.int64)
+    assert np.array_equal(m[m], np.arange(n))                    # involution
+    pairs = np.nonzero(m != np.arange(n))[0]
+    assert np.all(A[pairs, m[pairs]] == 1)                         # mates are adjacent
+    cid, nc = orc.cluster_ids(m.astype(np.uint32))
+    assert nc == n - len(pairs) // 2
+    assert np.array_equal(cid[m], cid)
+    reps = np.minimum(np.arange(n), m)
+    assert np.all(np.diff(cid[np.unique(reps)].astype(np.int64)) == 1) and cid[0] == 0
+    crp, ccol, cw = orc.contract(rp, col, None, cid, nc)
+    P = sp.csr_matrix((np.ones(n), (np.arange(n), cid.astype(np.int64))), shape=(n, nc))
+    Cm = (P.T @ A @ P).tolil()
+    Cm.setdiag(0)
+    Cm = Cm.tocsr()
+    Cm.eliminate_zeros()
+    Cm.sort_indices()
+    assert np.array_equal(crp.astype(np.int64), Cm.indptr)
+    assert np.array_equal(ccol.astype(np.int64), Cm.indices)
+    assert np.array_equal(cw.astype(np.int64), Cm.data.astype(np.int64))
+    assert cw.sum() == len(col) - 2 * len(pairs) // 2 * 1        # intra-pair edges removed
+
+
+def test_hierarchy_bounds(orc):
+    n, s, d = gg.barabasi_albert(3000, 3, 1)
+    rp, col = orc.canonical_graph(n, s, d)
+    levels = orc.hierarchy(rp, col, orc.Params(stop_nodes=100))
+    sizes = [lv.n for lv in levels]
+    assert sizes[0] == n and len(sizes) > 2
+    for a, b in zip(sizes, sizes[1:]):
+        assert b <= 0.8 * a
+    assert sizes[-2] >= 100
+    assert sum(sizes) <= 5 * n                                   # Sec. 3.2.3 bound on the node part
+    for l in range(1, len(levels)):
+        anc = levels[l].anc
+        assert anc.max() < levels[l].n and len(np.unique(anc)) == levels[l].n
+        prev = np.arange(n) if l == 1 else levels[l - 1].anc
+        assert np.array_equal(anc, levels[l - 1].parent[prev])
+
+
+# ---------------------------------------------------------------- metrics
+def test_metrics_of_a_path_on_a_line(orc):
+    n, s, d = gg.path(40)
+    rp, col = orc.canonical_graph(n, s, d)
+    Y = np.stack([np.arange(n) * 0.7, np.zeros(n)], axis=1)
+    assert orc.neighbourhood_preservation(rp, col, Y) == 1.0
+    assert orc.stress(rp, col, Y) < 1e-28
+
+
+def test_np_matches_brute_force(orc):
+    n, s, d = gg.barabasi_albert(120, 2, 5)
+    rp, col = orc.canonical_graph(n, s, d)
+    Y = np.random.default_rng(0).normal(size=(n, 2))
+    A = sp.csr_matrix((np.ones(len(col)), col.astype(np.int64), rp.astype(np.int64)), shape=(n, n))
+    spd = csg.shortest_path(A, unweighted=True, directed=False)
+    vals = []
+    for i in range(n):
+        G = set(np.nonzero((spd[i] <= 2) & (spd[i] > 0))[0].tolist())
+        k = len(G)
+        dd = ((Y - Y[i]) ** 2).sum(1)
+        order = sorted((dd[j], j) for j in range(n) if j != i)
+        Lset = set(j for _, j in order[:k])
+        vals.append(len(G & Lset) / len(G | Lset))
+    assert math.isclose(orc.neighbourhood_preservation(rp, col, Y), np.mean(vals), rel_tol=1e-12)
+
+
+def test_stress_matches_definition(orc):
+    n, s, d = gg.erdos_renyi(50, 80, 2)
+    rp, col = orc.canonical_graph(n, s, d)
+    Y = np.random.default_rng(1).normal(size=(n, 2))
+    A = sp.csr_matrix((np.ones(len(col)), col.astype(np.int64), rp.astype(np.int64)), shape=(n, n))
+    spd = csg.shortest_path(A, unweighted=True, directed=False)
+    L = np.sqrt(((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    m = np.isfinite(spd) & (spd > 0)
+    w = np.where(m, 1.0 / np.where(m, spd, 1) ** 2, 0)
+
+    def f(a):
+        return (w * (a * L - np.where(m, spd, 0)) ** 2)[m].sum() / n ** 2
+
+    best = minimize_scalar(f, bounds=(1e-3, 100), method="bounded", options={"xatol": 1e-12}).fun
+    assert math.isclose(orc.stress(rp, col, Y), best, rel_tol=1e-6)
+    assert math.isclose(orc.stress(rp, col, Y * 7.5), orc.stress(rp, col, Y), rel_tol=1e-9)
+
+
+# ---------------------------------------------------------------- whole runs
+def test_grid17_quality_near_paper(orc):
+    rows = [l.split() for l in open(golden("grid17_quality.txt")) if l.strip() and not l.startswith("#")]
+    paper = {int(r[0]): (float(r[1]), float(r[2])) for r in rows}
+    n, s, d = gg.grid(17, 17)
+    rp, col = orc.canonical_graph(n, s, d)
+    for k in (1, 3):
+        p = orc.Params(k=k, M=5, epochs=400, b=3.0, mode=1, stop_nodes=8, seed=0)
+        Y = orc.run(n, s, d, p)
+        np_, st = orc.neighbourhood_preservation(rp, col, Y), orc.stress(rp, col, Y)
+        # loose sanity range: the paper's RNG, sigma and learning rate are unknown
+        assert np_ > paper[k][0] - 0.12, (k, np_, paper[k])
+        assert st < paper[k][1] * 1.6, (k, st, paper[k])
