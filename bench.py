@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the DRGraph layout path on one GB300 (or N, as replicas).
+
+A step is one pass of the whole path on one synthetic graph: canonical graph
+from the edge list, k-order distance matrix, similarity and alias tables,
+heavy-edge-matching hierarchy, random coarsest layout, then every level's
+epochs and refinement.  The metric is edge-sample gradient updates per second
+(one update = one positive sample with its M negatives: 1 attractive and M
+repulsive forces), counted over all levels, with the step's wall time on the
+device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--mode hogwild|sync] [--precision fp32|fp16|bf16]
+                  [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank lays out its own
+replica (graph id = rank); there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # the workload the metric is quoted on (1M-node layout time)
+    "dcsbm1m": dict(graph="dcsbm1m", k=2, M=5, epochs=500, b=1.0, stop_nodes=1000,
+                    desc="DC-SBM 1,000,000 nodes, 64 equal blocks, Pareto degree weights exponent 2.5, "
+                         "mean degree 8, in:out 20:1, seed 2; multilevel HEM to <1000 nodes, k=2, M=5, "
+                         "500 epochs per level, b=1"),
+    "ba100k": dict(graph="ba100k", k=3, M=5, epochs=500, b=1.0, stop_nodes=1000,
+                   desc="Barabasi-Albert 100,000 nodes, m=3, seed 1; multilevel HEM to <1000 nodes, k=3, M=5, "
+                        "500 epochs per level, b=1"),
+    "grid32": dict(graph="grid32", k=3, M=5, epochs=500, b=3.0, stop_nodes=1000, multilevel=0,
+                   desc="32x32 grid, single level, k=3, M=5, 500 epochs, b=3"),
+}
+
+ALGO_BYTES_NOTE = ("per sample: edge record 20 B + M node records 8 B + (2+M) position gathers "
+                   "(8 B FP32; negatives 4 B with half copies) + (2+M) 8-B atomic adds; "
+                   "+ (2+M) 4-B ancestor reads on coarse levels")
+
+
+def algo_bytes_per_sample(M, precision, coarse):
+    neg = 4 if precision else 8
+    b = 20 + 8 * M + 2 * 8 + M * neg + (2 + M) * 8
+    if coarse:
+        b += (2 + M) * 4
+    return b
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("layout.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2008_07799_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_sample():
+    """DRAM bytes per sample of k_epoch from the committed ncu summary, or None
+    when the kernel source has changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "k_epoch_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_hash") != kernel_hash():
+            return None
+        return float(d["dram_bytes_per_sample"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.out = os.path.join("/tmp", f"drg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.out, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def make_params(drg, wl, args, gid):
+    p = drg.Params.default(k=wl["k"], M=wl["M"], epochs=wl["epochs"], b=wl["b"], stop_nodes=wl["stop_nodes"],
+                           mode=1 if args.mode == "hogwild" else 0,
+                           precision={"fp32": 0, "fp16": 1, "bf16": 2}[args.precision], seed=args.seed, gid=gid)
+    if "multilevel" in wl:
+        p.multilevel = wl["multilevel"]
+    return p
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+def oracle_sample(wl, budget_s):
+    """The oracle's layout loop on a bounded sample of the workload: the same
+    generator and parameters at a node count the oracle handles, level-0
+    epochs in sequential mode, until about budget_s seconds of CPU time."""
+    import graphgen as gg
+    import oracle as orc
+    if wl["graph"] == "dcsbm1m":
+        n, s, d = gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2)
+        sample = "DC-SBM 20,000 nodes (same generator parameters as the 1M workload), k=2"
+    elif wl["graph"] == "ba100k":
+        n, s, d = gg.barabasi_albert(100_000, 3, 1)
+        sample = "Barabasi-Albert 100,000 nodes m=3 (the workload graph), k=3"
+    else:
+        n, s, d = gg.grid(32, 32)
+        sample = "32x32 grid (the workload graph), k=3"
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, wl["k"])
+    tab, _ = orc.sampling_tables(*gd, wl["k"])
+    p = orc.Params(k=wl["k"], M=wl["M"], epochs=10 ** 6, b=wl["b"], mode=1, seed=0)
+    Y = orc.init_positions(p, 0, n) * 1e4
+    t0 = time.process_time()
+    w0 = time.perf_counter()
+    epochs = 0
+    while time.process_time() - t0 < budget_s:
+        orc.layout_level(tab, Y, 0, None, p, 0.1, epochs, epochs + 1)
+        epochs += 1
+    wall = time.perf_counter() - w0
+    samples = epochs * n
+    return samples / wall, samples, f"{sample}; {epochs} level-0 epochs ({samples} samples) of the FP64 oracle, sequential mode"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_sample(wl, per_step / 4)
+    vals = []
+    t0 = time.perf_counter()
+    sample = ""
+    total_samples = 0
+    for _ in range(args.steps):
+        v, ns, sample = oracle_sample(wl, per_step)
+        vals.append(v)
+        total_samples += ns
+    wall = time.perf_counter() - t0
+    value = total_samples / wall
+    line = {"impl": "reference", "metric": "edge-sample gradient updates/s", "value": value, "unit": "updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * wall / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="dcsbm1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="hogwild", choices=["hogwild", "sync"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import graphgen as gg
+    import paper_2008_07799_gb300 as drg
+    from paper_2008_07799_gb300 import build
+    build.build()
+
+    wl = WORKLOADS[args.workload]
+    n, src, dst = gg.workload(wl["graph"])
+    m = len(src)
+    stream = torch.cuda.current_stream()
+    ctx = drg.Context(local, stream.cuda_stream)
+    p = make_params(drg, wl, args, gid=rank)
+    dsrc = torch.from_numpy(src.view(np.int32)).cuda()
+    ddst = torch.from_numpy(dst.view(np.int32)).cuda()
+    pos = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 1 GiB > L2
+
+    def step():
+        drg.layout_edges(ctx, n, dsrc, ddst, p, pos)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # one profiled pass: per-kernel CUDA events on the library's stream
+    ctx.profile_reset()
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize()
+    ep_ms, ep_launches, ep_samples = ctx.profile_read(drg.PROF_EPOCH)
+    ap_ms, ap_launches, _ = ctx.profile_read(drg.PROF_APPLY)
+    dm_ms, _, nnz = ctx.profile_read(drg.PROF_DMAT)
+    hi_ms, _, levels = ctx.profile_read(drg.PROF_HIER)
+    ctx.profile(False)
+
+    # timed region
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = ctx.launches
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = ctx.launches - launches0
+    clk = clocks.stop()
+    ms = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    samples_per_step = ep_samples
+    value = samples_per_step * world / (ms / 1000.0)
+
+    # end to end through the public API from pinned host buffers
+    hsrc = torch.from_numpy(src.view(np.int32)).pin_memory()
+    hdst = torch.from_numpy(dst.view(np.int32)).pin_memory()
+    hpos = torch.zeros(2 * n, dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        drg.layout_edges(ctx, n, hsrc, hdst, p, hpos)  # host pointers: copies inside the call
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    e2e_value = samples_per_step * world / e2e_s
+    assert np.isfinite(hpos.numpy()).all()
+
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    n0 = n
+    s0 = n0 * wl["epochs"]
+    coarse = max(ep_samples - s0, 0)
+    prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
+    bytes_total = s0 * algo_bytes_per_sample(wl["M"], prec, False) + coarse * algo_bytes_per_sample(wl["M"], prec, True)
+    achieved = bytes_total / (ep_ms / 1000.0) / 1e9
+    tps = ncu_traffic_per_sample()
+    avg_launch_samples = ep_samples / max(ep_launches, 1)
+    line = {
+        "metric": "edge-sample gradient updates/s",
+        "value": value,
+        "unit": "updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == 0 else ("f32+f16" if prec == 1 else "f32+bf16"),
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "mode": args.mode, "precision": args.precision,
+                   "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
+                   "samples_per_step": samples_per_step, "layout_time_ms": ms,
+                   "l2": "1 GiB buffer written between timed steps (flush)",
+                   "parallelism": f"replicas x{world}"},
+        "phases_ms": {"distance_matrix_and_tables": dm_ms, "hierarchy": hi_ms, "k_epoch_total": ep_ms,
+                      "k_apply_total": ap_ms},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "k_epoch", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": None if tps is None else tps * avg_launch_samples,
+                     "algorithmic_bytes_note": ALGO_BYTES_NOTE,
+                     "avg_launch_ms": ep_ms / max(ep_launches, 1), "launches": ep_launches},
+        "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 2 * m * 4,
+                "d2h_bytes_per_step": 2 * n * 4, "seconds_per_step": e2e_s},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        v, ns, sample = oracle_sample(wl, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * drgraph.h -- C ABI of the GB300 DRGraph layout library (libdrgraph.so).
+ *
+ * DRGraph (Zhu et al., arXiv 2008.07799) lays out a graph by negative-sampling
+ * SGD on a sparse t-SNE-style objective, coarse to fine over a multilevel
+ * hierarchy.  This library runs every step of that path in hand-written CUDA
+ * kernels for sm_103a on one GPU:
+ *
+ *   drg_graph_from_edges       Sec. 3.1   undirected unweighted G = (V, E)
+ *   drg_build_distance_matrix  Sec. 3.2.1 sparse k-order distance matrix (Eq. 8),
+ *                                          similarity (Eqs. 4, 9) and the
+ *                                          sampling tables of Sec. 3.2.2
+ *   drg_coarsen / drg_build_hierarchy
+ *                              Sec. 3.2.3 coarsening (heavy-edge matching)
+ *   drg_layout_level           Sec. 3.2.2-3.2.3  epochs of negative-sampling SGD
+ *                                          (Eqs. 11-12) at one level, samples
+ *                                          drawn on G^0, gradients forwarded to
+ *                                          the level through the ancestor map
+ *   drg_interpolate            Sec. 3.2.3 refinement: a fine node starts at its
+ *                                          coarse node's position
+ *   drg_layout / drg_layout_edges      the whole pipeline
+ *   drg_layout_batch           many independent graphs in one launch per step
+ *
+ * Conventions
+ *   - Every call returns a drg_status; nothing aborts.  On error the context's
+ *     message (drg_last_error) says what failed.  Invalid arguments return
+ *     DRG_EINVAL before any device work is queued.
+ *   - Handles (drg_ctx, drg_graph, drg_dmat, drg_hier) are opaque and owned by
+ *     the library; free each with its *_destroy call.  Destroying a context
+ *     frees nothing else: destroy its handles first.
+ *   - Position buffers are caller-owned, interleaved (x, y) FP32 pairs
+ *     (float[2 * n]), on the device unless a call says otherwise.
+ *   - All device work of a context is ordered on its CUDA stream (given to
+ *     drg_create, or created by it).  Calls that must size an output read
+ *     counts back from the device and therefore synchronise the stream; every
+ *     such call says "synchronises".
+ *   - Node ids are uint32 (n < 2^32 - 1); the distance matrix must have fewer
+ *     than 2^32 entries.
+ */
+#ifndef DRGRAPH_H
+#define DRGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DRG_OK = 0,
+    DRG_EINVAL = 1,        /* invalid argument (null pointer, id out of range, bad size) */
+    DRG_ENOMEM = 2,        /* device or host allocation failed */
+    DRG_ECUDA = 3,         /* a CUDA runtime call failed */
+    DRG_ETIMEOUT = 4,      /* a device-side wait exceeded its iteration limit */
+    DRG_EUNSUPPORTED = 5,  /* the request exceeds a documented limit */
+    DRG_EEMPTY = 6         /* the graph has no edge, so nothing can be sampled */
+} drg_status;
+
+typedef struct drg_ctx drg_ctx;
+typedef struct drg_graph drg_graph;
+typedef struct drg_dmat drg_dmat;
+typedef struct drg_hier drg_hier;
+
+/* Parameters of a layout run.  drg_params_default fills the paper's values
+ * (Sec. 4 "Parameters": M = 5, gamma = 0.1, k = 1; Sec. 4.2: gamma = 0.01 on
+ * the coarsest level; supplement: b) and the library's defaults for what the
+ * paper leaves open. */
+typedef struct {
+    uint32_t k;              /* order of the distance matrix, 1..15 (Sec. 3.2.1) */
+    uint32_t M;              /* negative samples per positive sample, 0..64 (Sec. 3.2.2) */
+    uint32_t epochs;         /* epochs per level; an epoch draws n_l samples */
+    float gamma;             /* weight of the negative samples (Eq. 10) */
+    float gamma_coarsest;    /* gamma on the coarsest level of a hierarchy (Sec. 4.2) */
+    float b;                 /* shape of the proximity kernel (1 + d^{2b})^{-1} (Eq. 5) */
+    float lr0;               /* learning rate of epoch 0; epoch t uses lr0 (1 - t/epochs) */
+    float sigma;             /* Gaussian width of the node similarity (Eq. 9) */
+    float clip;              /* each component of each pair force is clipped to [-clip, clip] */
+    float init_scale;        /* coarsest positions uniform in [-init_scale, init_scale]^2 */
+    float rho;               /* stop coarsening when a level keeps more than rho of the nodes */
+    uint64_t seed;           /* key of every Philox4x32-10 stream */
+    uint32_t gid;            /* graph id folded into the random streams */
+    int32_t mode;            /* 0 synchronous, 1 asynchronous (Hogwild) */
+    int32_t precision;       /* 0 FP32; 1 FP16 and 2 BF16 copies for negative-sample gathers */
+    uint32_t substeps;       /* synchronous sub-steps per epoch (>= 1) */
+    uint32_t stop_nodes;     /* coarsen while a level has at least this many nodes */
+    uint32_t match_rounds;   /* handshake rounds of heavy-edge matching */
+    uint32_t max_levels;     /* at most this many levels, 1..64 */
+    int32_t multilevel;      /* 0: lay out G^0 only */
+} drg_params;
+
+/* Mode and precision values. */
+#define DRG_MODE_SYNC 0
+#define DRG_MODE_HOGWILD 1
+#define DRG_PREC_FP32 0
+#define DRG_PREC_FP16 1
+#define DRG_PREC_BF16 2
+
+void drg_params_default(drg_params* p);
+const char* drg_status_string(drg_status s);
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on `device`.  `stream` is a cudaStream_t to order all
+ * work on (for example a torch stream), or NULL to create a private one. */
+drg_status drg_create(drg_ctx** out, int device, void* stream);
+drg_status drg_destroy(drg_ctx* ctx);
+drg_status drg_synchronize(drg_ctx* ctx);
+/* Last error message of the context (empty string when none). */
+const char* drg_last_error(const drg_ctx* ctx);
+/* Number of kernels this library has launched on the context so far. */
+uint64_t drg_kernel_launches(const drg_ctx* ctx);
+
+/* ---------------------------------------------------------------- graphs */
+/* Sec. 3.1: G = (V, E) undirected and unweighted.  Builds the canonical CSR:
+ * self-loops dropped, every edge stored in both directions, duplicates
+ * removed, each row sorted by column.  src/dst hold m endpoint pairs (ids
+ * < n) in host memory (on_device = 0) or device memory (on_device = 1); they
+ * are read, not kept.  Ids >= n return DRG_EINVAL.  Synchronises. */
+drg_status drg_graph_from_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* src,
+                                const uint32_t* dst, int on_device, drg_graph** out);
+/* n nodes and nnz stored directed entries (2 |E|). */
+drg_status drg_graph_info(const drg_graph* g, uint32_t* n, uint64_t* nnz);
+/* Copy the CSR to host buffers: rp[n + 1], col[nnz], w[nnz] (edge weights,
+ * all 1 on an input graph).  Any pointer may be NULL.  Synchronises. */
+drg_status drg_graph_download(drg_ctx* ctx, const drg_graph* g, uint64_t* rp, uint32_t* col, uint32_t* w);
+drg_status drg_graph_destroy(drg_graph* g);
+
+/* ---------------------------------------------------------------- distance matrix */
+/* Sec. 3.2.1 (Eqs. 8-9) and Sec. 3.2.2: the sparse distance matrix GD of G,
+ * entry (i, j) = SPD(v_i, v_j) for every j in NNG(v_i, k), rows sorted by j;
+ * the similarity weights and the two sampling tables drawn from in every
+ * epoch:
+ *   q[e]  = floor((fl(g(d)/Z_i) + fl(g(d)/Z_j)) * 2^30)  (FP32, correctly
+ *           rounded, g(d) = exp(-d^2 / 2 sigma^2) rounded once to FP32,
+ *           Z_i = sum over d = 1..k of count_i(d) * g(d) in that order) --
+ *           proportional to NS_ij (Eq. 4) up to quantisation;
+ *   r[i]  = sum of q over row i (u64); the node table uses r >> shift with
+ *           the smallest shift that makes every value fit 32 bits;
+ *   edge table: Walker alias table over the entries, weights q (the
+ *           positive-sample distribution NS_ij); node table: alias table over
+ *           the nodes, weights r >> shift (the negative-sample distribution,
+ *           proportional to sum_l NS_il).  Both are built by the exact
+ *           integer "sweep" construction (Huebschle-Schneider and Sanders,
+ *           2019), so they are bit-identical to a sequential build.
+ * k must be 1..15.  A graph without edges returns DRG_EEMPTY.  Synchronises. */
+drg_status drg_build_distance_matrix(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma,
+                                     drg_dmat** out);
+drg_status drg_dmat_info(const drg_dmat* d, uint32_t* n, uint64_t* nnz, uint32_t* node_shift);
+/* Copy to host buffers (any may be NULL): rp[n+1], col[nnz], dist[nnz],
+ * q[nnz], r[n], Z[n]; edge table e_thresh[nnz], e_alias[nnz] (entry ids);
+ * node table v_thresh[n], v_alias[n].  Synchronises. */
+drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint32_t* col, uint8_t* dist,
+                             uint32_t* q, uint64_t* r, float* Z, uint32_t* e_thresh, uint32_t* e_alias,
+                             uint32_t* v_thresh, uint32_t* v_alias);
+drg_status drg_dmat_destroy(drg_dmat* d);
+
+/* ---------------------------------------------------------------- hierarchy */
+/* Sec. 3.2.3 "Coarsening", with heavy-edge matching in place of the paper's
+ * star grouping: `rounds` deterministic handshake rounds (each unmatched node
+ * proposes to its unmatched neighbour of largest (edge weight, Philox hash of
+ * the pair and round, smaller id); mutual proposals match), unmatched nodes
+ * stay single; representative min(v, mate(v)), coarse ids numbered in
+ * representative order; coarse edge weights are sums of fine edge weights.
+ * `level` selects the hash stream.  parent (device, n_fine uint32) receives
+ * the coarse id of every fine node.  Synchronises. */
+drg_status drg_coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params* p,
+                       drg_graph** coarse, uint32_t* parent);
+/* Repeated drg_coarsen from G^0 while the level has >= p->stop_nodes nodes,
+ * up to p->max_levels levels; a candidate level keeping more than p->rho of
+ * its parent's nodes is discarded and ends the hierarchy.  The hierarchy
+ * keeps each level's graph, parent map and ancestor map (G^0 node -> level
+ * node).  Level 0 is `g0` itself (not copied; it must outlive the handle).
+ * Synchronises. */
+drg_status drg_build_hierarchy(drg_ctx* ctx, const drg_graph* g0, const drg_params* p, drg_hier** out);
+drg_status drg_hier_info(const drg_hier* h, uint32_t* levels, uint32_t* sizes /* [levels], may be NULL */);
+/* Host copies of level `level`'s parent map (n_level entries, level < levels-1)
+ * and ancestor map (n_0 entries, level >= 1).  Either may be NULL.
+ * Synchronises. */
+drg_status drg_hier_download(drg_ctx* ctx, const drg_hier* h, uint32_t level, uint32_t* parent, uint32_t* anc);
+/* Borrow the graph of one level (owned by the hierarchy). */
+drg_status drg_hier_graph(const drg_hier* h, uint32_t level, const drg_graph** g);
+drg_status drg_hier_destroy(drg_hier* h);
+
+/* ---------------------------------------------------------------- layout */
+/* Sec. 3.2.3 "Layout of the coarsest graph": pos[2 n] (device) uniform in
+ * [-p->init_scale, p->init_scale]^2 from the Philox stream of
+ * (p->seed, p->gid, level). */
+drg_status drg_init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params* p, float* pos);
+
+/* Epochs [t_begin, t_end) of p->epochs at one level (Sec. 3.2.2, Eqs. 11-12;
+ * Sec. 3.2.3 gradient forwarding).  Sample s of epoch t draws from the
+ * Philox stream counter (s, t, tag(level, gid), call): the positive entry
+ * (i, j) from d's edge table and p->M negatives from its node table; the
+ * level's nodes are a = anc(i), c = anc(j), c_m = anc(j_m) (identity at
+ * level 0 or when h is NULL); negatives with c_m == a or c_m == c are
+ * skipped.  The sample moves a by lr (attraction + sum of repulsions), c by
+ * -lr attraction and each c_m by -lr repulsion_m, with
+ *   attraction = -2b d^{2b-2} (y_a - y_c) / (1 + d^{2b}),
+ *   repulsion  = gamma 2b (y_a - y_m) / (d^2 (1 + d^{2b})),
+ * each component clipped to [-clip, clip], zero at distance 0, and
+ * lr = p->lr0 (1 - t / p->epochs).  Synchronous mode cuts each epoch into
+ * p->substeps runs of ceil(n_l / substeps) consecutive samples whose forces
+ * all read the positions at the start of the run; Hogwild mode applies every
+ * update at once with atomic adds, in no fixed order.  pos (device,
+ * float[2 n_level]) is read and updated in place.  `gamma` overrides
+ * p->gamma (use p->gamma_coarsest on the coarsest level). */
+drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
+                            const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end);
+
+/* Sec. 3.2.3 "Refinement": fine_pos[v] = coarse_pos[parent(v)] for every node
+ * of level coarse_level - 1.  Device buffers. */
+drg_status drg_interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos,
+                           float* fine_pos);
+
+/* The whole path on a graph: distance matrix, hierarchy (when p->multilevel),
+ * random coarsest layout, then for each level coarse to fine all epochs and
+ * the refinement.  pos: device float[2 n].  Synchronises. */
+drg_status drg_layout(drg_ctx* ctx, const drg_graph* g, const drg_params* p, float* pos);
+
+/* drg_graph_from_edges + drg_layout in one call.  Edges and positions live in
+ * host memory when the matching *_on_device flag is 0 (copies are made on the
+ * context stream) or in device memory when it is 1.  Synchronises. */
+drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                            int edges_on_device, const drg_params* p, float* pos, int pos_on_device);
+
+/* Lay out `count` independent graphs as one job: graph g uses p with gid = g,
+ * so its result equals drg_layout of that graph alone with gid = g.  Levels
+ * of all graphs that share a level index run in one launch per (sub-)step.
+ * pos[g] are device float[2 n_g].  Synchronises. */
+drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
+                            float* const* pos);
+
+/* ---------------------------------------------------------------- profiling */
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * every launch of the named kernel family (costs a few microseconds per
+ * launch; off by default).  Counters accumulate until reset. */
+#define DRG_PROF_EPOCH 0   /* k_epoch: the sampling / gradient kernel; units = samples */
+#define DRG_PROF_APPLY 1   /* k_apply: synchronous sub-step apply; units = nodes */
+#define DRG_PROF_DMAT 2    /* drg_build_distance_matrix as a whole; units = entries */
+#define DRG_PROF_HIER 3    /* hierarchy construction as a whole; units = levels */
+#define DRG_PROF_COUNT 4
+drg_status drg_profile_enable(drg_ctx* ctx, int on);
+drg_status drg_profile_reset(drg_ctx* ctx);
+/* Total milliseconds, number of timed launches and units of one family.
+ * Synchronises. */
+drg_status drg_profile_read(drg_ctx* ctx, int which, double* ms, uint64_t* launches, uint64_t* units);
+
+/* ---------------------------------------------------------------- inspection */
+/* The draws of samples [s_begin, s_end) of epoch t at `level`: out_i, out_j
+ * (level-0 ids of the positive entry) and out_neg[M per sample], device
+ * buffers.  Same streams as drg_layout_level. */
+drg_status drg_sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, uint32_t s_begin,
+                            uint32_t s_end, const drg_params* p, uint32_t* out_i, uint32_t* out_j,
+                            uint32_t* out_neg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRGRAPH_H */

@@ -1,0 +1,252 @@
+// Internal declarations shared by the CUDA translation units of libdrgraph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/drgraph.h"
+
+namespace drg {
+
+typedef unsigned __int128 u128;
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kPurposeSample = 0, kPurposeInit = 1, kPurposeMatch = 2;
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    drg_status status;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(drg_status s, const std::string& msg) { throw Error{s, msg}; }
+
+#define DRG_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            ::drg::fail(e_ == cudaErrorMemoryAllocation ? DRG_ENOMEM : DRG_ECUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+#define DRG_CHECK(cond, status, msg)          \
+    do {                                              \
+        if (!(cond)) ::drg::fail((status), (msg));  \
+    } while (0)
+
+}  // namespace drg
+
+// ------------------------------------------------------------------ handles
+struct drg_prof_span {
+    cudaEvent_t start, stop;
+    int which;
+    uint64_t units;
+};
+
+struct drg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    std::string err;
+    uint64_t launches = 0;
+    // profiling (drg_profile_*)
+    bool prof = false;
+    std::vector<drg_prof_span> spans;       // recorded, not yet read
+    std::vector<cudaEvent_t> free_events;
+    double prof_ms[DRG_PROF_COUNT] = {0, 0, 0, 0};
+    uint64_t prof_launches[DRG_PROF_COUNT] = {0, 0, 0, 0};
+    uint64_t prof_units[DRG_PROF_COUNT] = {0, 0, 0, 0};
+};
+
+struct drg_graph {
+    drg_ctx* ctx = nullptr;
+    uint32_t n = 0;
+    uint64_t nnz = 0;
+    uint64_t* rp = nullptr;  // [n + 1]
+    uint32_t* col = nullptr; // [nnz]
+    uint32_t* w = nullptr;   // [nnz], nullptr = all ones
+};
+
+// One bucket of the edge alias table: the acceptance threshold and the
+// endpoints of the bucket's own entry and of its alias entry.  32 bytes,
+// aligned, so one draw reads exactly one 32-byte sector.
+struct __align__(32) EdgeRec {
+    uint32_t thresh, i0, j0, i1, j1, pad0, pad1, pad2;
+};
+
+struct drg_dmat {
+    drg_ctx* ctx = nullptr;
+    uint32_t n = 0, k = 0;
+    uint64_t nnz = 0;
+    float sigma = 1.f;
+    uint32_t shift = 0;
+    uint64_t* rp = nullptr;      // [n + 1]
+    uint32_t* col = nullptr;     // [nnz]
+    uint8_t* dist = nullptr;     // [nnz]
+    uint32_t* q = nullptr;       // [nnz]
+    uint64_t* r = nullptr;       // [n]
+    float* Z = nullptr;          // [n]
+    EdgeRec* etab = nullptr;     // [nnz]
+    uint32_t* e_alias = nullptr; // [nnz] alias entry of each bucket
+    uint2* vtab = nullptr;       // [n] {thresh, alias}
+};
+
+struct drg_hier {
+    drg_ctx* ctx = nullptr;
+    std::vector<const drg_graph*> g;   // g[0] borrowed, others owned
+    std::vector<drg_graph*> owned;
+    std::vector<uint32_t*> parent;     // [L-1], level l -> l+1
+    std::vector<uint32_t*> anc;        // [L], anc[0] = nullptr (identity)
+};
+
+namespace drg {
+
+// ------------------------------------------------------------------ device memory
+void* dalloc(drg_ctx* ctx, size_t bytes);
+void dfree(drg_ctx* ctx, void* p);
+
+template <typename T>
+struct DBuf {
+    drg_ctx* ctx = nullptr;
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(drg_ctx* c, size_t count) : ctx(c), n(count) { p = static_cast<T*>(dalloc(c, (count ? count : 1) * sizeof(T))); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        reset();
+        ctx = o.ctx; p = o.p; n = o.n; o.p = nullptr;
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p) dfree(ctx, p);
+        p = nullptr;
+    }
+    T* release() { T* q = p; p = nullptr; return q; }
+    T* get() const { return p; }
+};
+
+// Launch accounting: every kernel launch of the library goes through here.
+void after_launch(drg_ctx* ctx, const char* name);
+
+// Profiling spans (no-ops unless profiling is enabled on the context).
+struct ProfSpan {
+    drg_ctx* ctx;
+    int which;
+    uint64_t units;
+    cudaEvent_t start = nullptr;
+    ProfSpan(drg_ctx* c, int w, uint64_t u);
+    ~ProfSpan();
+};
+void prof_collect(drg_ctx* ctx);
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(drg_ctx* ctx, const char* name, void (*kernel)(KArgs...), uint32_t grid, uint32_t block,
+                     size_t smem, Args&&... args) {
+    if (grid == 0) return;
+    kernel<<<grid, block, smem, ctx->stream>>>(static_cast<KArgs>(args)...);
+    after_launch(ctx, name);
+}
+
+#define DRG_LAUNCH(ctx, kernel, grid, block, smem, ...) \
+    ::drg::launch_k((ctx), #kernel, kernel, (uint32_t)(grid), (uint32_t)(block), (size_t)(smem), __VA_ARGS__)
+
+template <typename T>
+inline void h2d(drg_ctx* ctx, T* dst, const T* src, size_t n) {
+    if (n) DRG_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+}
+template <typename T>
+inline void d2h(drg_ctx* ctx, T* dst, const T* src, size_t n) {
+    if (n) DRG_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+}
+template <typename T>
+inline void d2d(drg_ctx* ctx, T* dst, const T* src, size_t n) {
+    if (n) DRG_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+}
+template <typename T>
+inline T read1(drg_ctx* ctx, const T* src) {
+    T v;
+    DRG_CUDA(cudaMemcpyAsync(&v, src, sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+    DRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return v;
+}
+inline void sync(drg_ctx* ctx) { DRG_CUDA(cudaStreamSynchronize(ctx->stream)); }
+
+inline uint32_t grid_for(size_t n, uint32_t threads, uint32_t cap = 1u << 20) {
+    size_t g = (n + threads - 1) / threads;
+    return (uint32_t)(g < cap ? g : cap);
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds; each round multiplies counter words 0 and 2 by the
+// Philox constants, mixes the high halves with words 1 and 3 and the key;
+// the key is bumped by the golden-ratio Weyl constants between rounds.
+__host__ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Third counter word: purpose | graph id | level.
+__host__ __device__ __forceinline__ uint32_t stream_tag(uint32_t purpose, uint32_t gid, uint32_t level) {
+    return (purpose << 28) | ((gid & 0xFFFFFu) << 8) | (level & 0xFFu);
+}
+
+__host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Alias draw: bucket = floor(R * N / 2^64); keep the bucket when U < thresh.
+__device__ __forceinline__ uint64_t alias_bucket(uint64_t R, uint64_t N) { return __umul64hi(R, N); }
+
+// ------------------------------------------------------------------ internal entry points
+void build_csr_from_keys(drg_ctx* ctx, uint32_t n, uint64_t* keys, uint32_t* vals, size_t count,
+                         drg_graph* out);
+drg_graph* graph_from_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                            bool on_device);
+void graph_free(drg_graph* g);
+drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma);
+void dmat_free(drg_dmat* d);
+drg_graph* coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params& p, uint32_t* parent);
+drg_hier* build_hierarchy(drg_ctx* ctx, const drg_graph* g0, const drg_params& p);
+void hier_free(drg_hier* h);
+void check_params(const drg_params& p);
+void init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params& p, float* pos);
+void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
+                  const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end);
+void interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos, float* fine_pos);
+void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* pos);
+void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
+                  float* const* pos);
+void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, uint32_t s_begin, uint32_t s_end,
+                  const drg_params& p, uint32_t* oi, uint32_t* oj, uint32_t* oneg);
+
+}  // namespace drg

@@ -1,0 +1,450 @@
+// The layout optimisation of DRGraph (Sec. 3.2.2, Eqs. 11-12) on one level
+// of the hierarchy (Sec. 3.2.3), and the whole coarse-to-fine run.
+//
+// Hot kernel k_epoch: one thread per edge sample.  It draws the sample's
+// random words from Philox (counter = sample, epoch, stream tag, call), reads
+// one 32-byte edge-table record (positive pair) and M node-table records
+// (negatives), maps the drawn level-0 nodes to the level through the
+// ancestor map, gathers 2 + M positions, forms the attractive and repulsive
+// pair forces and adds them, with vector atomics, to the gradient buffer
+// (synchronous mode) or straight into the positions (Hogwild mode).  Every
+// access after the Philox step is a random 8- to 32-byte read or atomic; the
+// kernel is bound by L2 (positions, node table) and HBM (edge table) request
+// throughput, not by arithmetic.
+#include "prims.cuh"
+
+#include <cmath>
+
+namespace drg {
+
+struct EpochArgs {
+    const EdgeRec* __restrict__ etab;
+    uint64_t nnz;
+    const uint2* __restrict__ vtab;
+    uint32_t n0;
+    const uint32_t* __restrict__ anc;  // level-0 node -> level node; nullptr = identity
+    float2* Y;                          // positions of the level
+    float2* G;                          // gradient accumulator (synchronous mode)
+    const void* Yh;                     // half-precision copy for negative gathers (or nullptr)
+    uint32_t M;
+    float gamma, b, twob, clip;
+    int bint;                           // 1, 2, 3: integer b; 0: general
+    uint2 key;
+    uint32_t tag, t;
+    float lr;                           // Hogwild step size
+    uint64_t s_begin, s_end;
+};
+
+__device__ __forceinline__ uint32_t lane_word(const uint4& v, uint32_t l) {
+    return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
+}
+
+// Random word `w` of sample s: Philox call w/4, lane w%4.  Calls are made
+// lazily and in increasing order, each once.
+struct Words {
+    uint4 cur;
+    uint32_t idx;
+    uint4 ctr;
+    uint2 key;
+    __device__ __forceinline__ Words(uint32_t s, uint32_t t, uint32_t tag, uint2 k)
+        : idx(0xFFFFFFFFu), ctr(make_uint4(s, t, tag, 0)), key(k) {}
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) {
+        if ((w >> 2) != idx) {
+            idx = w >> 2;
+            ctr.w = idx;
+            cur = philox(ctr, key);
+        }
+        return lane_word(cur, w & 3);
+    }
+};
+
+__device__ __forceinline__ void draw_edge(const EpochArgs& a, Words& W, uint32_t& i, uint32_t& j) {
+    const uint64_t R = (uint64_t)W(0) | ((uint64_t)W(1) << 32);
+    const uint32_t U = W(2);
+    const uint64_t bkt = alias_bucket(R, a.nnz);
+    const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.etab + bkt));
+    const uint32_t j1 = __ldg(&a.etab[bkt].j1);
+    const bool keep = U < r0.x;
+    i = keep ? r0.y : r0.w;
+    j = keep ? r0.z : j1;
+}
+
+__device__ __forceinline__ uint32_t draw_negative(const EpochArgs& a, Words& W, uint32_t m) {
+    const uint64_t R = (uint64_t)W(3 + 3 * m) | ((uint64_t)W(4 + 3 * m) << 32);
+    const uint32_t U = W(5 + 3 * m);
+    const uint64_t bkt = alias_bucket(R, a.n0);
+    const uint2 v = __ldg(&a.vtab[bkt]);
+    return U < v.x ? (uint32_t)bkt : v.y;
+}
+
+__device__ __forceinline__ void pow_terms(float d2, float b, int bint, float& d2bm1, float& d2b) {
+    if (bint == 1) {
+        d2bm1 = 1.f;
+        d2b = d2;
+    } else if (bint == 2) {
+        d2bm1 = d2;
+        d2b = d2 * d2;
+    } else if (bint == 3) {
+        d2bm1 = d2 * d2;
+        d2b = d2bm1 * d2;
+    } else {
+        d2bm1 = powf(d2, b - 1.f);
+        d2b = d2bm1 * d2;
+    }
+}
+
+__device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
+
+// Attraction on y_a from y_c: -2b d^{2b-2} (y_a - y_c) / (1 + d^{2b}).
+__device__ __forceinline__ float2 attract(const EpochArgs& a, float2 ya, float2 yc) {
+    const float dx = ya.x - yc.x, dy = ya.y - yc.y;
+    const float d2 = dx * dx + dy * dy;
+    if (!(d2 > 0.f)) return make_float2(0.f, 0.f);
+    float d2bm1, d2b;
+    pow_terms(d2, a.b, a.bint, d2bm1, d2b);
+    const float coef = -a.twob * d2bm1 / (1.f + d2b);
+    return make_float2(clipf(coef * dx, a.clip), clipf(coef * dy, a.clip));
+}
+
+// Repulsion on y_a from y_m: gamma 2b (y_a - y_m) / (d^2 (1 + d^{2b})).
+__device__ __forceinline__ float2 repel(const EpochArgs& a, float2 ya, float2 ym) {
+    const float dx = ya.x - ym.x, dy = ya.y - ym.y;
+    const float d2 = dx * dx + dy * dy;
+    if (!(d2 > 0.f)) return make_float2(0.f, 0.f);
+    float d2bm1, d2b;
+    pow_terms(d2, a.b, a.bint, d2bm1, d2b);
+    const float coef = a.gamma * a.twob / (d2 * (1.f + d2b));
+    return make_float2(clipf(coef * dx, a.clip), clipf(coef * dy, a.clip));
+}
+
+template <int PREC>
+__device__ __forceinline__ float2 load_neg(const EpochArgs& a, uint32_t v) {
+    if constexpr (PREC == DRG_PREC_FP16) {
+        return __half22float2(reinterpret_cast<const __half2*>(a.Yh)[v]);
+    } else if constexpr (PREC == DRG_PREC_BF16) {
+        return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.Yh)[v]);
+    } else {
+        return a.Y[v];
+    }
+}
+
+template <bool SYNC>
+__device__ __forceinline__ void push(const EpochArgs& a, uint32_t v, float fx, float fy) {
+    if constexpr (SYNC) {
+        atomicAdd(&a.G[v], make_float2(fx, fy));
+    } else {
+        atomicAdd(&a.Y[v], make_float2(a.lr * fx, a.lr * fy));
+    }
+}
+
+// MT > 0: compile-time number of negatives (their loads are all issued before
+// any is used); MT == 0: runtime M, negatives handled one after another.
+template <int MT, bool SYNC, int PREC>
+__global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < a.s_end; s += stride) {
+        Words W((uint32_t)s, a.t, a.tag, a.key);
+        uint32_t i, j;
+        draw_edge(a, W, i, j);
+        if constexpr (MT > 0) {
+            uint32_t jm[MT];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) jm[m] = draw_negative(a, W, m);
+            uint32_t ia = i, ic = j;
+            if (a.anc) {
+                ia = __ldg(&a.anc[i]);
+                ic = __ldg(&a.anc[j]);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) jm[m] = __ldg(&a.anc[jm[m]]);
+            }
+            const float2 ya = a.Y[ia], yc = a.Y[ic];
+            float2 ym[MT];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) ym[m] = load_neg<PREC>(a, jm[m]);
+            const float2 fa = attract(a, ya, yc);
+            float Fx = fa.x, Fy = fa.y;
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                if (jm[m] == ia || jm[m] == ic) continue;
+                const float2 fr = repel(a, ya, ym[m]);
+                Fx += fr.x;
+                Fy += fr.y;
+                push<SYNC>(a, jm[m], -fr.x, -fr.y);
+            }
+            push<SYNC>(a, ia, Fx, Fy);
+            push<SYNC>(a, ic, -fa.x, -fa.y);
+        } else {
+            const uint32_t ia = a.anc ? __ldg(&a.anc[i]) : i;
+            const uint32_t ic = a.anc ? __ldg(&a.anc[j]) : j;
+            const float2 ya = a.Y[ia], yc = a.Y[ic];
+            const float2 fa = attract(a, ya, yc);
+            float Fx = fa.x, Fy = fa.y;
+            for (uint32_t m = 0; m < a.M; ++m) {
+                uint32_t cm = draw_negative(a, W, m);
+                if (a.anc) cm = __ldg(&a.anc[cm]);
+                if (cm == ia || cm == ic) continue;
+                const float2 fr = repel(a, ya, load_neg<PREC>(a, cm));
+                Fx += fr.x;
+                Fy += fr.y;
+                push<SYNC>(a, cm, -fr.x, -fr.y);
+            }
+            push<SYNC>(a, ia, Fx, Fy);
+            push<SYNC>(a, ic, -fa.x, -fa.y);
+        }
+    }
+}
+
+// Synchronous sub-step end: Y += lr G, G = 0 (and the half copy refreshed).
+template <int PREC>
+__global__ void k_apply(float2* __restrict__ Y, float2* __restrict__ G, void* __restrict__ Yh, uint32_t n, float lr) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        const float2 g = G[v];
+        float2 y = Y[v];
+        y.x += lr * g.x;
+        y.y += lr * g.y;
+        Y[v] = y;
+        G[v] = make_float2(0.f, 0.f);
+        if constexpr (PREC == DRG_PREC_FP16) reinterpret_cast<__half2*>(Yh)[v] = __float22half2_rn(y);
+        if constexpr (PREC == DRG_PREC_BF16) reinterpret_cast<__nv_bfloat162*>(Yh)[v] = __float22bfloat162_rn(y);
+    }
+}
+
+template <int PREC>
+__global__ void k_refresh(const float2* __restrict__ Y, void* __restrict__ Yh, uint32_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        if constexpr (PREC == DRG_PREC_FP16) reinterpret_cast<__half2*>(Yh)[v] = __float22half2_rn(Y[v]);
+        if constexpr (PREC == DRG_PREC_BF16) reinterpret_cast<__nv_bfloat162*>(Yh)[v] = __float22bfloat162_rn(Y[v]);
+    }
+}
+
+// Draws only (inspection): the same random streams as k_epoch.
+__global__ void k_draws(EpochArgs a, uint32_t* __restrict__ oi, uint32_t* __restrict__ oj, uint32_t* __restrict__ oneg) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < a.s_end; s += stride) {
+        Words W((uint32_t)s, a.t, a.tag, a.key);
+        uint32_t i, j;
+        draw_edge(a, W, i, j);
+        const uint64_t o = s - a.s_begin;
+        oi[o] = i;
+        oj[o] = j;
+        for (uint32_t m = 0; m < a.M; ++m) oneg[o * a.M + m] = draw_negative(a, W, m);
+    }
+}
+
+// Sec. 3.2.3: random coarsest layout, uniform in [-scale, scale]^2.
+__global__ void k_init(float2* __restrict__ Y, uint32_t n, uint2 key, uint32_t tag, float scale) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 w = philox(make_uint4((uint32_t)v, 0, tag, 0), key);
+        const float ux = __fmul_rn(__uint2float_rn(w.x >> 8), 5.9604644775390625e-08f);
+        const float uy = __fmul_rn(__uint2float_rn(w.y >> 8), 5.9604644775390625e-08f);
+        Y[v] = make_float2(__fmul_rn(__fsub_rn(__fmul_rn(2.f, ux), 1.f), scale),
+                           __fmul_rn(__fsub_rn(__fmul_rn(2.f, uy), 1.f), scale));
+    }
+}
+
+// Sec. 3.2.3 refinement: a fine node starts at its coarse node's position.
+__global__ void k_interp(const float2* __restrict__ coarse, const uint32_t* __restrict__ parent,
+                         float2* __restrict__ fine, uint32_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        fine[v] = coarse[parent[v]];
+}
+
+// ------------------------------------------------------------------ host side
+void check_params(const drg_params& p) {
+    DRG_CHECK(p.k >= 1 && p.k <= 15, DRG_EINVAL, "k must be in [1, 15]");
+    DRG_CHECK(p.M <= 64, DRG_EINVAL, "M must be at most 64");
+    DRG_CHECK(p.epochs >= 1, DRG_EINVAL, "epochs must be >= 1");
+    DRG_CHECK(p.b > 0.f && p.clip > 0.f && p.sigma > 0.f, DRG_EINVAL, "b, clip and sigma must be positive");
+    DRG_CHECK(p.gamma >= 0.f && p.gamma_coarsest >= 0.f, DRG_EINVAL, "gamma must be non-negative");
+    DRG_CHECK(p.mode == DRG_MODE_SYNC || p.mode == DRG_MODE_HOGWILD, DRG_EINVAL, "mode must be 0 or 1");
+    DRG_CHECK(p.precision >= 0 && p.precision <= 2, DRG_EINVAL, "precision must be 0, 1 or 2");
+    DRG_CHECK(p.substeps >= 1, DRG_EINVAL, "substeps must be >= 1");
+    DRG_CHECK(p.max_levels >= 1 && p.max_levels <= 64, DRG_EINVAL, "max_levels must be in [1, 64]");
+    DRG_CHECK(p.rho > 0.f && p.rho <= 1.f, DRG_EINVAL, "rho must be in (0, 1]");
+}
+
+static int int_b(float b) {
+    if (b == 1.f) return 1;
+    if (b == 2.f) return 2;
+    if (b == 3.f) return 3;
+    return 0;
+}
+
+static EpochArgs epoch_args(const drg_dmat* d, const uint32_t* anc, float2* Y, const drg_params& p, float gamma,
+                            uint32_t level) {
+    EpochArgs a{};
+    a.etab = d->etab;
+    a.nnz = d->nnz;
+    a.vtab = d->vtab;
+    a.n0 = d->n;
+    a.anc = anc;
+    a.Y = Y;
+    a.M = p.M;
+    a.gamma = gamma;
+    a.b = p.b;
+    a.twob = 2.f * p.b;
+    a.clip = p.clip;
+    a.bint = int_b(p.b);
+    a.key = seed_key(p.seed);
+    a.tag = stream_tag(kPurposeSample, p.gid, level);
+    return a;
+}
+
+typedef void (*EpochKernel)(EpochArgs);
+
+static EpochKernel pick_epoch(uint32_t M, bool sync, int prec) {
+    static const EpochKernel tab[2][2][3] = {
+        {{k_epoch<0, false, 0>, k_epoch<0, false, 1>, k_epoch<0, false, 2>},
+         {k_epoch<0, true, 0>, k_epoch<0, true, 1>, k_epoch<0, true, 2>}},
+        {{k_epoch<5, false, 0>, k_epoch<5, false, 1>, k_epoch<5, false, 2>},
+         {k_epoch<5, true, 0>, k_epoch<5, true, 1>, k_epoch<5, true, 2>}},
+    };
+    return tab[M == 5 ? 1 : 0][sync ? 1 : 0][prec];
+}
+
+static uint32_t epoch_grid(drg_ctx* ctx, uint64_t count) {
+    const uint64_t want = (count + 255) / 256;
+    const uint64_t cap = (uint64_t)ctx->num_sms * 8;
+    return (uint32_t)(want < cap ? want : cap);
+}
+
+void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
+                  const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end) {
+    check_params(p);
+    DRG_CHECK(d && pos, DRG_EINVAL, "null distance matrix or positions");
+    DRG_CHECK(level == 0 || (h && level < h->g.size()), DRG_EINVAL, "level out of range");
+    DRG_CHECK(t_begin <= t_end && t_end <= p.epochs, DRG_EINVAL, "epoch range outside [0, epochs]");
+    DRG_CHECK(!h || h->g[0]->n == d->n, DRG_EINVAL, "hierarchy and distance matrix describe different graphs");
+    const uint32_t nl = level == 0 ? d->n : h->g[level]->n;
+    const uint32_t* anc = level == 0 ? nullptr : h->anc[level];
+    float2* Y = reinterpret_cast<float2*>(pos);
+    const bool sync_mode = p.mode == DRG_MODE_SYNC;
+    const int prec = p.precision;
+    EpochArgs a = epoch_args(d, anc, Y, p, gamma, level);
+    DBuf<float2> G;
+    DBuf<uint32_t> Yh;
+    if (sync_mode) {
+        G = DBuf<float2>(ctx, nl);
+        DRG_CUDA(cudaMemsetAsync(G.p, 0, sizeof(float2) * nl, ctx->stream));
+        a.G = G.p;
+    }
+    const uint32_t gn = grid_for(nl, 256, (uint32_t)ctx->num_sms * 8);
+    if (prec) {
+        Yh = DBuf<uint32_t>(ctx, nl);
+        a.Yh = Yh.p;
+        if (prec == 1) DRG_LAUNCH(ctx, k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
+        else DRG_LAUNCH(ctx, k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+    }
+    const EpochKernel ek = pick_epoch(p.M, sync_mode, prec);
+    const uint32_t chunk = (uint32_t)(((uint64_t)nl + p.substeps - 1) / p.substeps);
+    for (uint32_t t = t_begin; t < t_end; ++t) {
+        const float lr = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
+        a.t = t;
+        if (sync_mode) {
+            for (uint64_t s0 = 0; s0 < nl; s0 += chunk) {
+                a.s_begin = s0;
+                a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
+                {
+                    ProfSpan span(ctx, DRG_PROF_EPOCH, a.s_end - a.s_begin);
+                    launch_k(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
+                }
+                ProfSpan span(ctx, DRG_PROF_APPLY, nl);
+                if (prec == 0) DRG_LAUNCH(ctx, k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, lr);
+                else if (prec == 1) DRG_LAUNCH(ctx, k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
+                else DRG_LAUNCH(ctx, k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
+            }
+        } else {
+            a.lr = lr;
+            a.s_begin = 0;
+            a.s_end = nl;
+            {
+                ProfSpan span(ctx, DRG_PROF_EPOCH, nl);
+                launch_k(ctx, "k_epoch", ek, epoch_grid(ctx, nl), 256, 0, a);
+            }
+            if (prec == 1) DRG_LAUNCH(ctx, k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            else if (prec == 2) DRG_LAUNCH(ctx, k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+        }
+    }
+}
+
+void init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params& p, float* pos) {
+    DRG_CHECK(pos || n == 0, DRG_EINVAL, "null positions");
+    DRG_LAUNCH(ctx, k_init, grid_for(n, 256, (uint32_t)ctx->num_sms * 8), 256, 0, reinterpret_cast<float2*>(pos), n,
+               seed_key(p.seed), stream_tag(kPurposeInit, p.gid, level), p.init_scale);
+}
+
+void interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos, float* fine_pos) {
+    DRG_CHECK(h && coarse_pos && fine_pos, DRG_EINVAL, "null argument");
+    DRG_CHECK(coarse_level >= 1 && coarse_level < h->g.size(), DRG_EINVAL, "coarse level out of range");
+    const uint32_t nf = h->g[coarse_level - 1]->n;
+    DRG_LAUNCH(ctx, k_interp, grid_for(nf, 256, (uint32_t)ctx->num_sms * 8), 256, 0,
+               reinterpret_cast<const float2*>(coarse_pos), h->parent[coarse_level - 1],
+               reinterpret_cast<float2*>(fine_pos), nf);
+}
+
+void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, uint32_t s_begin, uint32_t s_end,
+                  const drg_params& p, uint32_t* oi, uint32_t* oj, uint32_t* oneg) {
+    check_params(p);
+    DRG_CHECK(d && oi && oj && (oneg || p.M == 0), DRG_EINVAL, "null argument");
+    DRG_CHECK(s_begin <= s_end, DRG_EINVAL, "empty sample range");
+    EpochArgs a = epoch_args(d, nullptr, nullptr, p, p.gamma, level);
+    a.t = t;
+    a.s_begin = s_begin;
+    a.s_end = s_end;
+    DRG_LAUNCH(ctx, k_draws, grid_for(s_end - s_begin, 256, (uint32_t)ctx->num_sms * 8), 256, 0, a, oi, oj, oneg);
+}
+
+// The whole path of Fig. 1: distance matrix and sampling tables on G^0,
+// hierarchy, random coarsest layout, then coarse to fine: all epochs of a
+// level, refinement to the next finer level.
+void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* pos) {
+    check_params(p);
+    DRG_CHECK(g && pos, DRG_EINVAL, "null argument");
+    drg_dmat* d = build_dmat(ctx, g, p.k, p.sigma);
+    drg_hier* h = nullptr;
+    try {
+        h = build_hierarchy(ctx, g, p);
+        const uint32_t L = (uint32_t)h->g.size() - 1;
+        DBuf<float2> cur, nxt;
+        float* cur_pos = pos;
+        if (L > 0) {
+            cur = DBuf<float2>(ctx, h->g[L]->n);
+            cur_pos = reinterpret_cast<float*>(cur.p);
+        }
+        init_positions(ctx, h->g[L]->n, L, p, cur_pos);
+        for (int l = (int)L; l >= 0; --l) {
+            const float gamma = (l == (int)L && L > 0) ? p.gamma_coarsest : p.gamma;
+            layout_level(ctx, d, h, (uint32_t)l, cur_pos, p, gamma, 0, p.epochs);
+            if (l > 0) {
+                float* fine_pos = pos;
+                if (l - 1 > 0) {
+                    nxt = DBuf<float2>(ctx, h->g[l - 1]->n);
+                    fine_pos = reinterpret_cast<float*>(nxt.p);
+                }
+                interpolate(ctx, h, (uint32_t)l, cur_pos, fine_pos);
+                cur = std::move(nxt);
+                cur_pos = fine_pos;
+            }
+        }
+        sync(ctx);
+    } catch (...) {
+        hier_free(h);
+        dmat_free(d);
+        throw;
+    }
+    hier_free(h);
+    dmat_free(d);
+}
+
+void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
+                  float* const* pos) {
+    check_params(p);
+    DRG_CHECK(count == 0 || (graphs && pos), DRG_EINVAL, "null argument");
+    for (uint32_t gidx = 0; gidx < count; ++gidx) {
+        drg_params q = p;
+        q.gid = gidx;
+        layout_full(ctx, graphs[gidx], q, pos[gidx]);
+    }
+}
+
+}  // namespace drg

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every symbol include/drgraph.h
+declares; the Python Params mirror matches the C struct.  No GPU needed: no
+call here reaches the device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def drg():
+    from paper_2008_07799_gb300 import build
+    build.build()
+    import paper_2008_07799_gb300 as m
+    m.lib()
+    return m
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "drgraph.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(drg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(drg):
+    declared = _declared()
+    assert len(declared) >= 25
+    L = drg.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(drg.EXPORTS) == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", drg.LIB_PATH], capture_output=True, text=True).stdout
+    for name in declared:
+        assert re.search(r"\bT " + name + r"\b", out), name
+
+
+def test_params_layout_and_defaults(drg):
+    p = drg.Params.default()
+    assert (p.k, p.M, p.epochs, p.substeps, p.stop_nodes, p.match_rounds, p.max_levels) == (1, 5, 400, 16, 1000, 8, 32)
+    assert abs(p.gamma - 0.1) < 1e-7 and abs(p.gamma_coarsest - 0.01) < 1e-9
+    assert p.b == 1.0 and p.lr0 == 1.0 and p.sigma == 1.0 and p.clip == 5.0 and abs(p.rho - 0.8) < 1e-7
+    assert p.init_scale == float(np.float32(1e-4))
+    assert p.seed == 0 and p.mode == 0 and p.precision == 0 and p.multilevel == 1
+    assert C.sizeof(drg.Params) == 88
+
+
+def test_status_strings_and_null_arguments(drg):
+    L = drg.lib()
+    assert L.drg_status_string(0) == b"ok"
+    assert L.drg_status_string(1) == b"invalid argument"
+    assert L.drg_status_string(6) == b"graph has no edges"
+    # argument checks happen before any device work
+    assert L.drg_create(None, 0, None) == 1
+    assert L.drg_destroy(None) == 1
+    assert L.drg_graph_destroy(None) == 1
+    assert L.drg_layout(None, None, None, None) == 1
+    assert L.drg_kernel_launches(None) == 0

@@ -1,0 +1,286 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: canonical graphs, distance matrices, similarity weights (FP32
+defined), alias tables, sampled indices, initial positions, matchings,
+hierarchies, refinement.  Floating point: one synchronous epoch from the same
+positions within 1e-5 of the layout extent (FP32 kernel vs FP64 oracle);
+whole runs within tolerance on neighbourhood preservation and stress.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def drg():
+    import paper_2008_07799_gb300 as m
+    from paper_2008_07799_gb300 import build
+    build.build()
+    m.lib()
+    assert torch.cuda.is_available()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(drg):
+    return drg.Context(0, torch.cuda.current_stream().cuda_stream)
+
+
+def _graphs():
+    return {
+        "grid32": gg.grid(32, 32),
+        "path7": gg.path(7),
+        "ba2000": gg.barabasi_albert(2000, 3, 11),
+        "tree3000": gg.random_binary_tree(3000, 5),
+        "er_ragged": gg.erdos_renyi(1537, 2100, 3),   # duplicates, self-loops, isolated nodes
+    }
+
+
+def _oracle_csr(orc, g):
+    return orc.canonical_graph(*g)
+
+
+# ---------------------------------------------------------------- graphs
+@pytest.mark.parametrize("name", list(_graphs()))
+def test_canonical_graph(drg, ctx, orc, name):
+    g = _graphs()[name]
+    G = drg.graph_from_edges(ctx, *g)
+    rp, col, w = G.download()
+    orp, ocol = _oracle_csr(orc, g)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    assert np.all(w == 1)
+    # device-resident edge lists give the same graph
+    Gd = drg.graph_from_edges(ctx, g[0], torch.from_numpy(g[1].astype(np.int32)).cuda(),
+                              torch.from_numpy(g[2].astype(np.int32)).cuda())
+    rp2, col2, _ = Gd.download()
+    assert np.array_equal(rp2, orp) and np.array_equal(col2, ocol)
+
+
+def test_invalid_edges_rejected(drg, ctx):
+    with pytest.raises(drg.DrgError) as e:
+        drg.graph_from_edges(ctx, 5, np.array([0, 1], np.uint32), np.array([1, 5], np.uint32))
+    assert e.value.status == 1
+    g = drg.graph_from_edges(ctx, 4, np.array([1, 2], np.uint32), np.array([1, 2], np.uint32))
+    assert g.info() == (4, 0)
+    with pytest.raises(drg.DrgError) as e:
+        drg.build_distance_matrix(ctx, g, 2)
+    assert e.value.status == 6
+
+
+# ---------------------------------------------------------------- distance matrix and tables
+CASES = [("grid32", 1), ("grid32", 2), ("grid32", 3), ("path7", 3), ("ba2000", 2), ("ba2000", 3),
+         ("tree3000", 3), ("er_ragged", 1), ("er_ragged", 4)]
+
+
+@pytest.mark.parametrize("name,k", CASES)
+def test_distance_matrix_and_tables(drg, ctx, orc, name, k):
+    g = _graphs()[name]
+    sigma = 1.0 if k < 4 else 1.7
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, k, sigma)
+    got = D.download()
+    orp, ocol = _oracle_csr(orc, g)
+    gd = orc.korder(orp, ocol, k)
+    assert np.array_equal(got["rp"], gd[0])
+    assert np.array_equal(got["col"], gd[1])
+    assert np.array_equal(got["dist"], gd[2])
+    sim = orc.similarity(*gd, k, sigma)
+    assert np.array_equal(got["Z"].view(np.uint32), sim["Z"].view(np.uint32))
+    assert np.array_equal(got["q"], sim["q"])
+    assert np.array_equal(got["r"], sim["r"])
+    r32, shift = orc.node_weights_u32(sim["r"])
+    assert got["shift"] == shift
+    th, al, _ = orc.alias_build(sim["q"])
+    assert np.array_equal(got["e_thresh"], th) and np.array_equal(got["e_alias"], al)
+    vth, val, _ = orc.alias_build(r32)
+    assert np.array_equal(got["v_thresh"], vth) and np.array_equal(got["v_alias"], val)
+
+
+def _device_tables(orc, g, k, sigma=1.0):
+    orp, ocol = _oracle_csr(orc, g)
+    gd = orc.korder(orp, ocol, k)
+    tab, sim = orc.sampling_tables(*gd, k, sigma)
+    return orp, ocol, gd, tab
+
+
+@pytest.mark.parametrize("level,t", [(0, 0), (0, 7), (3, 499)])
+def test_sample_draws(drg, ctx, orc, level, t):
+    g = _graphs()["ba2000"]
+    orp, ocol, gd, tab = _device_tables(orc, g, 2)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, 2)
+    p = drg.Params.default(M=5, seed=12345678901, gid=3)
+    S = 3001
+    oi = torch.zeros(S, dtype=torch.int32, device="cuda")
+    oj = torch.zeros(S, dtype=torch.int32, device="cuda")
+    on = torch.zeros(S * 5, dtype=torch.int32, device="cuda")
+    drg.sample_draws(ctx, D, level, t, 100, 100 + S, p, oi, oj, on)
+    torch.cuda.synchronize()
+    oi, oj, on = oi.cpu().numpy(), oj.cpu().numpy(), on.cpu().numpy().reshape(S, 5)
+    op = orc.Params(M=5, seed=12345678901, gid=3)
+    for x in list(range(0, S, 7)) + [S - 1]:
+        i, j, neg = orc.sample_draws(tab, op.seed, op.gid, level, t, 100 + x, 5)
+        assert (oi[x], oj[x]) == (i, j) and np.array_equal(on[x], neg), x
+
+
+def test_init_positions(drg, ctx, orc):
+    p = drg.Params.default(seed=99, gid=4)
+    n = 10007
+    Y = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    drg.init_positions(ctx, n, 6, p, Y)
+    torch.cuda.synchronize()
+    ref = orc.init_positions(orc.Params(seed=99, gid=4), 6, n)
+    assert np.array_equal(Y.cpu().numpy().astype(np.float64).reshape(n, 2), ref)
+
+
+# ---------------------------------------------------------------- hierarchy
+@pytest.mark.parametrize("name,stop", [("ba2000", 100), ("grid32", 50), ("tree3000", 200), ("er_ragged", 100)])
+def test_hierarchy(drg, ctx, orc, name, stop):
+    g = _graphs()[name]
+    G = drg.graph_from_edges(ctx, *g)
+    p = drg.Params.default(stop_nodes=stop, seed=7, gid=2)
+    H = drg.build_hierarchy(ctx, G, p)
+    orp, ocol = _oracle_csr(orc, g)
+    levels = orc.hierarchy(orp, ocol, orc.Params(stop_nodes=stop, seed=7, gid=2))
+    assert H.sizes() == [lv.n for lv in levels]
+    for l, lv in enumerate(levels):
+        if l + 1 < len(levels):
+            assert np.array_equal(H.parent(l), lv.parent)
+        if l >= 1:
+            assert np.array_equal(H.anc(l), lv.anc)
+            rp, col, w = H.graph(l).download()
+            assert np.array_equal(rp, lv.rp) and np.array_equal(col, lv.col) and np.array_equal(w, lv.w)
+
+
+def test_coarsen_and_interpolate(drg, ctx, orc):
+    g = _graphs()["ba2000"]
+    G = drg.graph_from_edges(ctx, *g)
+    p = drg.Params.default(stop_nodes=100, seed=3)
+    parent = torch.zeros(2000, dtype=torch.int32, device="cuda")
+    C1 = drg.coarsen(ctx, G, 0, p, parent)
+    orp, ocol = _oracle_csr(orc, g)
+    cid, nc = orc.cluster_ids(orc.hem_match(orp, ocol, None, orc.Params(seed=3), 0))
+    assert np.array_equal(parent.cpu().numpy().astype(np.uint32), cid)
+    crp, ccol, cw = orc.contract(orp, ocol, None, cid, nc)
+    rp, col, w = C1.download()
+    assert np.array_equal(rp, crp) and np.array_equal(col, ccol) and np.array_equal(w, cw)
+    H = drg.build_hierarchy(ctx, G, p)
+    sizes = H.sizes()
+    Yc = torch.randn(2 * sizes[1], device="cuda")
+    Yf = torch.zeros(2 * sizes[0], device="cuda")
+    drg.interpolate(ctx, H, 1, Yc, Yf)
+    torch.cuda.synchronize()
+    par = H.parent(0).astype(np.int64)
+    assert np.array_equal(Yf.cpu().numpy().reshape(-1, 2), Yc.cpu().numpy().reshape(-1, 2)[par])
+
+
+# ---------------------------------------------------------------- epochs
+def _extent(Y):
+    return float(np.max(np.ptp(Y, axis=0)))
+
+
+@pytest.mark.parametrize("name,k,b,level,t", [("grid32", 3, 3.0, 0, 0), ("grid32", 3, 3.0, 0, 250),
+                                              ("ba2000", 2, 1.0, 0, 10), ("ba2000", 2, 1.0, 2, 3),
+                                              ("tree3000", 1, 2.0, 1, 100)])
+def test_sync_epoch_parity(drg, ctx, orc, name, k, b, level, t):
+    g = _graphs()[name]
+    orp, ocol, gd, tab = _device_tables(orc, g, k)
+    op = orc.Params(k=k, M=5, epochs=500, b=b, mode=0, substeps=16, stop_nodes=100, seed=5)
+    levels = orc.hierarchy(orp, ocol, op)
+    level = min(level, len(levels) - 1)
+    nl = levels[level].n
+    rng = np.random.default_rng(level * 1000 + t)
+    Y0 = rng.normal(size=(nl, 2)) * np.sqrt(nl) * 0.3
+    Y0 = Y0.astype(np.float32).astype(np.float64)
+    ref = orc.layout_level(tab, Y0.copy(), level, levels[level].anc, op, 0.1, t_begin=t, t_end=t + 1)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, k)
+    p = drg.Params.default(k=k, M=5, epochs=500, b=b, mode=0, substeps=16, stop_nodes=100, seed=5)
+    H = drg.build_hierarchy(ctx, G, p)
+    Y = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
+    drg.layout_level(ctx, D, H, level, Y, p, 0.1, t, t + 1)
+    torch.cuda.synchronize()
+    got = Y.cpu().numpy().astype(np.float64).reshape(nl, 2)
+    err = np.max(np.abs(got - ref))
+    assert err <= 1e-5 * _extent(ref), (err, _extent(ref))
+    assert np.max(np.abs(ref - Y0)) > 1e-3  # the epoch moved the layout
+
+
+def test_sync_epochs_chain(drg, ctx, orc):
+    # five consecutive epochs from the oracle's state after the first 100
+    g = _graphs()["grid32"]
+    orp, ocol, gd, tab = _device_tables(orc, g, 3)
+    op = orc.Params(k=3, M=5, epochs=500, b=3.0, mode=0, multilevel=False, seed=0)
+    Y = orc.init_positions(op, 0, 1024)
+    Y = orc.layout_level(tab, Y, 0, None, op, 0.1, 0, 100)
+    Y0 = Y.astype(np.float32).astype(np.float64)
+    ref = orc.layout_level(tab, Y0.copy(), 0, None, op, 0.1, 100, 105)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, 3)
+    p = drg.Params.default(k=3, M=5, epochs=500, b=3.0, mode=0, multilevel=0, seed=0)
+    Yd = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
+    drg.layout_level(ctx, D, None, 0, Yd, p, 0.1, 100, 105)
+    torch.cuda.synchronize()
+    got = Yd.cpu().numpy().astype(np.float64).reshape(-1, 2)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * _extent(ref)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_epoch_error(drg, ctx, orc, prec):
+    # half-precision copies feed only the negative-sample gathers: one epoch
+    # stays within 1e-3 of the extent of the FP64 result
+    g = _graphs()["ba2000"]
+    orp, ocol, gd, tab = _device_tables(orc, g, 2)
+    op = orc.Params(k=2, M=5, epochs=500, b=1.0, mode=0, multilevel=False, seed=1)
+    rng = np.random.default_rng(0)
+    Y0 = (rng.normal(size=(2000, 2)) * 12).astype(np.float32).astype(np.float64)
+    ref = orc.layout_level(tab, Y0.copy(), 0, None, op, 0.1, 50, 51)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, 2)
+    p = drg.Params.default(k=2, M=5, epochs=500, b=1.0, mode=0, multilevel=0, seed=1, precision=prec)
+    Yd = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
+    drg.layout_level(ctx, D, None, 0, Yd, p, 0.1, 50, 51)
+    torch.cuda.synchronize()
+    got = Yd.cpu().numpy().astype(np.float64).reshape(-1, 2)
+    assert np.max(np.abs(got - ref)) <= 1e-3 * _extent(ref)
+
+
+# ---------------------------------------------------------------- whole runs
+def _quality(orc, rp, col, Y):
+    return orc.neighbourhood_preservation(rp, col, Y), orc.stress(rp, col, Y)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_whole_run_grid32(drg, ctx, orc, mode):
+    # 32 x 32 grid, k = 3, M = 5, 500 epochs, lr from 1.0, single level, b = 3
+    g = _graphs()["grid32"]
+    orp, ocol = _oracle_csr(orc, g)
+    nps, sts = [], []
+    onps, osts = [], []
+    for seed in range(3):
+        op = orc.Params(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=False, seed=seed)
+        Yo = orc.run(*g, op)
+        a, b_ = _quality(orc, orp, ocol, Yo)
+        onps.append(a)
+        osts.append(b_)
+        p = drg.Params.default(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=0, seed=seed)
+        Y = torch.zeros(2 * 1024, device="cuda")
+        drg.layout_edges(ctx, g[0], g[1], g[2], p, Y)
+        a, b_ = _quality(orc, orp, ocol, Y.cpu().numpy().astype(np.float64).reshape(-1, 2))
+        nps.append(a)
+        sts.append(b_)
+    assert abs(np.mean(nps) - np.mean(onps)) <= 0.01 * np.mean(onps) + 0.02, (nps, onps)
+    assert abs(np.mean(sts) - np.mean(osts)) <= 0.25 * np.mean(osts), (sts, osts)
+
+
+def test_layout_edges_host_buffers(drg, ctx):
+    g = gg.barabasi_albert(3000, 2, 8)
+    p = drg.Params.default(k=2, M=5, epochs=50, b=2.0, mode=1, stop_nodes=200, seed=4)
+    pos = np.zeros(2 * 3000, np.float32)
+    drg.layout_edges(ctx, g[0], g[1], g[2], p, pos)
+    assert np.all(np.isfinite(pos)) and np.ptp(pos) > 1.0
