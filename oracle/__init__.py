@@ -61,7 +61,7 @@ def lib():
     L.orc_tag.restype = C.c_uint32
     L.orc_korder_counts.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, U64P]
     L.orc_korder_fill.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, U64P, U32P, U8P]
-    L.orc_similarity.argtypes = [C.c_uint32, U64P, U32P, U8P, C.c_uint32, C.c_double,
+    L.orc_similarity.argtypes = [C.c_uint32, U64P, U32P, U8P, C.c_uint32, C.c_float,
                                  F32P, F32P, U32P, U64P, F64P]
     L.orc_node_weights_u32.argtypes = [C.c_uint32, U64P, U32P]
     L.orc_node_weights_u32.restype = C.c_uint32

@@ -151,7 +151,8 @@ int orc_korder_fill(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_
  * and Sec. 3.1 Eq. 4 (NS_ij = (NS_{i|j} + NS_{j|i}) / 2|V|).
  *
  * Outputs:
- *   g[d-1]  FP32 Gaussian for d = 1..k (computed in FP64, rounded once)
+ *   g[d-1]  FP32 Gaussian for d = 1..k (computed in FP64 from the FP32
+ *           parameter sigma, rounded once)
  *   Z[i]    FP32 normaliser, summed over d = 1..k in that order
  *   q[e]    quantised edge weight: floor((fl(g/Z_i) + fl(g/Z_j)) * 2^30)
  *           (FP32, correctly rounded, no fused multiply-add); proportional
@@ -162,14 +163,14 @@ int orc_korder_fill(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_
  * Pinned by: rows of NS_{j|i} summing to 1, k = 1 giving 1/deg, symmetry,
  * sum NS_ij = 1 and the quantisation error bound.                           */
 int orc_similarity(uint32_t n, const uint64_t* rp, const uint32_t* col, const uint8_t* dist,
-                   uint32_t k, double sigma, float* g, float* Z, uint32_t* q, uint64_t* r, double* ns)
+                   uint32_t k, float sigma, float* g, float* Z, uint32_t* q, uint64_t* r, double* ns)
 {
     double* g64 = (double*)malloc(sizeof(double) * (k + 1));
     double* Z64 = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
     uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * (k + 1));
     if (!g64 || !Z64 || !cnt) { free(g64); free(Z64); free(cnt); return -1; }
     for (uint32_t d = 1; d <= k; ++d) {
-        g64[d] = exp(-(double)(d * d) / (2.0 * sigma * sigma));
+        g64[d] = exp(-(double)(d * d) / (2.0 * (double)sigma * (double)sigma));
         g[d - 1] = (float)g64[d];
     }
     for (uint32_t i = 0; i < n; ++i) {

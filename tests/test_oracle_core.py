@@ -125,7 +125,8 @@ def _sim_for(orc, g, k, sigma=1.0):
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_similarity_normalisation(orc, k):
     n, rp, col, gd, sim = _sim_for(orc, gg.barabasi_albert(300, 2, 7), k, sigma=1.3)
-    g64 = np.exp(-np.arange(1, k + 1) ** 2 / (2 * 1.3 ** 2))
+    s32 = float(np.float32(1.3))   # sigma is an FP32 parameter
+    g64 = np.exp(-np.arange(1, k + 1) ** 2 / (2 * s32 ** 2))
     assert np.allclose(sim["g"], g64.astype(np.float32), rtol=0, atol=0)
     rows = np.repeat(np.arange(n), np.diff(gd[0]).astype(np.int64))
     dist = gd[2].astype(np.int64)
