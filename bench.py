@@ -215,6 +215,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k", type=int, default=None, help="override the distance-matrix order (profiling cases)")
+    ap.add_argument("--single-level", action="store_true", help="lay out G^0 only (profiling cases)")
+    ap.add_argument("--once", action="store_true", help="run exactly one step and exit (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -236,7 +239,13 @@ def main():
     from paper_2008_07799_gb300 import build
     build.build()
 
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.k is not None:
+        wl["k"] = args.k
+        wl["desc"] += f" (k overridden to {args.k})"
+    if args.single_level:
+        wl["multilevel"] = 0
+        wl["desc"] += " (single level)"
     n, src, dst = gg.workload(wl["graph"])
     m = len(src)
     stream = torch.cuda.current_stream()
@@ -249,6 +258,12 @@ def main():
 
     def step():
         drg.layout_edges(ctx, n, dsrc, ddst, p, pos)
+
+    if args.once:
+        step()
+        torch.cuda.synchronize()
+        print(json.dumps({"once": args.workload, "k": wl["k"], "launches": ctx.launches}), flush=True)
+        return
 
     for _ in range(args.warmup):
         step()

@@ -200,8 +200,10 @@ drg_status drg_init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const dr
  * each component clipped to [-clip, clip], zero at distance 0, and
  * lr = p->lr0 (1 - t / p->epochs).  Synchronous mode cuts each epoch into
  * p->substeps runs of ceil(n_l / substeps) consecutive samples whose forces
- * all read the positions at the start of the run; Hogwild mode applies every
- * update at once with atomic adds, in no fixed order.  pos (device,
+ * all read the positions at the start of the run; Hogwild mode processes the
+ * same runs one after another, each sample applying its updates at once with
+ * atomic adds, in no fixed order within a run (bounding the concurrency to
+ * one run keeps asynchronous SGD close to the sequential method).  pos (device,
  * float[2 n_level]) is read and updated in place.  `gamma` overrides
  * p->gamma (use p->gamma_coarsest on the coarsest level). */
 drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,

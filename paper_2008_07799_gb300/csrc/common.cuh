@@ -162,6 +162,33 @@ inline void launch_k(drg_ctx* ctx, const char* name, void (*kernel)(KArgs...), u
 #define DRG_LAUNCH(ctx, kernel, grid, block, smem, ...) \
     ::drg::launch_k((ctx), #kernel, kernel, (uint32_t)(grid), (uint32_t)(block), (size_t)(smem), __VA_ARGS__)
 
+// Programmatic dependent launch: the kernel may start while the previous
+// kernel of the stream is still running; it must call grid_dependency_wait()
+// before touching anything that kernel writes.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(drg_ctx* ctx, const char* name, void (*kernel)(KArgs...), uint32_t grid, uint32_t block,
+                       size_t smem, Args&&... args) {
+    if (grid == 0) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    if (e != cudaSuccess) fail(DRG_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    after_launch(ctx, name);
+}
+
+// Let the next kernel of the stream start its prologue now.
+__device__ __forceinline__ void grid_dependency_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+// Wait until the previous kernel of the stream has finished and its writes are visible.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T>
 inline void h2d(drg_ctx* ctx, T* dst, const T* src, size_t n) {
     if (n) DRG_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));

@@ -137,26 +137,36 @@ __device__ __forceinline__ void push(const EpochArgs& a, uint32_t v, float fx, f
     }
 }
 
+// One sample per thread.  Prologue (independent of the positions): Philox
+// words, the edge record, the node records and the ancestor lookups.  Then
+// wait for the previous run of samples to finish (programmatic dependent
+// launch), and gather, compute and push.
 // MT > 0: compile-time number of negatives (their loads are all issued before
 // any is used); MT == 0: runtime M, negatives handled one after another.
 template <int MT, bool SYNC, int PREC>
 __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t s = a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < a.s_end; s += stride) {
+    grid_dependency_trigger();
+    const uint64_t s = a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool active = s < a.s_end;
+    {
         Words W((uint32_t)s, a.t, a.tag, a.key);
-        uint32_t i, j;
-        draw_edge(a, W, i, j);
+        uint32_t i = 0, j = 0;
+        if (active) draw_edge(a, W, i, j);
         if constexpr (MT > 0) {
             uint32_t jm[MT];
-#pragma unroll
-            for (int m = 0; m < MT; ++m) jm[m] = draw_negative(a, W, m);
             uint32_t ia = i, ic = j;
-            if (a.anc) {
-                ia = __ldg(&a.anc[i]);
-                ic = __ldg(&a.anc[j]);
+            if (active) {
 #pragma unroll
-                for (int m = 0; m < MT; ++m) jm[m] = __ldg(&a.anc[jm[m]]);
+                for (int m = 0; m < MT; ++m) jm[m] = draw_negative(a, W, m);
+                if (a.anc) {
+                    ia = __ldg(&a.anc[i]);
+                    ic = __ldg(&a.anc[j]);
+#pragma unroll
+                    for (int m = 0; m < MT; ++m) jm[m] = __ldg(&a.anc[jm[m]]);
+                }
             }
+            grid_dependency_wait();
+            if (!active) return;
             const float2 ya = a.Y[ia], yc = a.Y[ic];
             float2 ym[MT];
 #pragma unroll
@@ -174,8 +184,13 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
             push<SYNC>(a, ia, Fx, Fy);
             push<SYNC>(a, ic, -fa.x, -fa.y);
         } else {
-            const uint32_t ia = a.anc ? __ldg(&a.anc[i]) : i;
-            const uint32_t ic = a.anc ? __ldg(&a.anc[j]) : j;
+            uint32_t ia = i, ic = j;
+            if (active && a.anc) {
+                ia = __ldg(&a.anc[i]);
+                ic = __ldg(&a.anc[j]);
+            }
+            grid_dependency_wait();
+            if (!active) return;
             const float2 ya = a.Y[ia], yc = a.Y[ic];
             const float2 fa = attract(a, ya, yc);
             float Fx = fa.x, Fy = fa.y;
@@ -197,6 +212,8 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
 // Synchronous sub-step end: Y += lr G, G = 0 (and the half copy refreshed).
 template <int PREC>
 __global__ void k_apply(float2* __restrict__ Y, float2* __restrict__ G, void* __restrict__ Yh, uint32_t n, float lr) {
+    grid_dependency_trigger();
+    grid_dependency_wait();
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
         const float2 g = G[v];
         float2 y = Y[v];
@@ -211,6 +228,8 @@ __global__ void k_apply(float2* __restrict__ Y, float2* __restrict__ G, void* __
 
 template <int PREC>
 __global__ void k_refresh(const float2* __restrict__ Y, void* __restrict__ Yh, uint32_t n) {
+    grid_dependency_trigger();
+    grid_dependency_wait();
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
         if constexpr (PREC == DRG_PREC_FP16) reinterpret_cast<__half2*>(Yh)[v] = __float22half2_rn(Y[v]);
         if constexpr (PREC == DRG_PREC_BF16) reinterpret_cast<__nv_bfloat162*>(Yh)[v] = __float22bfloat162_rn(Y[v]);
@@ -302,11 +321,8 @@ static EpochKernel pick_epoch(uint32_t M, bool sync, int prec) {
     return tab[M == 5 ? 1 : 0][sync ? 1 : 0][prec];
 }
 
-static uint32_t epoch_grid(drg_ctx* ctx, uint64_t count) {
-    const uint64_t want = (count + 255) / 256;
-    const uint64_t cap = (uint64_t)ctx->num_sms * 8;
-    return (uint32_t)(want < cap ? want : cap);
-}
+// one thread per sample
+static uint32_t epoch_grid(drg_ctx*, uint64_t count) { return (uint32_t)((count + 255) / 256); }
 
 void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                   const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end) {
@@ -346,23 +362,26 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
                 a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
                 {
                     ProfSpan span(ctx, DRG_PROF_EPOCH, a.s_end - a.s_begin);
-                    launch_k(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
+                    launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
                 }
                 ProfSpan span(ctx, DRG_PROF_APPLY, nl);
-                if (prec == 0) DRG_LAUNCH(ctx, k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, lr);
-                else if (prec == 1) DRG_LAUNCH(ctx, k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
-                else DRG_LAUNCH(ctx, k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
+                if (prec == 0) launch_pdl(ctx, "k_apply", k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, lr);
+                else if (prec == 1) launch_pdl(ctx, "k_apply", k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
+                else launch_pdl(ctx, "k_apply", k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
             }
         } else {
+            // asynchronous: the same runs of samples, each run one launch whose
+            // samples update the positions at once; a run sees every update
+            // of the runs before it
             a.lr = lr;
-            a.s_begin = 0;
-            a.s_end = nl;
-            {
-                ProfSpan span(ctx, DRG_PROF_EPOCH, nl);
-                launch_k(ctx, "k_epoch", ek, epoch_grid(ctx, nl), 256, 0, a);
+            for (uint64_t s0 = 0; s0 < nl; s0 += chunk) {
+                a.s_begin = s0;
+                a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
+                ProfSpan span(ctx, DRG_PROF_EPOCH, a.s_end - a.s_begin);
+                launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
             }
-            if (prec == 1) DRG_LAUNCH(ctx, k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
-            else if (prec == 2) DRG_LAUNCH(ctx, k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            if (prec == 1) launch_pdl(ctx, "k_refresh", k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            else if (prec == 2) launch_pdl(ctx, "k_refresh", k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
         }
     }
 }

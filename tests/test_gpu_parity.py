@@ -211,29 +211,41 @@ def test_sync_epoch_parity(drg, ctx, orc, name, k, b, level, t):
     assert np.max(np.abs(ref - Y0)) > 1e-3  # the epoch moved the layout
 
 
-def test_sync_epochs_chain(drg, ctx, orc):
-    # five consecutive epochs from the oracle's state after the first 100
+@pytest.mark.parametrize("t0", [100, 480])
+def test_sync_epochs_chain(drg, ctx, orc, t0):
+    # Five consecutive epochs from the oracle's state after t0 epochs.  The
+    # dynamics amplify rounding differences (early on, a 1e-7 relative
+    # perturbation of the oracle's own input grows to ~15 % of the extent in
+    # five epochs), so the GPU's deviation is bounded by the oracle's own
+    # sensitivity: its divergence under an FP32-rounding-size perturbation.
     g = _graphs()["grid32"]
     orp, ocol, gd, tab = _device_tables(orc, g, 3)
     op = orc.Params(k=3, M=5, epochs=500, b=3.0, mode=0, multilevel=False, seed=0)
     Y = orc.init_positions(op, 0, 1024)
-    Y = orc.layout_level(tab, Y, 0, None, op, 0.1, 0, 100)
+    Y = orc.layout_level(tab, Y, 0, None, op, 0.1, 0, t0)
     Y0 = Y.astype(np.float32).astype(np.float64)
-    ref = orc.layout_level(tab, Y0.copy(), 0, None, op, 0.1, 100, 105)
+    ref = orc.layout_level(tab, Y0.copy(), 0, None, op, 0.1, t0, t0 + 5)
+    rng = np.random.default_rng(1)
+    sens = 0.0
+    for _ in range(3):
+        Yp = Y0 * (1 + 6e-8 * rng.standard_normal(Y0.shape))
+        sens = max(sens, np.max(np.abs(orc.layout_level(tab, Yp, 0, None, op, 0.1, t0, t0 + 5) - ref)))
     G = drg.graph_from_edges(ctx, *g)
     D = drg.build_distance_matrix(ctx, G, 3)
     p = drg.Params.default(k=3, M=5, epochs=500, b=3.0, mode=0, multilevel=0, seed=0)
     Yd = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
-    drg.layout_level(ctx, D, None, 0, Yd, p, 0.1, 100, 105)
+    drg.layout_level(ctx, D, None, 0, Yd, p, 0.1, t0, t0 + 5)
     torch.cuda.synchronize()
     got = Yd.cpu().numpy().astype(np.float64).reshape(-1, 2)
-    assert np.max(np.abs(got - ref)) <= 1e-4 * _extent(ref)
+    err = np.max(np.abs(got - ref))
+    assert err <= 10 * sens + 1e-5 * _extent(ref), (err, sens, _extent(ref))
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_mixed_precision_epoch_error(drg, ctx, orc, prec):
+@pytest.mark.parametrize("prec,tol", [(1, 1e-3), (2, 1e-2)])
+def test_mixed_precision_epoch_error(drg, ctx, orc, prec, tol):
     # half-precision copies feed only the negative-sample gathers: one epoch
-    # stays within 1e-3 of the extent of the FP64 result
+    # stays within a few units of the copy's rounding (FP16 2^-11, BF16 2^-8,
+    # relative to the positions) of the FP64 result
     g = _graphs()["ba2000"]
     orp, ocol, gd, tab = _device_tables(orc, g, 2)
     op = orc.Params(k=2, M=5, epochs=500, b=1.0, mode=0, multilevel=False, seed=1)
@@ -247,7 +259,8 @@ def test_mixed_precision_epoch_error(drg, ctx, orc, prec):
     drg.layout_level(ctx, D, None, 0, Yd, p, 0.1, 50, 51)
     torch.cuda.synchronize()
     got = Yd.cpu().numpy().astype(np.float64).reshape(-1, 2)
-    assert np.max(np.abs(got - ref)) <= 1e-3 * _extent(ref)
+    err = np.max(np.abs(got - ref))
+    assert err <= tol * _extent(ref), (err, _extent(ref))
 
 
 # ---------------------------------------------------------------- whole runs
@@ -257,15 +270,16 @@ def _quality(orc, rp, col, Y):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_whole_run_grid32(drg, ctx, orc, mode):
-    # 32 x 32 grid, k = 3, M = 5, 500 epochs, lr from 1.0, single level, b = 3
+    # 32 x 32 grid, k = 3, M = 5, 500 epochs, lr from 1.0, single level, b = 3.
+    # Runs diverge chaotically from the oracle's, so quality is compared as a
+    # statistic over seeds: medians within 1 % plus twice the oracle's
+    # seed-to-seed spread of the median.
     g = _graphs()["grid32"]
     orp, ocol = _oracle_csr(orc, g)
-    nps, sts = [], []
-    onps, osts = [], []
-    for seed in range(3):
+    nps, sts, onps, osts = [], [], [], []
+    for seed in range(7):
         op = orc.Params(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=False, seed=seed)
-        Yo = orc.run(*g, op)
-        a, b_ = _quality(orc, orp, ocol, Yo)
+        a, b_ = _quality(orc, orp, ocol, orc.run(*g, op))
         onps.append(a)
         osts.append(b_)
         p = drg.Params.default(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=0, seed=seed)
@@ -274,8 +288,12 @@ def test_whole_run_grid32(drg, ctx, orc, mode):
         a, b_ = _quality(orc, orp, ocol, Y.cpu().numpy().astype(np.float64).reshape(-1, 2))
         nps.append(a)
         sts.append(b_)
-    assert abs(np.mean(nps) - np.mean(onps)) <= 0.01 * np.mean(onps) + 0.02, (nps, onps)
-    assert abs(np.mean(sts) - np.mean(osts)) <= 0.25 * np.mean(osts), (sts, osts)
+
+    def spread(x):
+        return 1.2533 * np.std(x) / np.sqrt(len(x))   # standard error of a median
+
+    assert abs(np.median(nps) - np.median(onps)) <= 0.01 * np.median(onps) + 2 * spread(onps), (nps, onps)
+    assert abs(np.median(sts) - np.median(osts)) <= 0.01 * np.median(osts) + 2 * spread(osts), (sts, osts)
 
 
 def test_layout_edges_host_buffers(drg, ctx):
