@@ -11,10 +11,15 @@ __global__ void k_expand_rows(const uint64_t* __restrict__ rp, uint32_t n, uint3
 // ------------------------------------------------------------------ frontier BFS
 // One block per source at a time (rows handed out by an atomic counter).  The
 // block keeps a visited bitmap over all nodes (shared memory when it fits,
-// else a private global slice) and a list of the nodes it discovered, level
+// else a private global slice) and the list of nodes it discovered, level
 // after level.  Frontier expansion is load balanced over the block: frontier
 // nodes are taken BFS_THREADS at a time, their degrees prefix-summed, and
-// every thread then walks an equal share of the concatenated adjacency lists.
+// every thread walks an equal share of the concatenated adjacency lists.
+// Pass 0 only counts each row.  Pass 1 also keeps a summary bitmap (one bit
+// per non-empty bitmap word) and the hop distance of each discovered node,
+// and writes the row sorted by node id straight from the two bitmaps: the
+// summary yields the touched words in increasing order, a prefix sum of
+// their popcounts gives each word's output offset.  No global sort is needed.
 constexpr int BFS_THREADS = 512;
 
 struct BfsArgs {
@@ -22,13 +27,16 @@ struct BfsArgs {
     const uint32_t* col;
     uint32_t n, k;
     uint32_t words;           // bitmap words per block
+    uint32_t swords;          // summary words per block
     uint32_t* gbitmaps;       // nullptr: bitmap in shared memory
-    uint32_t* lists;          // [gridDim.x * n]
+    uint32_t* lists;          // [gridDim.x * n] discovered nodes
+    uint32_t* wlists;         // [gridDim.x * words] touched words (pass 1)
+    uint8_t* dlev;            // [gridDim.x * n] hop distance of discovered nodes (pass 1)
     uint32_t* next_row;       // work counter
     uint64_t* counts;         // pass 0: row sizes
     const uint64_t* gd_rp;    // pass 1: row offsets
-    uint64_t* keys;           // pass 1: (row, col, dist-1) keys
-    int cb, db;
+    uint32_t* gd_col;         // pass 1
+    uint8_t* gd_dist;         // pass 1
 };
 
 __device__ __forceinline__ void bfs_append(uint32_t v, bool isnew, uint32_t* list, uint32_t* s_len) {
@@ -41,22 +49,32 @@ __device__ __forceinline__ void bfs_append(uint32_t v, bool isnew, uint32_t* lis
     if (isnew) list[base + __popc(ballot & lanemask_lt())] = v;
 }
 
-__device__ __forceinline__ bool test_and_set(uint32_t* bm, uint32_t v) {
-    const uint32_t bit = 1u << (v & 31);
-    if (*(volatile uint32_t*)&bm[v >> 5] & bit) return false;
-    return !(atomicOr(&bm[v >> 5], bit) & bit);
+// Marks v visited; true for the one thread that marked it first.  In pass 1
+// the first bit set in a word also marks the word in the summary.
+template <bool FILL>
+__device__ __forceinline__ bool visit(uint32_t* bm, uint32_t* summ, uint32_t v) {
+    const uint32_t w = v >> 5, bit = 1u << (v & 31);
+    if (*(volatile uint32_t*)&bm[w] & bit) return false;
+    const uint32_t old = atomicOr(&bm[w], bit);
+    if (old & bit) return false;
+    if (FILL && old == 0) atomicOr(&summ[w >> 5], 1u << (w & 31));
+    return true;
 }
 
-__global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a, int pass) {
-    extern __shared__ uint32_t smem_bm[];
+template <bool FILL>
+__global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
+    extern __shared__ uint32_t dsm[];
     __shared__ uint64_t s_off[BFS_THREADS];
     __shared__ uint64_t s_start[BFS_THREADS];
     __shared__ uint64_t s_wt[BFS_THREADS / 32];
     __shared__ uint32_t s_row, s_len;
-    __shared__ uint32_t s_lvl_end[16];
-    uint32_t* bm = a.gbitmaps ? a.gbitmaps + (size_t)blockIdx.x * a.words : smem_bm;
+    uint32_t* bm = a.gbitmaps ? a.gbitmaps + (size_t)blockIdx.x * a.words : dsm;
+    uint32_t* summ = a.gbitmaps ? dsm : dsm + a.words;
     uint32_t* list = a.lists + (size_t)blockIdx.x * a.n;
+    uint32_t* wl = FILL ? a.wlists + (size_t)blockIdx.x * a.words : nullptr;
+    uint8_t* dl = FILL ? a.dlev + (size_t)blockIdx.x * a.n : nullptr;
     for (uint32_t w = threadIdx.x; w < a.words; w += BFS_THREADS) bm[w] = 0;
+    for (uint32_t w = threadIdx.x; w < a.swords; w += BFS_THREADS) summ[w] = 0;
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) {
@@ -66,7 +84,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a, int pass) {
         __syncthreads();
         const uint32_t row = s_row;
         if (row >= a.n) break;
-        if (threadIdx.x == 0) atomicOr(&bm[row >> 5], 1u << (row & 31));
+        if (threadIdx.x == 0) visit<FILL>(bm, summ, row);
         __syncthreads();
         // level 1: the source's own adjacency
         {
@@ -77,13 +95,13 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a, int pass) {
                 bool isnew = false;
                 if (x < e) {
                     v = a.col[x];
-                    isnew = test_and_set(bm, v);
+                    isnew = visit<FILL>(bm, summ, v);
+                    if (FILL && isnew) dl[v] = 1;
                 }
                 bfs_append(v, isnew, list, &s_len);
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_lvl_end[1] = s_len;
         uint32_t lo = 0, hi = s_len;
         __syncthreads();
         for (uint32_t d = 2; d <= a.k && lo < hi; ++d) {
@@ -113,7 +131,8 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a, int pass) {
                             if (s_off[mid] <= x) lo2 = mid; else hi2 = mid;
                         }
                         v = a.col[s_start[lo2] + (x - s_off[lo2])];
-                        isnew = test_and_set(bm, v);
+                        isnew = visit<FILL>(bm, summ, v);
+                        if (FILL && isnew) dl[v] = (uint8_t)d;
                     }
                     bfs_append(v, isnew, list, &s_len);
                 }
@@ -121,35 +140,58 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a, int pass) {
             }
             lo = hi;
             hi = s_len;
-            if (threadIdx.x == 0) s_lvl_end[d] = hi;
             __syncthreads();
         }
         const uint32_t total = s_len;
-        if (pass == 0) {
+        if (!FILL) {
             if (threadIdx.x == 0) a.counts[row] = total;
+            for (uint32_t x = threadIdx.x; x < total; x += BFS_THREADS) bm[list[x] >> 5] = 0;
+            if (threadIdx.x == 0) bm[row >> 5] = 0;
         } else {
-            const uint64_t base = a.gd_rp[row];
-            for (uint32_t x = threadIdx.x; x < total; x += BFS_THREADS) {
-                uint32_t d = 1;
-                while (d < a.k && x >= s_lvl_end[d]) ++d;
-                a.keys[base + x] = ((uint64_t)row << (a.cb + a.db)) | ((uint64_t)list[x] << a.db) | (d - 1);
+            if (threadIdx.x == 0) bm[row >> 5] &= ~(1u << (row & 31));  // the source is not its own neighbour
+            __syncthreads();
+            // touched words in increasing order (summary words split in equal ranges)
+            const uint32_t per = (a.swords + BFS_THREADS - 1) / BFS_THREADS;
+            const uint32_t s0 = threadIdx.x * per;
+            const uint32_t s1 = s0 + per < a.swords ? s0 + per : a.swords;
+            uint64_t mine = 0;
+            for (uint32_t s = s0; s < s1; ++s) mine += __popc(summ[s]);
+            uint64_t nw;
+            uint64_t pos = block_exclusive_scan<uint64_t, BFS_THREADS>(mine, s_wt, nw);
+            for (uint32_t s = s0; s < s1; ++s) {
+                uint32_t m = summ[s];
+                summ[s] = 0;
+                while (m) {
+                    const uint32_t b = __ffs(m) - 1;
+                    m &= m - 1;
+                    wl[pos++] = 32 * s + b;
+                }
+            }
+            __syncthreads();
+            // every touched word's bits, in order, with their hop distance
+            uint64_t out = a.gd_rp[row];
+            for (uint64_t c = 0; c < nw; c += BFS_THREADS) {
+                const uint64_t idx = c + threadIdx.x;
+                uint32_t wi = 0, w = 0;
+                if (idx < nw) {
+                    wi = wl[idx];
+                    w = bm[wi];
+                    bm[wi] = 0;
+                }
+                uint64_t tot;
+                uint64_t o = out + block_exclusive_scan<uint64_t, BFS_THREADS>((uint64_t)__popc(w), s_wt, tot);
+                while (w) {
+                    const uint32_t b = __ffs(w) - 1;
+                    w &= w - 1;
+                    const uint32_t v = 32 * wi + b;
+                    a.gd_col[o] = v;
+                    a.gd_dist[o] = dl[v];
+                    ++o;
+                }
+                out += tot;
             }
         }
         __syncthreads();
-        for (uint32_t x = threadIdx.x; x < total; x += BFS_THREADS) bm[list[x] >> 5] = 0;
-        if (threadIdx.x == 0) bm[row >> 5] = 0;
-        // s_lvl_end of unreached levels must not keep stale values
-        if (threadIdx.x < 16) s_lvl_end[threadIdx.x] = total;
-        __syncthreads();
-    }
-}
-
-__global__ void k_unpack_gd(const uint64_t* __restrict__ keys, uint64_t nnz, int db, uint32_t cmask,
-                            uint32_t* __restrict__ col, uint8_t* __restrict__ dist) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = keys[e];
-        col[e] = (uint32_t)(k >> db) & cmask;
-        dist[e] = (uint8_t)((k & ((1ull << db) - 1)) + 1);
     }
 }
 
@@ -172,51 +214,45 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         return;
     }
     const uint32_t words = (n + 31) / 32;
-    const size_t bm_bytes = (size_t)words * 4;
-    const bool smem_bm = bm_bytes + 16384 <= (size_t)ctx->max_smem_optin;
-    const size_t dyn = smem_bm ? bm_bytes : 0;
-    DRG_CUDA(cudaFuncSetAttribute(k_bfs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    const uint32_t swords = (words + 31) / 32;
+    const size_t bm_bytes = (size_t)words * 4, sm_bytes = (size_t)swords * 4;
+    const bool smem_bm = bm_bytes + sm_bytes + 16384 <= (size_t)ctx->max_smem_optin;
+    DRG_CHECK(sm_bytes + 16384 <= (size_t)ctx->max_smem_optin, DRG_EUNSUPPORTED, "graph too large for the BFS");
+    const size_t dyn = (smem_bm ? bm_bytes : 0) + sm_bytes;
+    DRG_CUDA(cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    DRG_CUDA(cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
-    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs, BFS_THREADS, dyn));
+    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs<true>, BFS_THREADS, dyn));
     if (per_sm < 1) per_sm = 1;
     uint32_t blocks = (uint32_t)ctx->num_sms * (uint32_t)per_sm;
     if (blocks > n) blocks = n;
-    // per-block discovered lists (and bitmaps when they live in global memory)
+    // per-block discovered lists, touched-word lists, hop distances (and
+    // bitmaps when they live in global memory)
     DBuf<uint32_t> lists(ctx, (size_t)blocks * n);
+    DBuf<uint32_t> wlists(ctx, (size_t)blocks * words);
+    DBuf<uint8_t> dlev(ctx, (size_t)blocks * n);
     DBuf<uint32_t> gbm(ctx, smem_bm ? 1 : (size_t)blocks * words);
     DBuf<uint32_t> counter(ctx, 1);
     DBuf<uint64_t> counts(ctx, (size_t)n);
     BfsArgs a{};
-    a.rp = g->rp; a.col = g->col; a.n = n; a.k = k; a.words = words;
+    a.rp = g->rp; a.col = g->col; a.n = n; a.k = k; a.words = words; a.swords = swords;
     a.gbitmaps = smem_bm ? nullptr : gbm.p;
-    a.lists = lists.p; a.next_row = counter.p; a.counts = counts.p;
-    a.cb = bitlen(n > 1 ? n - 1 : 1);
-    a.db = bitlen(k - 1);
-    DRG_CHECK(2 * a.cb + a.db <= 64, DRG_EUNSUPPORTED, "graph too large for the distance-matrix key");
+    a.lists = lists.p; a.wlists = wlists.p; a.dlev = dlev.p;
+    a.next_row = counter.p; a.counts = counts.p;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
-    DRG_LAUNCH(ctx, k_bfs, blocks, BFS_THREADS, dyn, a, 0);
+    DRG_LAUNCH(ctx, k_bfs<false>, blocks, BFS_THREADS, dyn, a);
     DBuf<uint64_t> tot(ctx, 1);
     scan<uint64_t>(ctx, LoadArr<uint64_t>{counts.p}, n, d->rp, false, tot.p);
     d2d(ctx, d->rp + n, tot.p, 1);
     d->nnz = read1(ctx, tot.p);
     DRG_CHECK(d->nnz < (1ull << 32), DRG_EUNSUPPORTED, "distance matrix has 2^32 entries or more");
-    const uint64_t nnz = d->nnz;
-    DBuf<uint64_t> keys(ctx, nnz), kalt(ctx, nnz);
+    d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (d->nnz ? d->nnz : 1)));
+    d->dist = static_cast<uint8_t*>(dalloc(ctx, d->nnz ? d->nnz : 1));
     a.gd_rp = d->rp;
-    a.keys = keys.p;
+    a.gd_col = d->col;
+    a.gd_dist = d->dist;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
-    DRG_LAUNCH(ctx, k_bfs, blocks, BFS_THREADS, dyn, a, 1);
-    lists.reset();
-    gbm.reset();
-    uint64_t* kp = keys.p;
-    uint64_t* ap = kalt.p;
-    uint32_t* v0 = nullptr;
-    uint32_t* v1 = nullptr;
-    radix_sort(ctx, kp, ap, v0, v1, nnz, 0, 2 * a.cb + a.db);
-    d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (nnz ? nnz : 1)));
-    d->dist = static_cast<uint8_t*>(dalloc(ctx, nnz ? nnz : 1));
-    const uint32_t cmask = a.cb >= 32 ? 0xFFFFFFFFu : ((1u << a.cb) - 1);
-    DRG_LAUNCH(ctx, k_unpack_gd, grid_for(nnz, 256, 65536), 256, 0, kp, nnz, a.db, cmask, d->col, d->dist);
+    DRG_LAUNCH(ctx, k_bfs<true>, blocks, BFS_THREADS, dyn, a);
 }
 
 // ------------------------------------------------------------------ similarity
@@ -365,34 +401,60 @@ __global__ void __launch_bounds__(MERGE_THREADS) k_merge_ranks(const u128* __res
     }
 }
 
-// floor(own * 2^32 / W) for own < W, by 32 steps of restoring division.
-__device__ __forceinline__ uint32_t frac32(uint64_t own, uint64_t W) {
-    u128 rem = own;
-    uint32_t t = 0;
-#pragma unroll 8
-    for (int b = 31; b >= 0; --b) {
-        rem <<= 1;
-        if (rem >= (u128)W) {
-            rem -= W;
-            t |= 1u << b;
-        }
+// floor(own * 2^32 / W) for own < W and a fixed W: division by an invariant
+// integer with a precomputed reciprocal (Moeller & Granlund, "Improved
+// division by invariant integers", IEEE Trans. Computers 2011, 2-by-1
+// division).  W is normalised to d = W << s (top bit set), v = floor((2^128 -
+// 1) / d) - 2^64; the numerator own * 2^(32 + s) splits into words (u1, u0).
+struct InvDiv {
+    uint64_t d, v;
+    int s;
+};
+
+static InvDiv make_invdiv(uint64_t W) {
+    const int s = __builtin_clzll(W);
+    const uint64_t d = W << s;
+    const u128 v = (~(u128)0) / d - ((u128)1 << 64);
+    return InvDiv{d, (uint64_t)v, s};
+}
+
+__device__ __forceinline__ uint32_t frac32(uint64_t own, const InvDiv& D) {
+    const int sh = 32 + D.s;
+    uint64_t u1, u0;
+    if (sh >= 64) {
+        u1 = own << (sh - 64);
+        u0 = 0;
+    } else {
+        u1 = own >> (64 - sh);
+        u0 = own << sh;
     }
-    return t;
+    uint64_t q0 = D.v * u1;
+    uint64_t q1 = __umul64hi(D.v, u1);
+    q0 += u0;
+    q1 += u1 + (q0 < u0 ? 1u : 0u);
+    q1 += 1;
+    uint64_t r = u0 - q1 * D.d;
+    if (r > q0) {
+        q1 -= 1;
+        r += D.d;
+    }
+    if (r >= D.d) q1 += 1;
+    return (uint32_t)q1;
 }
 
 __global__ void k_alias_lights(const uint32_t* __restrict__ q, const uint32_t* __restrict__ L, uint64_t nL,
                                const uint32_t* __restrict__ H, const uint32_t* __restrict__ a_rank, uint64_t N,
-                               uint64_t W, uint32_t* __restrict__ thresh, uint32_t* __restrict__ alias) {
+                               uint64_t W, InvDiv D, uint32_t* __restrict__ thresh, uint32_t* __restrict__ alias) {
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nL; x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t b = L[x];
-        thresh[b] = frac32((uint64_t)q[b] * N, W);
+        thresh[b] = frac32((uint64_t)q[b] * N, D);
         alias[b] = H[a_rank[x]];
     }
 }
 
 __global__ void k_alias_heavies(const uint32_t* __restrict__ H, uint64_t nH, const u128* __restrict__ S,
                                 const u128* __restrict__ Dl, const uint32_t* __restrict__ b_rank, uint64_t W,
-                                uint32_t* __restrict__ thresh, uint32_t* __restrict__ alias) {
+                                InvDiv D, uint32_t* __restrict__ thresh, uint32_t* __restrict__ alias) {
     for (uint64_t y = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; y < nH; y += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t b = H[y];
         const uint64_t own = (uint64_t)(S[y] + (u128)W - Dl[b_rank[y]]);
@@ -402,7 +464,7 @@ __global__ void k_alias_heavies(const uint32_t* __restrict__ H, uint64_t nH, con
             thresh[b] = 0xFFFFFFFFu;
             alias[b] = b;
         } else {
-            thresh[b] = frac32(own, W);
+            thresh[b] = frac32(own, D);
             alias[b] = H[y + 1];
         }
     }
@@ -442,8 +504,8 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, 
     DBuf<uint32_t> a_rank(ctx, nL), b_rank(ctx, nH);
     const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
     DRG_LAUNCH(ctx, k_merge_ranks, (uint32_t)tiles, MERGE_THREADS, 0, Dl.p, nL, S.p, nH, a_rank.p, b_rank.p);
-    DRG_LAUNCH(ctx, k_alias_lights, grid_for(nL, 256, 65536), 256, 0, q, L.p, nL, H.p, a_rank.p, N, W, thresh, alias);
-    DRG_LAUNCH(ctx, k_alias_heavies, grid_for(nH, 256, 65536), 256, 0, H.p, nH, S.p, Dl.p, b_rank.p, W, thresh,
+    DRG_LAUNCH(ctx, k_alias_lights, grid_for(nL, 256, 65536), 256, 0, q, L.p, nL, H.p, a_rank.p, N, W, make_invdiv(W), thresh, alias);
+    DRG_LAUNCH(ctx, k_alias_heavies, grid_for(nH, 256, 65536), 256, 0, H.p, nH, S.p, Dl.p, b_rank.p, W, make_invdiv(W), thresh,
                alias);
     return true;
 }
