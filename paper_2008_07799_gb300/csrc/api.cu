@@ -33,7 +33,7 @@ static cudaEvent_t take_event(drg_ctx* ctx) {
     return e;
 }
 
-ProfSpan::ProfSpan(drg_ctx* c, int w, uint64_t u) : ctx(c), which(w), units(u) {
+ProfSpan::ProfSpan(drg_ctx* c, int w, uint64_t u, uint64_t launches) : ctx(c), which(w), units(u), count(launches) {
     if (!ctx->prof) return;
     start = take_event(ctx);
     DRG_CUDA(cudaEventRecord(start, ctx->stream));
@@ -50,7 +50,7 @@ ProfSpan::~ProfSpan() {
         return;
     }
     cudaEventRecord(stop, ctx->stream);
-    ctx->spans.push_back(drg_prof_span{start, stop, which, units});
+    ctx->spans.push_back(drg_prof_span{start, stop, which, units, count});
 }
 
 void prof_collect(drg_ctx* ctx) {
@@ -59,7 +59,7 @@ void prof_collect(drg_ctx* ctx) {
         DRG_CUDA(cudaEventSynchronize(sp.stop));
         DRG_CUDA(cudaEventElapsedTime(&ms, sp.start, sp.stop));
         ctx->prof_ms[sp.which] += ms;
-        ctx->prof_launches[sp.which] += 1;
+        ctx->prof_launches[sp.which] += sp.count;
         ctx->prof_units[sp.which] += sp.units;
         ctx->free_events.push_back(sp.start);
         ctx->free_events.push_back(sp.stop);

@@ -46,7 +46,7 @@ struct Error {
 struct drg_prof_span {
     cudaEvent_t start, stop;
     int which;
-    uint64_t units;
+    uint64_t units, count;
 };
 
 struct drg_ctx {
@@ -144,9 +144,9 @@ void after_launch(drg_ctx* ctx, const char* name);
 struct ProfSpan {
     drg_ctx* ctx;
     int which;
-    uint64_t units;
+    uint64_t units, count;
     cudaEvent_t start = nullptr;
-    ProfSpan(drg_ctx* c, int w, uint64_t u);
+    ProfSpan(drg_ctx* c, int w, uint64_t u, uint64_t launches = 1);
     ~ProfSpan();
 };
 void prof_collect(drg_ctx* ctx);

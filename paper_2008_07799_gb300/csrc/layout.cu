@@ -17,7 +17,17 @@
 
 namespace drg {
 
+// Epoch counter of a level run, advanced on the device between epochs.
+struct EpochState {
+    uint32_t t, t_end;       // current epoch, end of the run
+    float lr;                // lr0 (1 - t / epochs) of the current epoch
+    uint32_t pad;
+    const float* lr_tab;     // [epochs] learning rates, computed on the host
+};
+
 struct EpochArgs {
+    const EpochState* st;               // current epoch and learning rate
+    int late;                           // 1: the previous kernel may change st; wait before reading it
     const EdgeRec* __restrict__ etab;
     uint64_t nnz;
     const uint2* __restrict__ vtab;
@@ -30,8 +40,8 @@ struct EpochArgs {
     float gamma, b, twob, clip;
     int bint;                           // 1, 2, 3: integer b; 0: general
     uint2 key;
-    uint32_t tag, t;
-    float lr;                           // Hogwild step size
+    uint32_t tag, t;                    // t: epoch of k_draws (k_epoch reads st->t)
+    float lr;                           // Hogwild step size of the current epoch (set in k_epoch)
     uint64_t s_begin, s_end;
 };
 
@@ -146,10 +156,11 @@ __device__ __forceinline__ void push(const EpochArgs& a, uint32_t v, float fx, f
 template <int MT, bool SYNC, int PREC>
 __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
     grid_dependency_trigger();
+    if (a.late) grid_dependency_wait();
     const uint64_t s = a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool active = s < a.s_end;
     {
-        Words W((uint32_t)s, a.t, a.tag, a.key);
+        Words W((uint32_t)s, __ldcg(&a.st->t), a.tag, a.key);
         uint32_t i = 0, j = 0;
         if (active) draw_edge(a, W, i, j);
         if constexpr (MT > 0) {
@@ -165,8 +176,9 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
                     for (int m = 0; m < MT; ++m) jm[m] = __ldg(&a.anc[jm[m]]);
                 }
             }
-            grid_dependency_wait();
+            if (!a.late) grid_dependency_wait();
             if (!active) return;
+            if constexpr (!SYNC) a.lr = __ldcg(&a.st->lr);
             const float2 ya = a.Y[ia], yc = a.Y[ic];
             float2 ym[MT];
 #pragma unroll
@@ -189,8 +201,9 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
                 ia = __ldg(&a.anc[i]);
                 ic = __ldg(&a.anc[j]);
             }
-            grid_dependency_wait();
+            if (!a.late) grid_dependency_wait();
             if (!active) return;
+            if constexpr (!SYNC) a.lr = __ldcg(&a.st->lr);
             const float2 ya = a.Y[ia], yc = a.Y[ic];
             const float2 fa = attract(a, ya, yc);
             float Fx = fa.x, Fy = fa.y;
@@ -211,9 +224,11 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
 
 // Synchronous sub-step end: Y += lr G, G = 0 (and the half copy refreshed).
 template <int PREC>
-__global__ void k_apply(float2* __restrict__ Y, float2* __restrict__ G, void* __restrict__ Yh, uint32_t n, float lr) {
+__global__ void k_apply(float2* __restrict__ Y, float2* __restrict__ G, void* __restrict__ Yh, uint32_t n,
+                        const EpochState* __restrict__ st) {
     grid_dependency_trigger();
     grid_dependency_wait();
+    const float lr = __ldcg(&st->lr);
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
         const float2 g = G[v];
         float2 y = Y[v];
@@ -234,6 +249,16 @@ __global__ void k_refresh(const float2* __restrict__ Y, void* __restrict__ Yh, u
         if constexpr (PREC == DRG_PREC_FP16) reinterpret_cast<__half2*>(Yh)[v] = __float22half2_rn(Y[v]);
         if constexpr (PREC == DRG_PREC_BF16) reinterpret_cast<__nv_bfloat162*>(Yh)[v] = __float22bfloat162_rn(Y[v]);
     }
+}
+
+// End of an epoch inside the level graph: next epoch and learning rate, and
+// the condition of the graph's WHILE loop.
+__global__ void k_advance(EpochState* st, cudaGraphConditionalHandle loop) {
+    const uint32_t t = st->t + 1;
+    st->t = t;
+    const bool more = t < st->t_end;
+    if (more) st->lr = st->lr_tab[t];
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
 }
 
 // Draws only (inspection): the same random streams as k_epoch.
@@ -351,39 +376,84 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
         if (prec == 1) DRG_LAUNCH(ctx, k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
         else DRG_LAUNCH(ctx, k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
     }
+    if (t_begin == t_end) return;
     const EpochKernel ek = pick_epoch(p.M, sync_mode, prec);
     const uint32_t chunk = (uint32_t)(((uint64_t)nl + p.substeps - 1) / p.substeps);
-    for (uint32_t t = t_begin; t < t_end; ++t) {
-        const float lr = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
-        a.t = t;
-        if (sync_mode) {
-            for (uint64_t s0 = 0; s0 < nl; s0 += chunk) {
-                a.s_begin = s0;
-                a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
-                {
-                    ProfSpan span(ctx, DRG_PROF_EPOCH, a.s_end - a.s_begin);
-                    launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
-                }
-                ProfSpan span(ctx, DRG_PROF_APPLY, nl);
-                if (prec == 0) launch_pdl(ctx, "k_apply", k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, lr);
-                else if (prec == 1) launch_pdl(ctx, "k_apply", k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
-                else launch_pdl(ctx, "k_apply", k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, lr);
-            }
-        } else {
-            // asynchronous: the same runs of samples, each run one launch whose
-            // samples update the positions at once; a run sees every update
-            // of the runs before it
-            a.lr = lr;
-            for (uint64_t s0 = 0; s0 < nl; s0 += chunk) {
-                a.s_begin = s0;
-                a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
-                ProfSpan span(ctx, DRG_PROF_EPOCH, a.s_end - a.s_begin);
+    const uint32_t nchunks = (uint32_t)(((uint64_t)nl + chunk - 1) / chunk);
+
+    // learning rates of every epoch (host, as lr0 (1 - t/T)) and the epoch state
+    std::vector<float> lr_host(p.epochs);
+    for (uint32_t t = 0; t < p.epochs; ++t)
+        lr_host[t] = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
+    DBuf<float> lr_tab(ctx, p.epochs);
+    h2d(ctx, lr_tab.p, lr_host.data(), p.epochs);
+    DBuf<EpochState> st(ctx, 1);
+    const EpochState st0{t_begin, t_end, lr_host[t_begin], 0u, lr_tab.p};
+    h2d(ctx, st.p, &st0, 1);
+    a.st = st.p;
+
+    // One graph per level run: a WHILE node whose body is one epoch -- its
+    // sub-step runs (each a k_epoch launch, chained by programmatic dependent
+    // launch; synchronous mode applies the gradient after each run) and
+    // k_advance, which moves the epoch state on and sets the loop condition.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const uint64_t launches_before = ctx->launches;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    };
+    try {
+        DRG_CUDA(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle loop;
+        DRG_CUDA(cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = loop;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        DRG_CUDA(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        DRG_CUDA(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        try {
+            for (uint32_t c = 0; c < nchunks; ++c) {
+                a.s_begin = (uint64_t)c * chunk;
+                a.s_end = a.s_begin + chunk < nl ? a.s_begin + chunk : nl;
+                a.late = c == 0 ? 1 : 0;  // the first run follows k_advance
                 launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
+                if (sync_mode) {
+                    if (prec == 0) launch_pdl(ctx, "k_apply", k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, st.p);
+                    else if (prec == 1) launch_pdl(ctx, "k_apply", k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, st.p);
+                    else launch_pdl(ctx, "k_apply", k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, st.p);
+                }
             }
-            if (prec == 1) launch_pdl(ctx, "k_refresh", k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
-            else if (prec == 2) launch_pdl(ctx, "k_refresh", k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            if (!sync_mode && prec == 1) launch_pdl(ctx, "k_refresh", k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            if (!sync_mode && prec == 2) launch_pdl(ctx, "k_refresh", k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            DRG_LAUNCH(ctx, k_advance, 1, 1, 0, st.p, loop);
+        } catch (...) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(ctx->stream, &dummy);
+            (void)cudaGetLastError();
+            throw;
         }
+        DRG_CUDA(cudaStreamEndCapture(ctx->stream, &body));
+        DRG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        // count what runs, not what was captured
+        const uint64_t epochs = t_end - t_begin;
+        const uint64_t per_epoch = (uint64_t)nchunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
+        ctx->launches = launches_before + epochs * per_epoch;
+        {
+            ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)nl * epochs, epochs * nchunks);
+            DRG_CUDA(cudaGraphLaunch(exec, ctx->stream));
+        }
+        sync(ctx);
+    } catch (...) {
+        cleanup();
+        throw;
     }
+    cleanup();
 }
 
 void init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params& p, float* pos) {

@@ -282,7 +282,12 @@ def test_whole_run_grid32(drg, ctx, orc, mode):
         a, b_ = _quality(orc, orp, ocol, orc.run(*g, op))
         onps.append(a)
         osts.append(b_)
-        p = drg.Params.default(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=0, seed=seed)
+        # Hogwild is compared with the sequential method: on this small, stiff
+        # (b = 3) grid it needs runs of n/64 samples to match it (measured:
+        # stress .062 at 16 runs, .022 at 64, oracle .017); graphs with b = 1
+        # match from 8 runs on.
+        p = drg.Params.default(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=0, seed=seed,
+                               substeps=16 if mode == 0 else 64)
         Y = torch.zeros(2 * 1024, device="cuda")
         drg.layout_edges(ctx, g[0], g[1], g[2], p, Y)
         a, b_ = _quality(orc, orp, ocol, Y.cpu().numpy().astype(np.float64).reshape(-1, 2))
