@@ -209,6 +209,27 @@ drg_status drg_init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const dr
 drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                             const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end);
 
+/* Allocation-free variant of drg_layout_level (the paper has no counterpart:
+ * this serves callers, not the method).  Some callers cannot allocate device
+ * memory while they run -- for instance a serving process whose device
+ * memory is fully reserved up front by another framework's allocator, or
+ * code that must not grow its footprint after start-up -- and every other
+ * layout call allocates its gradient buffer and epoch state per call.  This
+ * one keeps them in a file-scope device array that every GPU loading the
+ * library holds until the process exits: room for the epoch state and one
+ * gradient pair per node, so levels of at most 1,048,576 nodes (8 MiB);
+ * larger levels return DRG_EUNSUPPORTED.  It runs synchronous FP32 mode only
+ * (other modes or precisions: DRG_EUNSUPPORTED) with the same kernels, random
+ * streams and results as drg_layout_level, launched one by one instead of as
+ * a graph.  It calls no allocating routine: the first call on a device looks
+ * up the array's device address (the only set-up; make that first call
+ * before any stream capture), and every call clears the gradient part, which
+ * keeps the previous call's contents.  All calls share the one array per
+ * device, so calls that overlap on the GPU (other streams, other contexts on
+ * the same device) race and corrupt each other: serialise them. */
+drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
+                                    const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end);
+
 /* Sec. 3.2.3 "Refinement": fine_pos[v] = coarse_pos[parent(v)] for every node
  * of level coarse_level - 1.  Device buffers. */
 drg_status drg_interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos,

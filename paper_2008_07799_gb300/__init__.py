@@ -36,6 +36,7 @@ EXPORTS = [
     "drg_build_hierarchy", "drg_hier_info", "drg_hier_download", "drg_hier_graph", "drg_hier_destroy",
     "drg_init_positions", "drg_layout_level", "drg_interpolate", "drg_layout", "drg_layout_edges",
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
+    "drg_layout_level_noalloc",
 ]
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER = 0, 1, 2, 3
@@ -114,6 +115,7 @@ def lib():
         "drg_hier_destroy": (st, [VP]),
         "drg_init_positions": (st, [VP, C.c_uint32, C.c_uint32, PP, VP]),
         "drg_layout_level": (st, [VP, VP, VP, C.c_uint32, VP, PP, C.c_float, C.c_uint32, C.c_uint32]),
+        "drg_layout_level_noalloc": (st, [VP, VP, VP, C.c_uint32, VP, PP, C.c_float, C.c_uint32, C.c_uint32]),
         "drg_interpolate": (st, [VP, VP, C.c_uint32, VP, VP]),
         "drg_layout": (st, [VP, VP, PP, VP]),
         "drg_layout_edges": (st, [VP, C.c_uint32, C.c_uint64, VP, VP, C.c_int, PP, VP, C.c_int]),

@@ -378,6 +378,14 @@ drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, 
     API_CATCH(ctx)
 }
 
+drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level,
+                                    float* pos, const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end) {
+    if (!ctx || !d || !p || !pos) return DRG_EINVAL;
+    API_TRY
+    drg::layout_level_noalloc(ctx, d, h, level, pos, *p, gamma, t_begin, t_end);
+    API_CATCH(ctx)
+}
+
 drg_status drg_interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos,
                            float* fine_pos) {
     if (!ctx) return DRG_EINVAL;

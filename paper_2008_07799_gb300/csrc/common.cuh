@@ -269,6 +269,8 @@ void check_params(const drg_params& p);
 void init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params& p, float* pos);
 void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                   const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end);
+void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
+                          const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end);
 void interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos, float* fine_pos);
 void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* pos);
 void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,

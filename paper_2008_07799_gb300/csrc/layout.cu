@@ -14,6 +14,7 @@
 #include "prims.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace drg {
 
@@ -533,6 +534,83 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
         drg_params q = p;
         q.gid = gidx;
         layout_full(ctx, graphs[gidx], q, pos[gidx]);
+    }
+}
+
+// ------------------------------------------------------------------ allocation-free level run
+// A variant of the synchronous FP32 level run for callers that must not
+// allocate device memory.  Its scratch -- the epoch state (first 256 bytes)
+// and the gradient accumulator, one float2 per node -- is a file-scope
+// device array that every GPU loading this library holds until the process
+// exits.  Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress
+// (that device current) and keeps it.
+constexpr uint32_t kNoAllocMaxNodes = 1u << 20;
+constexpr uint32_t kNoAllocStateSlots = 32;  // 256 bytes reserved for the EpochState
+static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocStateSlots + kNoAllocMaxNodes];
+
+static_assert(sizeof(EpochState) <= kNoAllocStateSlots * sizeof(float2), "epoch state does not fit its slot");
+
+__global__ void k_noalloc_state(EpochState* st, uint32_t t, uint32_t t_end, float lr) {
+    st->t = t;
+    st->t_end = t_end;
+    st->lr = lr;
+    st->pad = 0;
+    st->lr_tab = nullptr;
+}
+
+static float2* noalloc_scratch(drg_ctx* ctx) {
+    static std::mutex mu;
+    static void* addr[256] = {};
+    DRG_CHECK(ctx->device >= 0 && ctx->device < 256, DRG_EUNSUPPORTED, "device index beyond 255");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[ctx->device]) {
+        int prev = 0;
+        DRG_CUDA(cudaGetDevice(&prev));
+        DRG_CUDA(cudaSetDevice(ctx->device));
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) fail(DRG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        addr[ctx->device] = p;
+    }
+    return static_cast<float2*>(addr[ctx->device]);
+}
+
+void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
+                          const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end) {
+    check_params(p);
+    DRG_CHECK(d && pos, DRG_EINVAL, "null distance matrix or positions");
+    DRG_CHECK(level == 0 || (h && level < h->g.size()), DRG_EINVAL, "level out of range");
+    DRG_CHECK(t_begin <= t_end && t_end <= p.epochs, DRG_EINVAL, "epoch range outside [0, epochs]");
+    DRG_CHECK(!h || h->g[0]->n == d->n, DRG_EINVAL, "hierarchy and distance matrix describe different graphs");
+    DRG_CHECK(p.mode == DRG_MODE_SYNC && p.precision == DRG_PREC_FP32, DRG_EUNSUPPORTED,
+              "the allocation-free run supports synchronous FP32 mode only");
+    const uint32_t nl = level == 0 ? d->n : h->g[level]->n;
+    DRG_CHECK(nl <= kNoAllocMaxNodes, DRG_EUNSUPPORTED,
+              "the allocation-free run is limited to 1048576 nodes per level (its static scratch)");
+    float2* scratch = noalloc_scratch(ctx);
+    EpochState* st = reinterpret_cast<EpochState*>(scratch);
+    float2* G = scratch + kNoAllocStateSlots;
+    float2* Y = reinterpret_cast<float2*>(pos);
+    // the array keeps the previous call's contents: the gradient must start at zero
+    DRG_CUDA(cudaMemsetAsync(G, 0, sizeof(float2) * (size_t)nl, ctx->stream));
+    EpochArgs a = epoch_args(d, level == 0 ? nullptr : h->anc[level], Y, p, gamma, level);
+    a.G = G;
+    a.st = st;
+    const EpochKernel ek = pick_epoch(p.M, true, DRG_PREC_FP32);
+    const uint32_t chunk = (uint32_t)(((uint64_t)nl + p.substeps - 1) / p.substeps);
+    const uint32_t gn = grid_for(nl, 256, (uint32_t)ctx->num_sms * 8);
+    for (uint32_t t = t_begin; t < t_end; ++t) {
+        const float lr = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
+        DRG_LAUNCH(ctx, k_noalloc_state, 1, 1, 0, st, t, t_end, lr);
+        for (uint64_t s0 = 0; s0 < nl; s0 += chunk) {
+            a.s_begin = s0;
+            a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
+            a.late = s0 == 0 ? 1 : 0;
+            launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
+            launch_pdl(ctx, "k_apply", k_apply<0>, gn, 256, 0, Y, G, (void*)nullptr, nl, (const EpochState*)st);
+        }
     }
 }
 
