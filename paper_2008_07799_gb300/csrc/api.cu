@@ -3,6 +3,7 @@
 // turns any failure into a status code plus the context's error message.
 #include "prims.cuh"
 
+#include <cstdlib>
 #include <new>
 
 namespace drg {
@@ -141,6 +142,10 @@ drg_status drg_create(drg_ctx** out, int device, void* stream) {
     API_TRY
     c = new drg_ctx();
     c->device = device;
+    {
+        const char* env = std::getenv("DRG_DIRECT_LAUNCH");
+        c->direct_launch = env && env[0] == '1';
+    }
     DRG_CUDA(cudaSetDevice(device));
     DRG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
     DRG_CUDA(cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));

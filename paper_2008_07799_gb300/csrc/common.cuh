@@ -57,6 +57,7 @@ struct drg_ctx {
     int max_smem_optin = 0;
     std::string err;
     uint64_t launches = 0;
+    bool direct_launch = false;             // DRG_DIRECT_LAUNCH=1: no level graphs (for profilers)
     // profiling (drg_profile_*)
     bool prof = false;
     std::vector<drg_prof_span> spans;       // recorded, not yet read

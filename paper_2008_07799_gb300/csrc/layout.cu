@@ -262,6 +262,15 @@ __global__ void k_advance(EpochState* st, cudaGraphConditionalHandle loop) {
     cudaGraphSetConditional(loop, more ? 1u : 0u);
 }
 
+// Epoch state set from the host side of a level run.
+__global__ void k_set_epoch(EpochState* st, uint32_t t, uint32_t t_end, float lr) {
+    st->t = t;
+    st->t_end = t_end;
+    st->lr = lr;
+    st->pad = 0;
+    st->lr_tab = nullptr;
+}
+
 // Draws only (inspection): the same random streams as k_epoch.
 __global__ void k_draws(EpochArgs a, uint32_t* __restrict__ oi, uint32_t* __restrict__ oj, uint32_t* __restrict__ oneg) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -397,6 +406,35 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
     // sub-step runs (each a k_epoch launch, chained by programmatic dependent
     // launch; synchronous mode applies the gradient after each run) and
     // k_advance, which moves the epoch state on and sets the loop condition.
+    auto epoch_body = [&]() {
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            a.s_begin = (uint64_t)c * chunk;
+            a.s_end = a.s_begin + chunk < nl ? a.s_begin + chunk : nl;
+            a.late = c == 0 ? 1 : 0;  // the first run follows the epoch-state update
+            launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
+            if (sync_mode) {
+                if (prec == 0) launch_pdl(ctx, "k_apply", k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, st.p);
+                else if (prec == 1) launch_pdl(ctx, "k_apply", k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, st.p);
+                else launch_pdl(ctx, "k_apply", k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, st.p);
+            }
+        }
+        if (!sync_mode && prec == 1) launch_pdl(ctx, "k_refresh", k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
+        if (!sync_mode && prec == 2) launch_pdl(ctx, "k_refresh", k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+    };
+    const uint64_t epochs = t_end - t_begin;
+    if (ctx->direct_launch) {
+        // the same launches issued from the host, epoch by epoch (profilers
+        // cannot look inside graphs with conditional nodes)
+        {
+            ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)nl * epochs, epochs * nchunks);
+            for (uint32_t t = t_begin; t < t_end; ++t) {
+                DRG_LAUNCH(ctx, k_set_epoch, 1, 1, 0, st.p, t, t_end, lr_host[t]);
+                epoch_body();
+            }
+        }
+        sync(ctx);
+        return;
+    }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const uint64_t launches_before = ctx->launches;
@@ -419,19 +457,7 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
         DRG_CUDA(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
         try {
-            for (uint32_t c = 0; c < nchunks; ++c) {
-                a.s_begin = (uint64_t)c * chunk;
-                a.s_end = a.s_begin + chunk < nl ? a.s_begin + chunk : nl;
-                a.late = c == 0 ? 1 : 0;  // the first run follows k_advance
-                launch_pdl(ctx, "k_epoch", ek, epoch_grid(ctx, a.s_end - a.s_begin), 256, 0, a);
-                if (sync_mode) {
-                    if (prec == 0) launch_pdl(ctx, "k_apply", k_apply<0>, gn, 256, 0, Y, G.p, (void*)nullptr, nl, st.p);
-                    else if (prec == 1) launch_pdl(ctx, "k_apply", k_apply<1>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, st.p);
-                    else launch_pdl(ctx, "k_apply", k_apply<2>, gn, 256, 0, Y, G.p, (void*)Yh.p, nl, st.p);
-                }
-            }
-            if (!sync_mode && prec == 1) launch_pdl(ctx, "k_refresh", k_refresh<1>, gn, 256, 0, Y, (void*)Yh.p, nl);
-            if (!sync_mode && prec == 2) launch_pdl(ctx, "k_refresh", k_refresh<2>, gn, 256, 0, Y, (void*)Yh.p, nl);
+            epoch_body();
             DRG_LAUNCH(ctx, k_advance, 1, 1, 0, st.p, loop);
         } catch (...) {
             cudaGraph_t dummy = nullptr;
@@ -442,7 +468,6 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
         DRG_CUDA(cudaStreamEndCapture(ctx->stream, &body));
         DRG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         // count what runs, not what was captured
-        const uint64_t epochs = t_end - t_begin;
         const uint64_t per_epoch = (uint64_t)nchunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
         ctx->launches = launches_before + epochs * per_epoch;
         {
@@ -551,13 +576,6 @@ static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocStateSlots + k
 
 static_assert(sizeof(EpochState) <= kNoAllocStateSlots * sizeof(float2), "epoch state does not fit its slot");
 
-__global__ void k_noalloc_state(EpochState* st, uint32_t t, uint32_t t_end, float lr) {
-    st->t = t;
-    st->t_end = t_end;
-    st->lr = lr;
-    st->pad = 0;
-    st->lr_tab = nullptr;
-}
 
 static float2* noalloc_scratch(drg_ctx* ctx) {
     static std::mutex mu;
@@ -603,7 +621,7 @@ void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, ui
     const uint32_t gn = grid_for(nl, 256, (uint32_t)ctx->num_sms * 8);
     for (uint32_t t = t_begin; t < t_end; ++t) {
         const float lr = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
-        DRG_LAUNCH(ctx, k_noalloc_state, 1, 1, 0, st, t, t_end, lr);
+        DRG_LAUNCH(ctx, k_set_epoch, 1, 1, 0, st, t, t_end, lr);
         for (uint64_t s0 = 0; s0 < nl; s0 += chunk) {
             a.s_begin = s0;
             a.s_end = s0 + chunk < nl ? s0 + chunk : nl;
