@@ -278,6 +278,9 @@ def main():
     ap_ms, ap_launches, _ = ctx.profile_read(drg.PROF_APPLY)
     dm_ms, _, nnz = ctx.profile_read(drg.PROF_DMAT)
     hi_ms, _, levels = ctx.profile_read(drg.PROF_HIER)
+    sub_ms = {name: ctx.profile_read(w)[0] for name, w in
+              (("graph", drg.PROF_GRAPH), ("bfs", drg.PROF_BFS), ("similarity", drg.PROF_SIM),
+               ("alias_tables", drg.PROF_ALIAS))}
     ctx.profile(False)
 
     # timed region
@@ -354,8 +357,7 @@ def main():
                    "samples_per_step": samples_per_step, "layout_time_ms": ms,
                    "l2": "1 GiB buffer written between timed steps (flush)",
                    "parallelism": f"replicas x{world}"},
-        "phases_ms": {"distance_matrix_and_tables": dm_ms, "hierarchy": hi_ms, "k_epoch_total": ep_ms,
-                      "k_apply_total": ap_ms},
+        "phases_ms": {"distance_matrix_and_tables": dm_ms, "hierarchy": hi_ms, "layout_levels": ep_ms, **sub_ms},
         "gpu_launches": launches,
         "roofline": {"kernel": "k_epoch", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,

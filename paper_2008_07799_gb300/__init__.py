@@ -39,7 +39,7 @@ EXPORTS = [
     "drg_layout_level_noalloc",
 ]
 
-PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER = 0, 1, 2, 3
+PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS = range(8)
 
 
 class DrgError(RuntimeError):

@@ -40,7 +40,7 @@ ProfSpan::ProfSpan(drg_ctx* c, int w, uint64_t u, uint64_t launches) : ctx(c), w
     DRG_CUDA(cudaEventRecord(start, ctx->stream));
 }
 
-ProfSpan::~ProfSpan() {
+void ProfSpan::close() {
     if (!start) return;
     cudaEvent_t stop = nullptr;
     if (!ctx->free_events.empty()) {
@@ -48,10 +48,22 @@ ProfSpan::~ProfSpan() {
         ctx->free_events.pop_back();
     } else if (cudaEventCreate(&stop) != cudaSuccess) {
         ctx->free_events.push_back(start);
+        start = nullptr;
         return;
     }
     cudaEventRecord(stop, ctx->stream);
     ctx->spans.push_back(drg_prof_span{start, stop, which, units, count});
+    start = nullptr;
+}
+
+void ProfSpan::reopen(int w, uint64_t u) {
+    close();
+    which = w;
+    units = u;
+    count = 1;
+    if (!ctx->prof) return;
+    start = take_event(ctx);
+    DRG_CUDA(cudaEventRecord(start, ctx->stream));
 }
 
 void prof_collect(drg_ctx* ctx) {

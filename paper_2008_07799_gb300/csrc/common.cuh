@@ -62,9 +62,9 @@ struct drg_ctx {
     bool prof = false;
     std::vector<drg_prof_span> spans;       // recorded, not yet read
     std::vector<cudaEvent_t> free_events;
-    double prof_ms[DRG_PROF_COUNT] = {0, 0, 0, 0};
-    uint64_t prof_launches[DRG_PROF_COUNT] = {0, 0, 0, 0};
-    uint64_t prof_units[DRG_PROF_COUNT] = {0, 0, 0, 0};
+    double prof_ms[DRG_PROF_COUNT] = {};
+    uint64_t prof_launches[DRG_PROF_COUNT] = {};
+    uint64_t prof_units[DRG_PROF_COUNT] = {};
 };
 
 struct drg_graph {
@@ -148,7 +148,11 @@ struct ProfSpan {
     uint64_t units, count;
     cudaEvent_t start = nullptr;
     ProfSpan(drg_ctx* c, int w, uint64_t u, uint64_t launches = 1);
-    ~ProfSpan();
+    ~ProfSpan() { close(); }
+    void close();                          // end the span now (idempotent)
+    void reopen(int w, uint64_t u);        // end it and start a new one
+    ProfSpan(const ProfSpan&) = delete;
+    ProfSpan& operator=(const ProfSpan&) = delete;
 };
 void prof_collect(drg_ctx* ctx);
 

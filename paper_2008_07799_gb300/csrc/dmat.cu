@@ -11,15 +11,21 @@ __global__ void k_expand_rows(const uint64_t* __restrict__ rp, uint32_t n, uint3
 // ------------------------------------------------------------------ frontier BFS
 // One block per source at a time (rows handed out by an atomic counter).  The
 // block keeps a visited bitmap over all nodes (shared memory when it fits,
-// else a private global slice) and the list of nodes it discovered, level
-// after level.  Frontier expansion is load balanced over the block: frontier
-// nodes are taken BFS_THREADS at a time, their degrees prefix-summed, and
-// every thread walks an equal share of the concatenated adjacency lists.
-// Pass 0 only counts each row.  Pass 1 also keeps a summary bitmap (one bit
-// per non-empty bitmap word) and the hop distance of each discovered node,
-// and writes the row sorted by node id straight from the two bitmaps: the
-// summary yields the touched words in increasing order, a prefix sum of
-// their popcounts gives each word's output offset.  No global sort is needed.
+// else a private global slice), a summary bitmap with one bit per non-empty
+// bitmap word, and the list of nodes it discovered, level after level.
+// Frontier expansion is load balanced over the block: frontier nodes are
+// taken BFS_THREADS at a time, their degrees prefix-summed, and every thread
+// walks an equal share of the concatenated adjacency lists.  The row is then
+// written sorted by node id straight from the bitmaps (the summary yields the
+// touched words in increasing order; a prefix sum of their popcounts gives
+// each word's output offset) -- no global sort.  Hop distances: for k = 2 a
+// node is at distance 1 exactly when it is in the source's adjacency, whose
+// nodes are located in the emitted row by binary search; for k > 2 the
+// block records each discovered node's level.
+// Staged mode writes each row into a staging area at an offset reserved with
+// an atomic cursor (one traversal gives the counts and the rows); direct mode
+// writes at the final row offsets and is the fallback when the staging area
+// overflows.
 constexpr int BFS_THREADS = 512;
 
 struct BfsArgs {
@@ -30,13 +36,18 @@ struct BfsArgs {
     uint32_t swords;          // summary words per block
     uint32_t* gbitmaps;       // nullptr: bitmap in shared memory
     uint32_t* lists;          // [gridDim.x * n] discovered nodes
-    uint32_t* wlists;         // [gridDim.x * words] touched words (pass 1)
-    uint8_t* dlev;            // [gridDim.x * n] hop distance of discovered nodes (pass 1)
+    uint32_t* wlists;         // [gridDim.x * words] touched words
+    uint8_t* dlev;            // [gridDim.x * n] hop distance of discovered nodes (k > 2)
     uint32_t* next_row;       // work counter
-    uint64_t* counts;         // pass 0: row sizes
-    const uint64_t* gd_rp;    // pass 1: row offsets
-    uint32_t* gd_col;         // pass 1
-    uint8_t* gd_dist;         // pass 1
+    uint64_t* counts;         // row sizes (written in both modes)
+    int staged;               // 1: write at a reserved staging offset
+    unsigned long long* cursor;  // staged: next free staging entry
+    uint64_t cap;             // staged: staging capacity
+    uint64_t* row_off;        // staged: staging offset of each row
+    uint32_t* overflow;       // staged: set when a row did not fit
+    const uint64_t* gd_rp;    // direct: row offsets
+    uint32_t* out_col;        // staging or final column array
+    uint8_t* out_dist;        // staging or final distance array
 };
 
 __device__ __forceinline__ void bfs_append(uint32_t v, bool isnew, uint32_t* list, uint32_t* s_len) {
@@ -49,30 +60,31 @@ __device__ __forceinline__ void bfs_append(uint32_t v, bool isnew, uint32_t* lis
     if (isnew) list[base + __popc(ballot & lanemask_lt())] = v;
 }
 
-// Marks v visited; true for the one thread that marked it first.  In pass 1
-// the first bit set in a word also marks the word in the summary.
-template <bool FILL>
+// Marks v visited; true for the one thread that marked it first.  The first
+// bit set in a word also marks the word in the summary.
 __device__ __forceinline__ bool visit(uint32_t* bm, uint32_t* summ, uint32_t v) {
     const uint32_t w = v >> 5, bit = 1u << (v & 31);
     if (*(volatile uint32_t*)&bm[w] & bit) return false;
     const uint32_t old = atomicOr(&bm[w], bit);
     if (old & bit) return false;
-    if (FILL && old == 0) atomicOr(&summ[w >> 5], 1u << (w & 31));
+    if (old == 0) atomicOr(&summ[w >> 5], 1u << (w & 31));
     return true;
 }
 
-template <bool FILL>
+template <bool K2>
 __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint64_t s_off[BFS_THREADS];
     __shared__ uint64_t s_start[BFS_THREADS];
     __shared__ uint64_t s_wt[BFS_THREADS / 32];
     __shared__ uint32_t s_row, s_len;
+    __shared__ uint64_t s_base;
+    __shared__ int s_skip;
     uint32_t* bm = a.gbitmaps ? a.gbitmaps + (size_t)blockIdx.x * a.words : dsm;
     uint32_t* summ = a.gbitmaps ? dsm : dsm + a.words;
     uint32_t* list = a.lists + (size_t)blockIdx.x * a.n;
-    uint32_t* wl = FILL ? a.wlists + (size_t)blockIdx.x * a.words : nullptr;
-    uint8_t* dl = FILL ? a.dlev + (size_t)blockIdx.x * a.n : nullptr;
+    uint32_t* wl = a.wlists + (size_t)blockIdx.x * a.words;
+    uint8_t* dl = K2 ? nullptr : a.dlev + (size_t)blockIdx.x * a.n;
     for (uint32_t w = threadIdx.x; w < a.words; w += BFS_THREADS) bm[w] = 0;
     for (uint32_t w = threadIdx.x; w < a.swords; w += BFS_THREADS) summ[w] = 0;
     __syncthreads();
@@ -84,22 +96,20 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
         __syncthreads();
         const uint32_t row = s_row;
         if (row >= a.n) break;
-        if (threadIdx.x == 0) visit<FILL>(bm, summ, row);
+        if (threadIdx.x == 0) visit(bm, summ, row);
         __syncthreads();
+        const uint64_t ab = a.rp[row], ae = a.rp[row + 1];
         // level 1: the source's own adjacency
-        {
-            const uint64_t b = a.rp[row], e = a.rp[row + 1];
-            for (uint64_t x0 = b; x0 < e; x0 += BFS_THREADS) {
-                const uint64_t x = x0 + threadIdx.x;
-                uint32_t v = 0;
-                bool isnew = false;
-                if (x < e) {
-                    v = a.col[x];
-                    isnew = visit<FILL>(bm, summ, v);
-                    if (FILL && isnew) dl[v] = 1;
-                }
-                bfs_append(v, isnew, list, &s_len);
+        for (uint64_t x0 = ab; x0 < ae; x0 += BFS_THREADS) {
+            const uint64_t x = x0 + threadIdx.x;
+            uint32_t v = 0;
+            bool isnew = false;
+            if (x < ae) {
+                v = a.col[x];
+                isnew = visit(bm, summ, v);
+                if (!K2 && isnew) dl[v] = 1;
             }
+            bfs_append(v, isnew, list, &s_len);
         }
         __syncthreads();
         uint32_t lo = 0, hi = s_len;
@@ -131,8 +141,8 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
                             if (s_off[mid] <= x) lo2 = mid; else hi2 = mid;
                         }
                         v = a.col[s_start[lo2] + (x - s_off[lo2])];
-                        isnew = visit<FILL>(bm, summ, v);
-                        if (FILL && isnew) dl[v] = (uint8_t)d;
+                        isnew = visit(bm, summ, v);
+                        if (!K2 && isnew) dl[v] = (uint8_t)d;
                     }
                     bfs_append(v, isnew, list, &s_len);
                 }
@@ -143,55 +153,100 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
             __syncthreads();
         }
         const uint32_t total = s_len;
-        if (!FILL) {
-            if (threadIdx.x == 0) a.counts[row] = total;
-            for (uint32_t x = threadIdx.x; x < total; x += BFS_THREADS) bm[list[x] >> 5] = 0;
-            if (threadIdx.x == 0) bm[row >> 5] = 0;
-        } else {
-            if (threadIdx.x == 0) bm[row >> 5] &= ~(1u << (row & 31));  // the source is not its own neighbour
-            __syncthreads();
-            // touched words in increasing order (summary words split in equal ranges)
-            const uint32_t per = (a.swords + BFS_THREADS - 1) / BFS_THREADS;
-            const uint32_t s0 = threadIdx.x * per;
-            const uint32_t s1 = s0 + per < a.swords ? s0 + per : a.swords;
-            uint64_t mine = 0;
-            for (uint32_t s = s0; s < s1; ++s) mine += __popc(summ[s]);
-            uint64_t nw;
-            uint64_t pos = block_exclusive_scan<uint64_t, BFS_THREADS>(mine, s_wt, nw);
-            for (uint32_t s = s0; s < s1; ++s) {
-                uint32_t m = summ[s];
-                summ[s] = 0;
-                while (m) {
-                    const uint32_t b = __ffs(m) - 1;
-                    m &= m - 1;
-                    wl[pos++] = 32 * s + b;
+        if (threadIdx.x == 0) {
+            bm[row >> 5] &= ~(1u << (row & 31));  // the source is not its own neighbour
+            a.counts[row] = total;
+            uint64_t base = 0;
+            int skip = 0;
+            if (a.staged) {
+                base = atomicAdd(a.cursor, (unsigned long long)total);
+                if (base + total > a.cap) {
+                    skip = 1;
+                    atomicExch(a.overflow, 1u);
                 }
+                a.row_off[row] = base;
+            } else {
+                base = a.gd_rp[row];
             }
-            __syncthreads();
-            // every touched word's bits, in order, with their hop distance
-            uint64_t out = a.gd_rp[row];
-            for (uint64_t c = 0; c < nw; c += BFS_THREADS) {
-                const uint64_t idx = c + threadIdx.x;
-                uint32_t wi = 0, w = 0;
-                if (idx < nw) {
-                    wi = wl[idx];
-                    w = bm[wi];
-                    bm[wi] = 0;
-                }
-                uint64_t tot;
-                uint64_t o = out + block_exclusive_scan<uint64_t, BFS_THREADS>((uint64_t)__popc(w), s_wt, tot);
+            s_base = base;
+            s_skip = skip;
+        }
+        __syncthreads();
+        // touched words in increasing order (summary words split in equal ranges)
+        const uint32_t per = (a.swords + BFS_THREADS - 1) / BFS_THREADS;
+        const uint32_t s0 = threadIdx.x * per;
+        const uint32_t s1 = s0 + per < a.swords ? s0 + per : a.swords;
+        uint64_t mine = 0;
+        for (uint32_t s = s0; s < s1; ++s) mine += __popc(summ[s]);
+        uint64_t nw;
+        uint64_t pos = block_exclusive_scan<uint64_t, BFS_THREADS>(mine, s_wt, nw);
+        for (uint32_t s = s0; s < s1; ++s) {
+            uint32_t m = summ[s];
+            summ[s] = 0;
+            while (m) {
+                const uint32_t b = __ffs(m) - 1;
+                m &= m - 1;
+                wl[pos++] = 32 * s + b;
+            }
+        }
+        __syncthreads();
+        const bool emit = !s_skip;
+        // every touched word's bits, in order
+        uint64_t out = s_base;
+        for (uint64_t c = 0; c < nw; c += BFS_THREADS) {
+            const uint64_t idx = c + threadIdx.x;
+            uint32_t wi = 0, w = 0;
+            if (idx < nw) {
+                wi = wl[idx];
+                w = bm[wi];
+                bm[wi] = 0;
+            }
+            uint64_t tot;
+            uint64_t o = out + block_exclusive_scan<uint64_t, BFS_THREADS>((uint64_t)__popc(w), s_wt, tot);
+            if (emit) {
                 while (w) {
                     const uint32_t b = __ffs(w) - 1;
                     w &= w - 1;
                     const uint32_t v = 32 * wi + b;
-                    a.gd_col[o] = v;
-                    a.gd_dist[o] = dl[v];
+                    a.out_col[o] = v;
+                    a.out_dist[o] = K2 ? (uint8_t)2 : dl[v];
                     ++o;
                 }
-                out += tot;
+            }
+            out += tot;
+        }
+        if (K2 && emit) {
+            __syncthreads();
+            // distance 1: the source's adjacency, located in the emitted (sorted)
+            // row by binary search
+            const uint32_t* rowc = a.out_col + s_base;
+            for (uint64_t x = ab + threadIdx.x; x < ae; x += BFS_THREADS) {
+                const uint32_t v = a.col[x];
+                uint32_t lo3 = 0, hi3 = total;
+                while (lo3 < hi3) {
+                    const uint32_t mid = (lo3 + hi3) >> 1;
+                    if (rowc[mid] < v) lo3 = mid + 1; else hi3 = mid;
+                }
+                a.out_dist[s_base + lo3] = 1;
             }
         }
         __syncthreads();
+    }
+}
+
+// Moves staged rows to their final place (one warp per row).
+__global__ void k_unstage(const uint64_t* __restrict__ row_off, const uint64_t* __restrict__ rp, uint32_t n,
+                          const uint32_t* __restrict__ scol, const uint8_t* __restrict__ sdist,
+                          uint32_t* __restrict__ col, uint8_t* __restrict__ dist) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = warp0; r < n; r += nwarps) {
+        const uint64_t src = row_off[r], dst = rp[r], cnt = rp[r + 1] - rp[r];
+        for (uint64_t e = lane; e < cnt; e += 32) {
+            col[dst + e] = scol[src + e];
+            dist[dst + e] = sdist[src + e];
+        }
     }
 }
 
@@ -199,6 +254,14 @@ __global__ void k_fill_u8(uint8_t* p, uint64_t n, uint8_t v) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x)
         p[e] = v;
 }
+
+struct DegSq {
+    const uint64_t* rp;
+    __device__ __forceinline__ uint64_t operator()(size_t v) const {
+        const uint64_t d = rp[v + 1] - rp[v];
+        return d * d;
+    }
+};
 
 static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat* d) {
     const uint32_t n = g->n;
@@ -213,46 +276,82 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         DRG_LAUNCH(ctx, k_fill_u8, grid_for(d->nnz, 256, 65536), 256, 0, d->dist, d->nnz, (uint8_t)1);
         return;
     }
+    const bool k2 = k == 2;
+    auto kern = k2 ? k_bfs<true> : k_bfs<false>;
     const uint32_t words = (n + 31) / 32;
     const uint32_t swords = (words + 31) / 32;
     const size_t bm_bytes = (size_t)words * 4, sm_bytes = (size_t)swords * 4;
     const bool smem_bm = bm_bytes + sm_bytes + 16384 <= (size_t)ctx->max_smem_optin;
     DRG_CHECK(sm_bytes + 16384 <= (size_t)ctx->max_smem_optin, DRG_EUNSUPPORTED, "graph too large for the BFS");
     const size_t dyn = (smem_bm ? bm_bytes : 0) + sm_bytes;
-    DRG_CUDA(cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    DRG_CUDA(cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    DRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
-    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs<true>, BFS_THREADS, dyn));
+    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BFS_THREADS, dyn));
     if (per_sm < 1) per_sm = 1;
     uint32_t blocks = (uint32_t)ctx->num_sms * (uint32_t)per_sm;
     if (blocks > n) blocks = n;
-    // per-block discovered lists, touched-word lists, hop distances (and
-    // bitmaps when they live in global memory)
+    // per-block discovered lists, touched words, word offsets / hop distances
+    // (and bitmaps when they live in global memory)
     DBuf<uint32_t> lists(ctx, (size_t)blocks * n);
     DBuf<uint32_t> wlists(ctx, (size_t)blocks * words);
-    DBuf<uint8_t> dlev(ctx, (size_t)blocks * n);
+    DBuf<uint8_t> dlev(ctx, k2 ? 1 : (size_t)blocks * n);
     DBuf<uint32_t> gbm(ctx, smem_bm ? 1 : (size_t)blocks * words);
-    DBuf<uint32_t> counter(ctx, 1);
-    DBuf<uint64_t> counts(ctx, (size_t)n);
+    DBuf<uint32_t> counter(ctx, 1), overflow(ctx, 1);
+    DBuf<uint64_t> counts(ctx, (size_t)n), row_off(ctx, (size_t)n);
+    DBuf<unsigned long long> cursor(ctx, 1);
+    // staging capacity: for k = 2 a row has at most deg(i) + sum over its
+    // neighbours of (deg(u) - 1) entries, so the total is at most sum deg^2;
+    // for k > 2 whatever a quarter of the free memory holds
+    uint64_t cap;
+    if (k2) {
+        DBuf<uint64_t> s2(ctx, 1);
+        DBuf<uint64_t> tmp(ctx, n);
+        scan<uint64_t>(ctx, DegSq{g->rp}, n, tmp.p, false, s2.p);
+        cap = read1(ctx, s2.p);
+    } else {
+        size_t fr = 0, tt = 0;
+        DRG_CUDA(cudaMemGetInfo(&fr, &tt));
+        cap = fr / 4 / 5;
+    }
+    if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
+    size_t fr = 0, tt = 0;
+    DRG_CUDA(cudaMemGetInfo(&fr, &tt));
+    if (cap * 5 > fr / 2) cap = fr / 2 / 5;  // leave room for the final arrays
+    DBuf<uint32_t> scol(ctx, cap ? cap : 1);
+    DBuf<uint8_t> sdist(ctx, cap ? cap : 1);
     BfsArgs a{};
     a.rp = g->rp; a.col = g->col; a.n = n; a.k = k; a.words = words; a.swords = swords;
     a.gbitmaps = smem_bm ? nullptr : gbm.p;
     a.lists = lists.p; a.wlists = wlists.p; a.dlev = dlev.p;
     a.next_row = counter.p; a.counts = counts.p;
+    a.staged = 1; a.cursor = cursor.p; a.cap = cap; a.row_off = row_off.p; a.overflow = overflow.p;
+    a.out_col = scol.p; a.out_dist = sdist.p;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
-    DRG_LAUNCH(ctx, k_bfs<false>, blocks, BFS_THREADS, dyn, a);
+    DRG_CUDA(cudaMemsetAsync(overflow.p, 0, 4, ctx->stream));
+    DRG_CUDA(cudaMemsetAsync(cursor.p, 0, 8, ctx->stream));
+    DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
     DBuf<uint64_t> tot(ctx, 1);
     scan<uint64_t>(ctx, LoadArr<uint64_t>{counts.p}, n, d->rp, false, tot.p);
     d2d(ctx, d->rp + n, tot.p, 1);
     d->nnz = read1(ctx, tot.p);
     DRG_CHECK(d->nnz < (1ull << 32), DRG_EUNSUPPORTED, "distance matrix has 2^32 entries or more");
+    const bool overflowed = read1(ctx, overflow.p) != 0;
     d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (d->nnz ? d->nnz : 1)));
     d->dist = static_cast<uint8_t*>(dalloc(ctx, d->nnz ? d->nnz : 1));
+    if (!overflowed) {
+        DRG_LAUNCH(ctx, k_unstage, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, row_off.p,
+                   d->rp, n, scol.p, sdist.p, d->col, d->dist);
+        return;
+    }
+    // the staging area was too small: traverse again, writing at the final offsets
+    scol.reset();
+    sdist.reset();
+    a.staged = 0;
     a.gd_rp = d->rp;
-    a.gd_col = d->col;
-    a.gd_dist = d->dist;
+    a.out_col = d->col;
+    a.out_dist = d->dist;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
-    DRG_LAUNCH(ctx, k_bfs<true>, blocks, BFS_THREADS, dyn, a);
+    DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
 }
 
 // ------------------------------------------------------------------ similarity
@@ -268,22 +367,22 @@ __global__ void k_row_Z(const uint64_t* __restrict__ rp, const uint8_t* __restri
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t i = warp0; i < n; i += nwarps) {
-        uint32_t c[16];
+        // class counts by warp ballots: every lane ends with the same totals
+        uint32_t c[15];
 #pragma unroll
-        for (int d = 0; d < 16; ++d) c[d] = 0;
-        for (uint64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
-            const uint32_t dd = dist[e];
+        for (int d = 0; d < 15; ++d) c[d] = 0;
+        const uint64_t e0 = rp[i], e1 = rp[i + 1];
+        for (uint64_t b = e0; b < e1; b += 32) {
+            const uint64_t e = b + lane;
+            const uint32_t dd = e < e1 ? dist[e] : 0u;
 #pragma unroll
-            for (int d = 0; d < 16; ++d) c[d] += (dd == (uint32_t)(d + 1));
+            for (int d = 0; d < 15; ++d)
+                if ((uint32_t)d < k) c[d] += __popc(__ballot_sync(0xFFFFFFFFu, dd == (uint32_t)(d + 1)));
         }
         float z = 0.f;
 #pragma unroll
-        for (int d = 0; d < 16; ++d) {
-            uint32_t v = c[d];
-#pragma unroll
-            for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
-            if ((uint32_t)d < k) z = __fadd_rn(z, __fmul_rn(__uint2float_rn(v), gs.g[d]));
-        }
+        for (int d = 0; d < 15; ++d)
+            if ((uint32_t)d < k) z = __fadd_rn(z, __fmul_rn(__uint2float_rn(c[d]), gs.g[d]));
         if (lane == 0) Z[i] = z;
     }
 }
@@ -553,10 +652,15 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
     try {
         DRG_CHECK(g->nnz > 0, DRG_EEMPTY, "graph has no edges");
         ProfSpan span(ctx, DRG_PROF_DMAT, 0);
-        build_korder(ctx, g, k, d);
+        {
+            ProfSpan sb(ctx, DRG_PROF_BFS, 0);
+            build_korder(ctx, g, k, d);
+            sb.units = d->nnz;
+        }
         span.units = d->nnz;
         const uint32_t n = d->n;
         const uint64_t nnz = d->nnz;
+        ProfSpan ss(ctx, DRG_PROF_SIM, nnz);
         Gauss gs{};
         for (uint32_t x = 1; x <= k; ++x)
             gs.g[x - 1] = (float)std::exp(-(double)(x * x) / (2.0 * (double)sigma * (double)sigma));
@@ -574,6 +678,7 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
         const uint64_t mx = read1(ctx, rmax.p);
         const int bits = bitlen(mx);
         d->shift = bits > 32 ? (uint32_t)(bits - 32) : 0u;
+        ss.reopen(DRG_PROF_ALIAS, nnz + n);
         // edge table over the entries (positive samples)
         {
             DBuf<uint32_t> th(ctx, nnz);

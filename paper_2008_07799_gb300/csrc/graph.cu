@@ -95,6 +95,7 @@ drg_graph* graph_from_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
     drg_graph* g = new drg_graph();
     g->ctx = ctx;
     try {
+        ProfSpan span(ctx, DRG_PROF_GRAPH, m);
         DBuf<uint32_t> ds, dd;
         const uint32_t* s = src;
         const uint32_t* d = dst;
