@@ -41,7 +41,58 @@ WORKLOADS = {
                         "500 epochs per level, b=1"),
     "grid32": dict(graph="grid32", k=3, M=5, epochs=500, b=3.0, stop_nodes=1000, multilevel=0,
                    desc="32x32 grid, single level, k=3, M=5, 500 epochs, b=3"),
+    "batch256": dict(graph="batch256", k=2, M=5, epochs=300, b=2.0, stop_nodes=1000,
+                     desc="256 graphs (grids b=3, random binary trees and Barabasi-Albert m=2 b=2), node counts "
+                          "log-uniform in [1k, 50k], seed 3; multilevel, k=2, M=5, 300 epochs, one batched launch "
+                          "per sub-step across graphs"),
 }
+
+
+class Job:
+    """One step's input and the two ways to run it: device-resident edges and
+    positions (`step`), or host buffers with the copies inside (`e2e`)."""
+
+    def __init__(self, drg, ctx, wl, p, np, torch):
+        import graphgen as gg
+        self.drg, self.ctx, self.p, self.np, self.torch = drg, ctx, p, np, torch
+        if wl["graph"] == "batch256":
+            items = gg.batch_mix(256, 1000, 50000, 3)
+            self.graphs = [g for _, g in items]
+            self.b = [3.0 if kind == "grid" else 2.0 for kind, _ in items]
+        else:
+            self.graphs = [gg.workload(wl["graph"])]
+            self.b = None
+        self.n = sum(g[0] for g in self.graphs)
+        self.m = sum(len(g[1]) for g in self.graphs)
+        self.dev = [(g[0], torch.from_numpy(g[1].view(np.int32)).cuda(), torch.from_numpy(g[2].view(np.int32)).cuda())
+                    for g in self.graphs]
+        self.pos = [torch.zeros(2 * g[0], dtype=torch.float32, device="cuda") for g in self.graphs]
+        self.host = None
+
+    def _run(self, edges, pos):
+        drg, ctx = self.drg, self.ctx
+        if self.b is None:
+            n, s, d = edges[0]
+            drg.layout_edges(ctx, n, s, d, self.p, pos[0])
+        else:
+            gs = [drg.graph_from_edges(ctx, n, s, d) for n, s, d in edges]
+            dpos = pos if pos[0].is_cuda else [self.torch.zeros(x.shape, device="cuda") for x in pos]
+            drg.layout_batch(ctx, gs, self.p, dpos, b=self.b)
+            if dpos is not pos:
+                for x, y in zip(pos, dpos):
+                    x.copy_(y)
+
+    def step(self):
+        self._run(self.dev, self.pos)
+
+    def e2e(self):
+        np, torch = self.np, self.torch
+        if self.host is None:
+            self.host = ([(g[0], torch.from_numpy(g[1].view(np.int32)).pin_memory(),
+                           torch.from_numpy(g[2].view(np.int32)).pin_memory()) for g in self.graphs],
+                         [torch.zeros(2 * g[0], dtype=torch.float32).pin_memory() for g in self.graphs])
+        self._run(*self.host)
+        return self.host[1]
 
 ALGO_BYTES_NOTE = ("per sample: edge record 20 B + M node records 8 B + (2+M) position gathers "
                    "(8 B FP32; negatives 4 B with half copies) + (2+M) 8-B atomic adds; "
@@ -152,6 +203,9 @@ def oracle_sample(wl, budget_s):
     if wl["graph"] == "dcsbm1m":
         n, s, d = gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2)
         sample = "DC-SBM 20,000 nodes (same generator parameters as the 1M workload), k=2"
+    elif wl["graph"] == "batch256":
+        n, s, d = gg.barabasi_albert(20_000, 2, 3)
+        sample = "one Barabasi-Albert 20,000-node m=2 member of the batch family, k=2"
     elif wl["graph"] == "ba100k":
         n, s, d = gg.barabasi_albert(100_000, 3, 1)
         sample = "Barabasi-Albert 100,000 nodes m=3 (the workload graph), k=3"
@@ -246,18 +300,13 @@ def main():
     if args.single_level:
         wl["multilevel"] = 0
         wl["desc"] += " (single level)"
-    n, src, dst = gg.workload(wl["graph"])
-    m = len(src)
     stream = torch.cuda.current_stream()
     ctx = drg.Context(local, stream.cuda_stream)
     p = make_params(drg, wl, args, gid=rank)
-    dsrc = torch.from_numpy(src.view(np.int32)).cuda()
-    ddst = torch.from_numpy(dst.view(np.int32)).cuda()
-    pos = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    job = Job(drg, ctx, wl, p, np, torch)
+    n, m = job.n, job.m
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 1 GiB > L2
-
-    def step():
-        drg.layout_edges(ctx, n, dsrc, ddst, p, pos)
+    step = job.step
 
     if args.once:
         step()
@@ -280,7 +329,7 @@ def main():
     hi_ms, _, levels = ctx.profile_read(drg.PROF_HIER)
     sub_ms = {name: ctx.profile_read(w)[0] for name, w in
               (("graph", drg.PROF_GRAPH), ("bfs", drg.PROF_BFS), ("similarity", drg.PROF_SIM),
-               ("alias_tables", drg.PROF_ALIAS))}
+               ("alias_tables", drg.PROF_ALIAS), ("host_alloc", drg.PROF_ALLOC))}
     ctx.profile(False)
 
     # timed region
@@ -313,20 +362,18 @@ def main():
     value = samples_per_step * world / (ms / 1000.0)
 
     # end to end through the public API from pinned host buffers
-    hsrc = torch.from_numpy(src.view(np.int32)).pin_memory()
-    hdst = torch.from_numpy(dst.view(np.int32)).pin_memory()
-    hpos = torch.zeros(2 * n, dtype=torch.float32).pin_memory()
     e2e_times = []
+    hpos = None
     for _ in range(max(1, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        drg.layout_edges(ctx, n, hsrc, hdst, p, hpos)  # host pointers: copies inside the call
+        hpos = job.e2e()  # host pointers: the copies happen inside the calls
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_times) / len(e2e_times)
     e2e_value = samples_per_step * world / e2e_s
-    assert np.isfinite(hpos.numpy()).all()
+    assert all(np.isfinite(x.numpy()).all() for x in hpos)
 
     if rank != 0:
         return

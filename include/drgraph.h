@@ -246,12 +246,16 @@ drg_status drg_layout(drg_ctx* ctx, const drg_graph* g, const drg_params* p, flo
 drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                             int edges_on_device, const drg_params* p, float* pos, int pos_on_device);
 
-/* Lay out `count` independent graphs as one job: graph g uses p with gid = g,
- * so its result equals drg_layout of that graph alone with gid = g.  Levels
- * of all graphs that share a level index run in one launch per (sub-)step.
- * pos[g] are device float[2 n_g].  Synchronises. */
+/* Lay out `count` independent graphs as one job.  Graph g uses p with
+ * gid = g and shape b[g] (b may be NULL: p->b for all), i.e. its own random
+ * streams, distance matrix, tables and hierarchy; in synchronous mode its
+ * result equals drg_layout of that graph alone with those parameters up to
+ * the order of FP32 atomic additions.  Levels run in rounds aligned at every
+ * graph's coarsest level; within a round, sub-step run c of every active
+ * graph is one kernel launch, and all epochs of the round are one CUDA graph
+ * launch.  pos[g] are device float[2 n_g].  Synchronises. */
 drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
-                            float* const* pos);
+                            const float* b, float* const* pos);
 
 /* ---------------------------------------------------------------- profiling */
 /* Per-kernel timing with CUDA events recorded on the context stream around
@@ -265,7 +269,8 @@ drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const
 #define DRG_PROF_BFS 5     /* k-order BFS of the distance matrix; units = entries */
 #define DRG_PROF_SIM 6     /* similarity and quantised weights; units = entries */
 #define DRG_PROF_ALIAS 7   /* both alias tables and the edge records; units = entries + nodes */
-#define DRG_PROF_COUNT 8
+#define DRG_PROF_ALLOC 8   /* host time inside device allocation calls; launches = calls, units = bytes */
+#define DRG_PROF_COUNT 9
 drg_status drg_profile_enable(drg_ctx* ctx, int on);
 drg_status drg_profile_reset(drg_ctx* ctx);
 /* Total milliseconds, number of timed launches and units of one family.

@@ -39,7 +39,7 @@ EXPORTS = [
     "drg_layout_level_noalloc",
 ]
 
-PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS = range(8)
+PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
 
 
 class DrgError(RuntimeError):
@@ -119,7 +119,7 @@ def lib():
         "drg_interpolate": (st, [VP, VP, C.c_uint32, VP, VP]),
         "drg_layout": (st, [VP, VP, PP, VP]),
         "drg_layout_edges": (st, [VP, C.c_uint32, C.c_uint64, VP, VP, C.c_int, PP, VP, C.c_int]),
-        "drg_layout_batch": (st, [VP, C.c_uint32, VP, PP, VP]),
+        "drg_layout_batch": (st, [VP, C.c_uint32, VP, PP, VP, VP]),
         "drg_sample_draws": (st, [VP, VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, PP, VP, VP, VP]),
         "drg_profile_enable": (st, [VP, C.c_int]),
         "drg_profile_reset": (st, [VP]),
@@ -372,11 +372,13 @@ def layout_edges(ctx: Context, n, src, dst, p: Params, pos):
                                      _ptr(pos), int(_is_device(pos))))
 
 
-def layout_batch(ctx: Context, graphs, p: Params, positions):
+def layout_batch(ctx: Context, graphs, p: Params, positions, b=None):
+    """b: optional per-graph kernel shapes (sequence of floats)."""
     n = len(graphs)
     garr = (VP * max(n, 1))(*[g.h for g in graphs])
     parr = (VP * max(n, 1))(*[_ptr(x) for x in positions])
-    ctx.check(lib().drg_layout_batch(ctx.h, n, garr, C.byref(p), parr))
+    barr = None if b is None else np.ascontiguousarray(b, np.float32)
+    ctx.check(lib().drg_layout_batch(ctx.h, n, garr, C.byref(p), _ptr(barr), parr))
 
 
 def sample_draws(ctx: Context, d: DistanceMatrix, level, t, s_begin, s_end, p: Params, out_i, out_j, out_neg):

@@ -3,6 +3,7 @@
 // turns any failure into a status code plus the context's error message.
 #include "prims.cuh"
 
+#include <chrono>
 #include <cstdlib>
 #include <new>
 
@@ -10,7 +11,14 @@ namespace drg {
 
 void* dalloc(drg_ctx* ctx, size_t bytes) {
     void* p = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 1, ctx->stream);
+    if (ctx->prof) {
+        ctx->prof_ms[DRG_PROF_ALLOC] +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        ctx->prof_launches[DRG_PROF_ALLOC] += 1;
+        ctx->prof_units[DRG_PROF_ALLOC] += bytes;
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         fail(e == cudaErrorMemoryAllocation ? DRG_ENOMEM : DRG_ECUDA,
@@ -442,10 +450,10 @@ drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
 }
 
 drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
-                            float* const* pos) {
+                            const float* b, float* const* pos) {
     if (!ctx || !p) return DRG_EINVAL;
     API_TRY
-    drg::layout_batch(ctx, count, graphs, *p, pos);
+    drg::layout_batch(ctx, count, graphs, *p, b, pos);
     API_CATCH(ctx)
 }
 

@@ -279,7 +279,7 @@ void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, ui
 void interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos, float* fine_pos);
 void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* pos);
 void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
-                  float* const* pos);
+                  const float* b_per_graph, float* const* pos);
 void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, uint32_t s_begin, uint32_t s_end,
                   const drg_params& p, uint32_t* oi, uint32_t* oj, uint32_t* oneg);
 

@@ -155,10 +155,7 @@ __device__ __forceinline__ void push(const EpochArgs& a, uint32_t v, float fx, f
 // MT > 0: compile-time number of negatives (their loads are all issued before
 // any is used); MT == 0: runtime M, negatives handled one after another.
 template <int MT, bool SYNC, int PREC>
-__global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
-    grid_dependency_trigger();
-    if (a.late) grid_dependency_wait();
-    const uint64_t s = a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void epoch_sample(EpochArgs& a, const uint64_t s) {
     const bool active = s < a.s_end;
     {
         Words W((uint32_t)s, __ldcg(&a.st->t), a.tag, a.key);
@@ -221,6 +218,94 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
             push<SYNC>(a, ic, -fa.x, -fa.y);
         }
     }
+}
+
+template <int MT, bool SYNC, int PREC>
+__global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
+    grid_dependency_trigger();
+    if (a.late) grid_dependency_wait();
+    epoch_sample<MT, SYNC, PREC>(a, a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x);
+}
+
+// ------------------------------------------------------------------ batches of graphs
+// Sub-step c of the current level of many graphs in one launch.  Blocks are
+// assigned to jobs (graph, level) by a prefix sum of each job's block count;
+// each job's run c covers its own samples [c chunk, min(n_l, (c+1) chunk)).
+struct BatchJob {
+    const EdgeRec* etab;
+    uint64_t nnz;
+    const uint2* vtab;
+    const uint32_t* anc;
+    float2* Y;
+    float2* G;
+    void* Yh;
+    uint32_t n0, nl, chunk, tag;
+    float gamma, b, twob;
+    int bint;
+};
+
+struct BatchArgs {
+    EpochArgs common;             // st, late, M, clip, key
+    const BatchJob* jobs;
+    const uint32_t* block_prefix; // [njobs + 1] sample blocks per job, prefix-summed
+    const uint32_t* node_prefix;  // [njobs + 1] node blocks per job, prefix-summed
+    uint32_t njobs;
+};
+
+__device__ __forceinline__ uint32_t find_job(const uint32_t* prefix, uint32_t njobs, uint32_t blk) {
+    uint32_t lo = 0, hi = njobs;  // last job whose prefix is <= blk
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= blk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int MT, bool SYNC, int PREC>
+__global__ void __launch_bounds__(256) k_epoch_batch(BatchArgs ba, uint32_t c) {
+    grid_dependency_trigger();
+    if (ba.common.late) grid_dependency_wait();
+    const uint32_t jb = find_job(ba.block_prefix, ba.njobs, blockIdx.x);
+    const BatchJob J = ba.jobs[jb];
+    EpochArgs a = ba.common;
+    a.etab = J.etab;
+    a.nnz = J.nnz;
+    a.vtab = J.vtab;
+    a.n0 = J.n0;
+    a.anc = J.anc;
+    a.Y = J.Y;
+    a.G = J.G;
+    a.Yh = J.Yh;
+    a.tag = J.tag;
+    a.gamma = J.gamma;
+    a.b = J.b;
+    a.twob = J.twob;
+    a.bint = J.bint;
+    a.s_begin = (uint64_t)c * J.chunk;
+    a.s_end = a.s_begin + J.chunk < J.nl ? a.s_begin + J.chunk : J.nl;
+    const uint64_t s = a.s_begin + (uint64_t)(blockIdx.x - ba.block_prefix[jb]) * blockDim.x + threadIdx.x;
+    epoch_sample<MT, SYNC, PREC>(a, s);
+}
+
+template <int PREC>
+__global__ void k_apply_batch(BatchArgs ba) {
+    grid_dependency_trigger();
+    grid_dependency_wait();
+    const uint32_t jb = find_job(ba.node_prefix, ba.njobs, blockIdx.x);
+    const BatchJob J = ba.jobs[jb];
+    const float lr = __ldcg(&ba.common.st->lr);
+    const uint64_t v = (uint64_t)(blockIdx.x - ba.node_prefix[jb]) * blockDim.x + threadIdx.x;
+    if (v >= J.nl) return;
+    float2 y = J.Y[v];
+    if (J.G) {
+        const float2 g = J.G[v];
+        y.x += lr * g.x;
+        y.y += lr * g.y;
+        J.Y[v] = y;
+        J.G[v] = make_float2(0.f, 0.f);
+    }
+    if constexpr (PREC == DRG_PREC_FP16) reinterpret_cast<__half2*>(J.Yh)[v] = __float22half2_rn(y);
+    if constexpr (PREC == DRG_PREC_BF16) reinterpret_cast<__nv_bfloat162*>(J.Yh)[v] = __float22bfloat162_rn(y);
 }
 
 // Synchronous sub-step end: Y += lr G, G = 0 (and the half copy refreshed).
@@ -359,6 +444,58 @@ static EpochKernel pick_epoch(uint32_t M, bool sync, int prec) {
 // one thread per sample
 static uint32_t epoch_grid(drg_ctx*, uint64_t count) { return (uint32_t)((count + 255) / 256); }
 
+// One CUDA graph for a level run: a WHILE node whose body is one epoch --
+// `body` captures its launches (sub-step runs chained by programmatic
+// dependent launch) -- closed by k_advance, which moves the epoch state on and
+// sets the loop condition.  One graph launch then runs every epoch.
+template <typename Body>
+static void run_epoch_loop_graph(drg_ctx* ctx, EpochState* st, Body&& body, uint64_t launches_run,
+                                 uint64_t prof_units, uint64_t prof_launches) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const uint64_t launches_before = ctx->launches;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    };
+    try {
+        DRG_CUDA(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle loop;
+        DRG_CUDA(cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = loop;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        DRG_CUDA(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &np));
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        DRG_CUDA(cudaStreamBeginCaptureToGraph(ctx->stream, bodyg, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        try {
+            body();
+            DRG_LAUNCH(ctx, k_advance, 1, 1, 0, st, loop);
+        } catch (...) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(ctx->stream, &dummy);
+            (void)cudaGetLastError();
+            throw;
+        }
+        DRG_CUDA(cudaStreamEndCapture(ctx->stream, &bodyg));
+        DRG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        ctx->launches = launches_before + launches_run;  // count what runs, not what was captured
+        {
+            ProfSpan span(ctx, DRG_PROF_EPOCH, prof_units, prof_launches);
+            DRG_CUDA(cudaGraphLaunch(exec, ctx->stream));
+        }
+        sync(ctx);
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
 void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                   const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end) {
     check_params(p);
@@ -435,51 +572,8 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
         sync(ctx);
         return;
     }
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    const uint64_t launches_before = ctx->launches;
-    auto cleanup = [&]() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-    };
-    try {
-        DRG_CUDA(cudaGraphCreate(&graph, 0));
-        cudaGraphConditionalHandle loop;
-        DRG_CUDA(cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault));
-        cudaGraphNodeParams np = {};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = loop;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        cudaGraphNode_t wnode;
-        DRG_CUDA(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &np));
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        DRG_CUDA(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
-                                               cudaStreamCaptureModeThreadLocal));
-        try {
-            epoch_body();
-            DRG_LAUNCH(ctx, k_advance, 1, 1, 0, st.p, loop);
-        } catch (...) {
-            cudaGraph_t dummy = nullptr;
-            cudaStreamEndCapture(ctx->stream, &dummy);
-            (void)cudaGetLastError();
-            throw;
-        }
-        DRG_CUDA(cudaStreamEndCapture(ctx->stream, &body));
-        DRG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-        // count what runs, not what was captured
-        const uint64_t per_epoch = (uint64_t)nchunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
-        ctx->launches = launches_before + epochs * per_epoch;
-        {
-            ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)nl * epochs, epochs * nchunks);
-            DRG_CUDA(cudaGraphLaunch(exec, ctx->stream));
-        }
-        sync(ctx);
-    } catch (...) {
-        cleanup();
-        throw;
-    }
-    cleanup();
+    const uint64_t per_epoch = (uint64_t)nchunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
+    run_epoch_loop_graph(ctx, st.p, epoch_body, epochs * per_epoch, (uint64_t)nl * epochs, epochs * nchunks);
 }
 
 void init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params& p, float* pos) {
@@ -551,15 +645,190 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
     dmat_free(d);
 }
 
+typedef void (*EpochBatchKernel)(BatchArgs, uint32_t);
+
+static EpochBatchKernel pick_epoch_batch(uint32_t M, bool sync, int prec) {
+    static const EpochBatchKernel tab[2][2][3] = {
+        {{k_epoch_batch<0, false, 0>, k_epoch_batch<0, false, 1>, k_epoch_batch<0, false, 2>},
+         {k_epoch_batch<0, true, 0>, k_epoch_batch<0, true, 1>, k_epoch_batch<0, true, 2>}},
+        {{k_epoch_batch<5, false, 0>, k_epoch_batch<5, false, 1>, k_epoch_batch<5, false, 2>},
+         {k_epoch_batch<5, true, 0>, k_epoch_batch<5, true, 1>, k_epoch_batch<5, true, 2>}},
+    };
+    return tab[M == 5 ? 1 : 0][sync ? 1 : 0][prec];
+}
+
+static void launch_apply_batch(drg_ctx* ctx, int prec, uint32_t grid, const BatchArgs& ba) {
+    if (prec == 0) launch_pdl(ctx, "k_apply_batch", k_apply_batch<0>, grid, 256, 0, ba);
+    else if (prec == 1) launch_pdl(ctx, "k_apply_batch", k_apply_batch<1>, grid, 256, 0, ba);
+    else launch_pdl(ctx, "k_apply_batch", k_apply_batch<2>, grid, 256, 0, ba);
+}
+
+// Many independent graphs as one job.  Every graph gets its own distance
+// matrix, tables and hierarchy (graph id g in all random streams).  Levels
+// run in rounds aligned at each graph's coarsest level: in round r graph g
+// lays out its level L_g - r.  A round is one CUDA graph: a WHILE loop over
+// the epochs whose body launches, for each sub-step run c, one batched
+// k_epoch over all active graphs (and the batched apply in synchronous mode).
 void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
-                  float* const* pos) {
+                  const float* b_per_graph, float* const* pos) {
     check_params(p);
     DRG_CHECK(count == 0 || (graphs && pos), DRG_EINVAL, "null argument");
-    for (uint32_t gidx = 0; gidx < count; ++gidx) {
-        drg_params q = p;
-        q.gid = gidx;
-        layout_full(ctx, graphs[gidx], q, pos[gidx]);
+    for (uint32_t g = 0; g < count; ++g) {
+        DRG_CHECK(graphs[g] && pos[g], DRG_EINVAL, "null graph or position buffer");
+        DRG_CHECK(!b_per_graph || b_per_graph[g] > 0.f, DRG_EINVAL, "b must be positive");
     }
+    if (count == 0) return;
+    struct GS {
+        drg_dmat* d = nullptr;
+        drg_hier* h = nullptr;
+        uint32_t L = 0;
+        DBuf<float2> buf;
+        float2* cur = nullptr;
+        DBuf<float2> G;
+        DBuf<uint32_t> Yh;
+    };
+    std::vector<GS> gs(count);
+    auto free_all = [&]() {
+        for (auto& s : gs) {
+            hier_free(s.h);
+            dmat_free(s.d);
+            s.h = nullptr;
+            s.d = nullptr;
+        }
+    };
+    try {
+        const bool sync_mode = p.mode == DRG_MODE_SYNC;
+        const int prec = p.precision;
+        uint32_t Lmax = 0;
+        for (uint32_t g = 0; g < count; ++g) {
+            drg_params q = p;
+            q.gid = g;
+            gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma);
+            gs[g].h = build_hierarchy(ctx, graphs[g], q);
+            gs[g].L = (uint32_t)gs[g].h->g.size() - 1;
+            const uint32_t nL = gs[g].h->g[gs[g].L]->n;
+            if (gs[g].L > 0) {
+                gs[g].buf = DBuf<float2>(ctx, nL);
+                gs[g].cur = gs[g].buf.p;
+            } else {
+                gs[g].cur = reinterpret_cast<float2*>(pos[g]);
+            }
+            init_positions(ctx, nL, gs[g].L, q, reinterpret_cast<float*>(gs[g].cur));
+            Lmax = gs[g].L > Lmax ? gs[g].L : Lmax;
+        }
+        std::vector<float> lr_host(p.epochs);
+        for (uint32_t t = 0; t < p.epochs; ++t)
+            lr_host[t] = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
+        DBuf<float> lr_tab(ctx, p.epochs);
+        h2d(ctx, lr_tab.p, lr_host.data(), p.epochs);
+        DBuf<EpochState> st(ctx, 1);
+        const EpochState st_host{0u, p.epochs, lr_host[0], 0u, lr_tab.p};
+        const EpochBatchKernel ek = pick_epoch_batch(p.M, sync_mode, prec);
+        const EpochArgs proto = epoch_args(gs[0].d, nullptr, nullptr, p, p.gamma, 0);
+        for (uint32_t r = 0; r <= Lmax; ++r) {
+            std::vector<BatchJob> jobs;
+            std::vector<uint32_t> bpre(1, 0), npre(1, 0), owner;
+            uint64_t samples = 0;
+            uint32_t max_chunks = 0;
+            for (uint32_t g = 0; g < count; ++g) {
+                GS& s = gs[g];
+                if (s.L < r) continue;
+                const uint32_t level = s.L - r;
+                const uint32_t nl = s.h->g[level]->n;
+                const float b = b_per_graph ? b_per_graph[g] : p.b;
+                BatchJob J{};
+                J.etab = s.d->etab;
+                J.nnz = s.d->nnz;
+                J.vtab = s.d->vtab;
+                J.anc = level == 0 ? nullptr : s.h->anc[level];
+                J.Y = s.cur;
+                if (sync_mode) {
+                    s.G = DBuf<float2>(ctx, nl);
+                    DRG_CUDA(cudaMemsetAsync(s.G.p, 0, sizeof(float2) * nl, ctx->stream));
+                    J.G = s.G.p;
+                }
+                if (prec) {
+                    s.Yh = DBuf<uint32_t>(ctx, nl);
+                    J.Yh = s.Yh.p;
+                }
+                J.n0 = s.d->n;
+                J.nl = nl;
+                J.chunk = (uint32_t)(((uint64_t)nl + p.substeps - 1) / p.substeps);
+                J.tag = stream_tag(kPurposeSample, g, level);
+                J.gamma = (level == s.L && s.L > 0) ? p.gamma_coarsest : p.gamma;
+                J.b = b;
+                J.twob = 2.f * b;
+                J.bint = int_b(b);
+                const uint32_t chunks = (uint32_t)(((uint64_t)nl + J.chunk - 1) / J.chunk);
+                max_chunks = chunks > max_chunks ? chunks : max_chunks;
+                jobs.push_back(J);
+                owner.push_back(g);
+                bpre.push_back(bpre.back() + (J.chunk + 255) / 256);
+                npre.push_back(npre.back() + (nl + 255) / 256);
+                samples += nl;
+            }
+            const uint32_t njobs = (uint32_t)jobs.size();
+            DBuf<BatchJob> djobs(ctx, njobs);
+            DBuf<uint32_t> dbpre(ctx, njobs + 1), dnpre(ctx, njobs + 1);
+            h2d(ctx, djobs.p, jobs.data(), njobs);
+            h2d(ctx, dbpre.p, bpre.data(), njobs + 1);
+            h2d(ctx, dnpre.p, npre.data(), njobs + 1);
+            BatchArgs ba{};
+            ba.common = proto;
+            ba.common.st = st.p;
+            ba.jobs = djobs.p;
+            ba.block_prefix = dbpre.p;
+            ba.node_prefix = dnpre.p;
+            ba.njobs = njobs;
+            h2d(ctx, st.p, &st_host, 1);
+            if (prec) launch_apply_batch(ctx, prec, npre.back(), ba);  // first half copies (G is zero)
+            auto epoch_body = [&]() {
+                for (uint32_t c = 0; c < max_chunks; ++c) {
+                    BatchArgs bc = ba;
+                    bc.common.late = c == 0 ? 1 : 0;
+                    launch_pdl(ctx, "k_epoch_batch", ek, bpre.back(), 256, 0, bc, c);
+                    if (sync_mode) launch_apply_batch(ctx, prec, npre.back(), ba);
+                }
+                if (!sync_mode && prec) launch_apply_batch(ctx, prec, npre.back(), ba);
+            };
+            const uint64_t per_epoch = (uint64_t)max_chunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
+            if (ctx->direct_launch) {
+                ProfSpan span(ctx, DRG_PROF_EPOCH, samples * p.epochs, (uint64_t)p.epochs * max_chunks);
+                for (uint32_t t = 0; t < p.epochs; ++t) {
+                    DRG_LAUNCH(ctx, k_set_epoch, 1, 1, 0, st.p, t, p.epochs, lr_host[t]);
+                    epoch_body();
+                }
+            } else {
+                run_epoch_loop_graph(ctx, st.p, epoch_body, (uint64_t)p.epochs * per_epoch, samples * p.epochs,
+                                     (uint64_t)p.epochs * max_chunks);
+            }
+            sync(ctx);
+            // refinement of every graph whose level was not its finest
+            for (uint32_t x = 0; x < njobs; ++x) {
+                GS& s = gs[owner[x]];
+                const uint32_t level = s.L - r;
+                s.G.reset();
+                s.Yh.reset();
+                if (level == 0) continue;
+                const uint32_t nf = s.h->g[level - 1]->n;
+                DBuf<float2> nb;
+                float2* fine = reinterpret_cast<float2*>(pos[owner[x]]);
+                if (level - 1 > 0) {
+                    nb = DBuf<float2>(ctx, nf);
+                    fine = nb.p;
+                }
+                DRG_LAUNCH(ctx, k_interp, grid_for(nf, 256, (uint32_t)ctx->num_sms * 8), 256, 0, s.cur,
+                           s.h->parent[level - 1], fine, nf);
+                s.buf = std::move(nb);
+                s.cur = fine;
+            }
+        }
+        sync(ctx);
+    } catch (...) {
+        free_all();
+        throw;
+    }
+    free_all();
 }
 
 // ------------------------------------------------------------------ allocation-free level run
