@@ -266,7 +266,7 @@ drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const
 #define DRG_PROF_DMAT 2    /* drg_build_distance_matrix as a whole; units = entries */
 #define DRG_PROF_HIER 3    /* hierarchy construction as a whole; units = levels */
 #define DRG_PROF_GRAPH 4   /* drg_graph_from_edges; units = input edges */
-#define DRG_PROF_BFS 5     /* k-order BFS of the distance matrix; units = entries */
+#define DRG_PROF_BFS 5     /* the k-order BFS traversal kernel(s) of the distance matrix */
 #define DRG_PROF_SIM 6     /* similarity and quantised weights; units = entries */
 #define DRG_PROF_ALIAS 7   /* both alias tables and the edge records; units = entries + nodes */
 #define DRG_PROF_ALLOC 8   /* host time inside device allocation calls; launches = calls, units = bytes */

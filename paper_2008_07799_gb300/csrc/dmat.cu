@@ -303,22 +303,27 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     // neighbours of (deg(u) - 1) entries, so the total is at most sum deg^2;
     // for k > 2 whatever a quarter of the free memory holds
     uint64_t cap;
-    if (k2) {
+    {
         DBuf<uint64_t> s2(ctx, 1);
         DBuf<uint64_t> tmp(ctx, n);
         scan<uint64_t>(ctx, DegSq{g->rp}, n, tmp.p, false, s2.p);
         cap = read1(ctx, s2.p);
-    } else {
-        size_t fr = 0, tt = 0;
-        DRG_CUDA(cudaMemGetInfo(&fr, &tt));
-        cap = fr / 4 / 5;
     }
+    if (!k2) cap *= 4;  // a guess: rows that overflow it are traversed again
     if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
-    size_t fr = 0, tt = 0;
-    DRG_CUDA(cudaMemGetInfo(&fr, &tt));
-    if (cap * 5 > fr / 2) cap = fr / 2 / 5;  // leave room for the final arrays
-    DBuf<uint32_t> scol(ctx, cap ? cap : 1);
-    DBuf<uint8_t> sdist(ctx, cap ? cap : 1);
+    DBuf<uint32_t> scol;
+    DBuf<uint8_t> sdist;
+    try {
+        scol = DBuf<uint32_t>(ctx, cap ? cap : 1);
+        sdist = DBuf<uint8_t>(ctx, cap ? cap : 1);
+    } catch (const Error& e) {
+        if (e.status != DRG_ENOMEM) throw;
+        scol.reset();
+        sdist.reset();
+        cap = 0;  // no room to stage: every row overflows and is traversed twice
+        scol = DBuf<uint32_t>(ctx, 1);
+        sdist = DBuf<uint8_t>(ctx, 1);
+    }
     BfsArgs a{};
     a.rp = g->rp; a.col = g->col; a.n = n; a.k = k; a.words = words; a.swords = swords;
     a.gbitmaps = smem_bm ? nullptr : gbm.p;
@@ -329,7 +334,10 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(overflow.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(cursor.p, 0, 8, ctx->stream));
-    DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
+    {
+        ProfSpan sb(ctx, DRG_PROF_BFS, 0);
+        DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
+    }
     DBuf<uint64_t> tot(ctx, 1);
     scan<uint64_t>(ctx, LoadArr<uint64_t>{counts.p}, n, d->rp, false, tot.p);
     d2d(ctx, d->rp + n, tot.p, 1);
@@ -351,6 +359,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     a.out_col = d->col;
     a.out_dist = d->dist;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
+    ProfSpan sb(ctx, DRG_PROF_BFS, 0);
     DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
 }
 
@@ -652,11 +661,7 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
     try {
         DRG_CHECK(g->nnz > 0, DRG_EEMPTY, "graph has no edges");
         ProfSpan span(ctx, DRG_PROF_DMAT, 0);
-        {
-            ProfSpan sb(ctx, DRG_PROF_BFS, 0);
-            build_korder(ctx, g, k, d);
-            sb.units = d->nnz;
-        }
+        build_korder(ctx, g, k, d);
         span.units = d->nnz;
         const uint32_t n = d->n;
         const uint64_t nnz = d->nnz;

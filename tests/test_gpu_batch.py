@@ -31,31 +31,33 @@ def _mixed():
 
 
 def test_batch_equals_single_graph_runs(env):
-    # Two single-graph runs of the same input already differ by the order of
-    # their FP32 atomic adds, and the dynamics amplify that; the batch must
-    # stay within that run-to-run spread (x10) of a single run.
+    # With repulsion switched off (gamma = 0) the updates are attraction only,
+    # a contracting dynamic that does not amplify the different order of FP32
+    # atomic adds; the M negatives are still drawn from each graph's own node
+    # table.  Every graph of the batch must then match its single run closely.
     drg, ctx = env
     items = _mixed()
-    p = drg.Params.default(k=2, M=5, epochs=3, lr0=0.05, mode=0, stop_nodes=200, seed=11)
+    p = drg.Params.default(k=2, M=5, epochs=20, gamma=0.0, gamma_coarsest=0.0, mode=0, stop_nodes=200, seed=11)
     graphs = [drg.graph_from_edges(ctx, *g) for _, g, _ in items]
     bs = [b for _, _, b in items]
     pos = [torch.zeros(2 * g[0], device="cuda") for _, g, _ in items]
     drg.layout_batch(ctx, graphs, p, pos, b=bs)
     torch.cuda.synchronize()
     for gid, ((_, g, b), G, out) in enumerate(zip(items, graphs, pos)):
-        q = p.replace(gid=gid, b=b)
-        runs = []
-        for _ in range(3):
-            ref = torch.zeros(2 * g[0], device="cuda")
-            drg.layout(ctx, G, q, ref)
-            torch.cuda.synchronize()
-            runs.append(ref.cpu().numpy().reshape(-1, 2).astype(np.float64))
+        ref = torch.zeros(2 * g[0], device="cuda")
+        drg.layout(ctx, G, p.replace(gid=gid, b=b), ref)
+        torch.cuda.synchronize()
         a = out.cpu().numpy().reshape(-1, 2).astype(np.float64)
-        ext = float(np.max(np.ptp(runs[0], axis=0)))
-        spread = max(np.max(np.abs(runs[i] - runs[j])) for i in range(3) for j in range(i))
-        assert ext > 0 and np.all(np.isfinite(a))
-        err = np.max(np.abs(a - runs[0]))
-        assert err <= 10 * spread + 1e-4 * ext, (gid, err, spread, ext)
+        r = ref.cpu().numpy().reshape(-1, 2).astype(np.float64)
+        scale = float(np.max(np.abs(r)))
+        assert scale > 0 and np.all(np.isfinite(a))
+        err = float(np.max(np.abs(a - r)))
+        assert err <= 1e-4 * scale, (gid, err, scale)
+    # and a different graph id gives a different layout (the ids reach the streams)
+    ref = torch.zeros(2 * items[0][1][0], device="cuda")
+    drg.layout(ctx, graphs[0], p.replace(gid=1, b=bs[0]), ref)
+    torch.cuda.synchronize()
+    assert float(torch.max(torch.abs(ref - pos[0]))) > 1e-3 * float(torch.max(torch.abs(pos[0])))
 
 
 def test_batch_quality_matches_oracle(env, orc):
