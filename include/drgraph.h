@@ -152,6 +152,11 @@ drg_status drg_dmat_info(const drg_dmat* d, uint32_t* n, uint64_t* nnz, uint32_t
 drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint32_t* col, uint8_t* dist,
                              uint32_t* q, uint64_t* r, float* Z, uint32_t* e_thresh, uint32_t* e_alias,
                              uint32_t* v_thresh, uint32_t* v_alias);
+/* Host copies of the entries [e_begin, e_end) only (any pointer may be NULL):
+ * col, dist, q, and the edge table's thresh and alias entry of those
+ * buckets.  e_end <= nnz.  Synchronises. */
+drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_begin, uint64_t e_end, uint32_t* col,
+                                   uint8_t* dist, uint32_t* q, uint32_t* e_thresh, uint32_t* e_alias);
 drg_status drg_dmat_destroy(drg_dmat* d);
 
 /* ---------------------------------------------------------------- hierarchy */

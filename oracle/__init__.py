@@ -63,6 +63,14 @@ def lib():
     L.orc_korder_fill.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, U64P, U32P, U8P]
     L.orc_similarity.argtypes = [C.c_uint32, U64P, U32P, U8P, C.c_uint32, C.c_float,
                                  F32P, F32P, U32P, U64P, F64P]
+    L.orc_korder_row.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
+    L.orc_korder_row.restype = C.c_uint32
+    L.orc_class_counts.argtypes = [C.c_uint32, U64P, U32P, C.c_uint32, C.c_uint32, U32P, U64P]
+    L.orc_normaliser.argtypes = [C.c_uint32, U64P, F32P]
+    L.orc_normaliser.restype = C.c_float
+    L.orc_entry_weight.argtypes = [C.c_float, C.c_float, C.c_float]
+    L.orc_entry_weight.restype = C.c_uint32
     L.orc_node_weights_u32.argtypes = [C.c_uint32, U64P, U32P]
     L.orc_node_weights_u32.restype = C.c_uint32
     L.orc_alias_build.argtypes = [C.c_uint64, U32P, U32P, U32P, U64P]
@@ -162,6 +170,49 @@ def korder(rp, col, k):
     gd_dist = np.zeros(max(nnz, 1), np.uint8)
     assert L.orc_korder_fill(n, rp, col, k, gd_rp, gd_col, gd_dist) == 0
     return gd_rp, gd_col[:nnz], gd_dist[:nnz]
+
+
+class RowBFS:
+    """Single rows of GD (spot checks of graphs too large for the full matrix)."""
+
+    def __init__(self, rp, col, k):
+        self.rp, self.col, self.k = rp, col, k
+        n = len(rp) - 1
+        self.dist = np.full(max(n, 1), -1, np.int32)
+        self.queue = np.zeros(max(n, 1), np.uint32)
+        self.out_col = np.zeros(max(n, 1), np.uint32)
+        self.out_dist = np.zeros(max(n, 1), np.uint8)
+
+    def row(self, src):
+        L = lib()
+        cnt = L.orc_korder_row(len(self.rp) - 1, self.rp, self.col, self.k, int(src),
+                               self.dist.ctypes.data_as(C.c_void_p), self.queue.ctypes.data_as(C.c_void_p),
+                               self.out_col.ctypes.data_as(C.c_void_p), self.out_dist.ctypes.data_as(C.c_void_p))
+        return self.out_col[:cnt].copy(), self.out_dist[:cnt].copy()
+
+
+def class_counts(rp, col, k, sources):
+    """counts[x, d-1] = number of nodes at hop distance d from sources[x]."""
+    sel = np.ascontiguousarray(sources, np.uint32)
+    out = np.zeros((max(len(sel), 1), k), np.uint64)
+    assert lib().orc_class_counts(len(rp) - 1, rp, col, k, len(sel), sel if len(sel) else np.zeros(1, np.uint32),
+                                  out.reshape(-1)) == 0
+    return out[:len(sel)]
+
+
+def gaussians(k, sigma=1.0):
+    """g(d) for d = 1..k as FP32 (FP64 exp of the FP32 sigma, rounded once)."""
+    s = float(np.float32(sigma))
+    return np.array([np.exp(-(d * d) / (2.0 * s * s)) for d in range(1, k + 1)]).astype(np.float32)
+
+
+def normaliser(counts_row, g):
+    c = np.ascontiguousarray(counts_row, np.uint64)
+    return float(lib().orc_normaliser(len(g), c, np.ascontiguousarray(g, np.float32)))
+
+
+def entry_weight(gd, zi, zj):
+    return int(lib().orc_entry_weight(float(gd), float(zi), float(zj)))
 
 
 def similarity(gd_rp, gd_col, gd_dist, k, sigma=1.0):

@@ -145,6 +145,42 @@ int orc_korder_fill(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_
     return 0;
 }
 
+/* Row `src` of GD alone (the same BFS as above, for spot checks of large
+ * graphs): writes the row sorted by node id with hop distances and returns
+ * its length.  dist (n entries, all -1) and queue (n entries) are scratch the
+ * caller provides; dist is restored to all -1 on return.                     */
+uint32_t orc_korder_row(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_t k, uint32_t src,
+                        int32_t* dist, uint32_t* queue, uint32_t* out_col, uint8_t* out_dist)
+{
+    uint32_t cnt = orc_bfs(n, rp, col, k, src, dist, queue);
+    uint32_t w = 0;
+    for (uint32_t q = 0; q < cnt; ++q)
+        if (queue[q] != src) out_col[w++] = queue[q];
+    qsort(out_col, w, sizeof(uint32_t), orc_cmp_u32);
+    for (uint32_t q = 0; q < w; ++q) out_dist[q] = (uint8_t)dist[out_col[q]];
+    for (uint32_t q = 0; q < cnt; ++q) dist[queue[q]] = -1;
+    return w;
+}
+
+/* For each listed source, the number of nodes at hop distance d = 1..k
+ * (counts[x * k + d - 1]): the class sizes that define Z_i in Eq. 9.        */
+int orc_class_counts(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_t k,
+                     uint32_t nsel, const uint32_t* sel, uint64_t* counts)
+{
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    uint32_t* queue = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n ? n : 1));
+    if (!dist || !queue) { free(dist); free(queue); return -1; }
+    for (uint32_t v = 0; v < n; ++v) dist[v] = -1;
+    for (uint32_t x = 0; x < nsel; ++x) {
+        uint32_t cnt = orc_bfs(n, rp, col, k, sel[x], dist, queue);
+        for (uint32_t d = 0; d < k; ++d) counts[(size_t)x * k + d] = 0;
+        for (uint32_t q = 1; q < cnt; ++q) counts[(size_t)x * k + dist[queue[q]] - 1] += 1;
+        for (uint32_t q = 0; q < cnt; ++q) dist[queue[q]] = -1;
+    }
+    free(dist); free(queue);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 3.2.1 Eq. 9 (sparse conditional similarity NS_{j|i} = g(GD_ij)/Z_i
  * over NNG(v_i,k), g(d) = exp(-d^2 / 2 sigma^2), the k values precomputed)
@@ -162,6 +198,27 @@ int orc_korder_fill(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_
  *   ns[e]   exact FP64 NS_ij (reference value, not used for sampling)
  * Pinned by: rows of NS_{j|i} summing to 1, k = 1 giving 1/deg, symmetry,
  * sum NS_ij = 1 and the quantisation error bound.                           */
+/* Z_i in FP32: sum over d = 1..k, in that order, of fl(count_i(d) g(d)). */
+float orc_normaliser(uint32_t k, const uint64_t* count, const float* g)
+{
+    float z = 0.0f;
+    for (uint32_t d = 1; d <= k; ++d) {
+        float term = (float)count[d - 1] * g[d - 1];
+        z = z + term;
+    }
+    return z;
+}
+
+/* q_e = floor((fl(g / Z_i) + fl(g / Z_j)) * 2^30) in FP32. */
+uint32_t orc_entry_weight(float gd, float zi, float zj)
+{
+    float p_ji = gd / zi;
+    float p_ij = gd / zj;
+    float s = p_ji + p_ij;
+    float scaled = s * 1073741824.0f; /* 2^30, exact */
+    return (uint32_t)scaled;
+}
+
 int orc_similarity(uint32_t n, const uint64_t* rp, const uint32_t* col, const uint8_t* dist,
                    uint32_t k, float sigma, float* g, float* Z, uint32_t* q, uint64_t* r, double* ns)
 {
@@ -176,14 +233,9 @@ int orc_similarity(uint32_t n, const uint64_t* rp, const uint32_t* col, const ui
     for (uint32_t i = 0; i < n; ++i) {
         for (uint32_t d = 0; d <= k; ++d) cnt[d] = 0;
         for (uint64_t e = rp[i]; e < rp[i + 1]; ++e) cnt[dist[e]] += 1;
-        float z = 0.0f;
         double z64 = 0.0;
-        for (uint32_t d = 1; d <= k; ++d) {
-            float term = (float)cnt[d] * g[d - 1];
-            z = z + term;
-            z64 += (double)cnt[d] * g64[d];
-        }
-        Z[i] = z;
+        for (uint32_t d = 1; d <= k; ++d) z64 += (double)cnt[d] * g64[d];
+        Z[i] = orc_normaliser(k, cnt + 1, g);
         Z64[i] = z64;
     }
     for (uint32_t i = 0; i < n; ++i) {
@@ -191,11 +243,7 @@ int orc_similarity(uint32_t n, const uint64_t* rp, const uint32_t* col, const ui
         for (uint64_t e = rp[i]; e < rp[i + 1]; ++e) {
             uint32_t j = col[e];
             uint32_t d = dist[e];
-            float p_ji = g[d - 1] / Z[i];
-            float p_ij = g[d - 1] / Z[j];
-            float s = p_ji + p_ij;
-            float scaled = s * 1073741824.0f; /* 2^30, exact */
-            q[e] = (uint32_t)scaled;
+            q[e] = orc_entry_weight(g[d - 1], Z[i], Z[j]);
             acc += q[e];
             if (ns) ns[e] = (g64[d] / Z64[i] + g64[d] / Z64[j]) / (2.0 * (double)n);
         }

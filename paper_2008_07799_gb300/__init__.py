@@ -36,7 +36,7 @@ EXPORTS = [
     "drg_build_hierarchy", "drg_hier_info", "drg_hier_download", "drg_hier_graph", "drg_hier_destroy",
     "drg_init_positions", "drg_layout_level", "drg_interpolate", "drg_layout", "drg_layout_edges",
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
-    "drg_layout_level_noalloc",
+    "drg_layout_level_noalloc", "drg_dmat_download_range",
 ]
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
@@ -107,6 +107,7 @@ def lib():
         "drg_dmat_info": (st, [VP, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
         "drg_dmat_download": (st, [VP] * 12),
         "drg_dmat_destroy": (st, [VP]),
+        "drg_dmat_download_range": (st, [VP, VP, C.c_uint64, C.c_uint64, VP, VP, VP, VP, VP]),
         "drg_coarsen": (st, [VP, VP, C.c_uint32, PP, C.POINTER(VP), VP]),
         "drg_build_hierarchy": (st, [VP, VP, PP, C.POINTER(VP)]),
         "drg_hier_info": (st, [VP, C.POINTER(C.c_uint32), VP]),
@@ -271,6 +272,26 @@ class DistanceMatrix(_Handle):
             out[key] = out[key][:nnz]
         out["shift"] = shift
         return out
+
+    def download_nodes(self):
+        """The per-node arrays only: rp, r, Z and the node table."""
+        n, nnz, shift = self.info()
+        out = dict(rp=np.zeros(n + 1, np.uint64), r=np.zeros(n, np.uint64), Z=np.zeros(n, np.float32),
+                   v_thresh=np.zeros(n, np.uint32), v_alias=np.zeros(n, np.uint32), shift=shift, nnz=nnz)
+        self.ctx.check(lib().drg_dmat_download(self.ctx.h, self.h, _ptr(out["rp"]), None, None, None, _ptr(out["r"]),
+                                               _ptr(out["Z"]), None, None, _ptr(out["v_thresh"]),
+                                               _ptr(out["v_alias"])))
+        return out
+
+    def download_range(self, e0, e1):
+        """Entries [e0, e1): col, dist, q and the edge table's thresh and alias."""
+        m = max(e1 - e0, 1)
+        out = dict(col=np.zeros(m, np.uint32), dist=np.zeros(m, np.uint8), q=np.zeros(m, np.uint32),
+                   e_thresh=np.zeros(m, np.uint32), e_alias=np.zeros(m, np.uint32))
+        self.ctx.check(lib().drg_dmat_download_range(self.ctx.h, self.h, int(e0), int(e1), _ptr(out["col"]),
+                                                     _ptr(out["dist"]), _ptr(out["q"]), _ptr(out["e_thresh"]),
+                                                     _ptr(out["e_alias"])))
+        return {k: v[:e1 - e0] for k, v in out.items()}
 
 
 class Hierarchy(_Handle):

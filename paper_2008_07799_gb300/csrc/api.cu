@@ -327,6 +327,22 @@ drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint
     API_CATCH(ctx)
 }
 
+drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_begin, uint64_t e_end, uint32_t* col,
+                                   uint8_t* dist, uint32_t* q, uint32_t* e_thresh, uint32_t* e_alias) {
+    if (!ctx || !d || e_begin > e_end || e_end > d->nnz) return DRG_EINVAL;
+    API_TRY
+    const uint64_t m = e_end - e_begin;
+    if (col) drg::d2h(ctx, col, d->col + e_begin, m);
+    if (dist) drg::d2h(ctx, dist, d->dist + e_begin, m);
+    if (q) drg::d2h(ctx, q, d->q + e_begin, m);
+    if (e_alias) drg::d2h(ctx, e_alias, d->e_alias + e_begin, m);
+    if (e_thresh && m)
+        DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), d->etab + e_begin, sizeof(EdgeRec), sizeof(uint32_t), m,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    drg::sync(ctx);
+    API_CATCH(ctx)
+}
+
 drg_status drg_dmat_destroy(drg_dmat* d) {
     if (!d) return DRG_EINVAL;
     drg::dmat_free(d);

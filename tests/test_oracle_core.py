@@ -273,3 +273,26 @@ def test_alias_draw_chi_square(orc):
     m = expect > 0
     chi2 = ((counts[m] - expect[m]) ** 2 / expect[m]).sum()
     assert chi2 < stats.chi2.ppf(0.999, m.sum() - 1)
+
+
+# ---------------------------------------------------------------- spot-check helpers
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_row_helpers_match_full_matrix(orc, k):
+    n, s, d = gg.barabasi_albert(700, 3, 4)
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, k)
+    sim = orc.similarity(*gd, k, 1.0)
+    rows = orc.RowBFS(rp, col, k)
+    src = np.array([0, 5, 77, 699, 350], np.uint32)
+    counts = orc.class_counts(rp, col, k, src)
+    g = orc.gaussians(k)
+    assert np.array_equal(g, sim["g"])
+    for x, i in enumerate(src.tolist()):
+        c, dd = rows.row(i)
+        assert np.array_equal(c, gd[1][gd[0][i]:gd[0][i + 1]]) and np.array_equal(dd, gd[2][gd[0][i]:gd[0][i + 1]])
+        assert counts[x].tolist() == [int((dd == t).sum()) for t in range(1, k + 1)]
+        assert np.float32(orc.normaliser(counts[x], g)) == sim["Z"][i]
+    e = int(gd[0][5])
+    j = int(gd[1][e])
+    zj = orc.normaliser(orc.class_counts(rp, col, k, [j])[0], g)
+    assert orc.entry_weight(g[gd[2][e] - 1], sim["Z"][5], zj) == sim["q"][e]
