@@ -124,10 +124,18 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_sample():
-    """DRAM bytes per sample of k_epoch from the committed ncu summary, or None
-    when the kernel source has changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "k_epoch_traffic.json")
+def epoch_kernel(graph, mode, precision):
+    """The kernel that runs a level's samples: one persistent launch per level
+    for FP32 Hogwild on one graph, sub-step launches otherwise."""
+    if graph == "batch256":
+        return "k_epoch_batch"
+    return "k_hogwild" if mode == "hogwild" and precision == "fp32" else "k_epoch"
+
+
+def ncu_traffic_per_sample(kernel):
+    """DRAM bytes per sample of the level kernel from the committed ncu
+    summary, or None when the kernel source has changed since that capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -384,7 +392,8 @@ def main():
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
     bytes_total = s0 * algo_bytes_per_sample(wl["M"], prec, False) + coarse * algo_bytes_per_sample(wl["M"], prec, True)
     achieved = bytes_total / (ep_ms / 1000.0) / 1e9
-    tps = ncu_traffic_per_sample()
+    kname = epoch_kernel(wl["graph"], args.mode, args.precision)
+    tps = ncu_traffic_per_sample(kname)
     avg_launch_samples = ep_samples / max(ep_launches, 1)
     line = {
         "metric": "edge-sample gradient updates/s",
@@ -406,7 +415,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "phases_ms": {"distance_matrix_and_tables": dm_ms, "hierarchy": hi_ms, "layout_levels": ep_ms, **sub_ms},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_epoch", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
                      "traffic": None if tps is None else tps * avg_launch_samples,
                      "algorithmic_bytes_note": ALGO_BYTES_NOTE,

@@ -473,19 +473,27 @@ __device__ __forceinline__ uint64_t merge_path(const u128* A, uint64_t nA, const
 
 constexpr int MERGE_THREADS = 256, MERGE_ITEMS = 8, MERGE_TILE = MERGE_THREADS * MERGE_ITEMS;
 
+// Merge-path split of every tile boundary (diagonal t * MERGE_TILE, and the
+// end): one thread per boundary, all searches in flight together.
+__global__ void k_merge_partition(const u128* __restrict__ A, uint64_t nA, const u128* __restrict__ B, uint64_t nB,
+                                  uint64_t tiles, uint64_t* __restrict__ part) {
+    const uint64_t total = nA + nB;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= tiles; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = t * MERGE_TILE < total ? t * MERGE_TILE : total;
+        part[t] = merge_path(A, nA, B, nB, d);
+    }
+}
+
 __global__ void __launch_bounds__(MERGE_THREADS) k_merge_ranks(const u128* __restrict__ A, uint64_t nA,
                                                                const u128* __restrict__ B, uint64_t nB,
+                                                               const uint64_t* __restrict__ part,
                                                                uint32_t* __restrict__ a_rank,
                                                                uint32_t* __restrict__ b_rank) {
     __shared__ u128 s[MERGE_TILE];
-    __shared__ uint64_t s_x0, s_x1;
     const uint64_t total = nA + nB;
     const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_TILE;
     const uint64_t d1 = d0 + MERGE_TILE < total ? d0 + MERGE_TILE : total;
-    if (threadIdx.x == 0) s_x0 = merge_path(A, nA, B, nB, d0);
-    if (threadIdx.x == 32) s_x1 = merge_path(A, nA, B, nB, d1);
-    __syncthreads();
-    const uint64_t x0 = s_x0, x1 = s_x1, y0 = d0 - x0, y1 = d1 - x1;
+    const uint64_t x0 = part[blockIdx.x], x1 = part[blockIdx.x + 1], y0 = d0 - x0, y1 = d1 - x1;
     const uint32_t na = (uint32_t)(x1 - x0), nb = (uint32_t)(y1 - y0);
     for (uint32_t t = threadIdx.x; t < na; t += MERGE_THREADS) s[t] = A[x0 + t];
     for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) s[na + t] = B[y0 + t];
@@ -611,7 +619,12 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, 
     scan<u128>(ctx, HeavyExcess{q, H.p, N, W}, nH, S.p, true, nullptr);
     DBuf<uint32_t> a_rank(ctx, nL), b_rank(ctx, nH);
     const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
-    DRG_LAUNCH(ctx, k_merge_ranks, (uint32_t)tiles, MERGE_THREADS, 0, Dl.p, nL, S.p, nH, a_rank.p, b_rank.p);
+    {
+        DBuf<uint64_t> part(ctx, tiles + 1);
+        DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, Dl.p, nL, S.p, nH, tiles, part.p);
+        DRG_LAUNCH(ctx, k_merge_ranks, (uint32_t)tiles, MERGE_THREADS, 0, Dl.p, nL, S.p, nH, part.p, a_rank.p,
+                   b_rank.p);
+    }
     DRG_LAUNCH(ctx, k_alias_lights, grid_for(nL, 256, 65536), 256, 0, q, L.p, nL, H.p, a_rank.p, N, W, make_invdiv(W), thresh, alias);
     DRG_LAUNCH(ctx, k_alias_heavies, grid_for(nH, 256, 65536), 256, 0, H.p, nH, S.p, Dl.p, b_rank.p, W, make_invdiv(W), thresh,
                alias);

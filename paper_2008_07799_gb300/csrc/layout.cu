@@ -227,6 +227,204 @@ __global__ void __launch_bounds__(256) k_epoch(EpochArgs a) {
     epoch_sample<MT, SYNC, PREC>(a, a.s_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x);
 }
 
+// Index of the last entry of prefix[0 .. njobs) that is <= blk (prefix is
+// non-decreasing, prefix[0] = 0): the job that owns block or thread blk.
+__device__ __forceinline__ uint32_t find_job(const uint32_t* prefix, uint32_t njobs, uint32_t blk) {
+    uint32_t lo = 0, hi = njobs;  // last job whose prefix is <= blk
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= blk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------ Hogwild level run in one launch
+// Asynchronous mode (Sec. 4.3) as one persistent grid of T threads.  The
+// samples of the run, epoch after epoch, form the sequence q = (t - t_begin)
+// n_l + s; thread g takes q = g, g + T, g + 2T, ... one at a time.  A sample
+// is in flight from its position gathers to its atomic adds, so at most T <=
+// ceil(n_l / substeps) samples are in flight at any moment -- the bound the
+// sub-step runs give -- but no thread ever waits for another.  Each thread
+// keeps two samples ahead of the one it updates: the next sample's table
+// records are resolved (and mapped through the ancestors) and the one after
+// has its Philox words drawn and its records requested while the current
+// sample's gathers are in flight.  Positions are read through L2 only
+// (ld.global.cg), since other SMs change them for the whole launch.
+struct HogwildArgs {
+    EpochArgs a;
+    const float* lr_tab;  // [epochs] learning rate of each epoch
+    uint32_t t_begin, T;  // first epoch; number of threads
+    uint32_t nl;          // samples per epoch
+    uint64_t total;       // (t_end - t_begin) n_l
+};
+
+// A sample's table records, requested (stage 1).
+template <int MT>
+struct Requested {
+    uint4 e;             // thresh, i0, j0, i1 of the drawn edge bucket
+    uint32_t j1, Ue;
+    uint2 v[MT];         // node-table records of the negatives' buckets
+    uint32_t bkt[MT], Uv[MT];
+};
+
+// A sample's nodes on the level (stage 2).
+template <int MT>
+struct Resolved {
+    uint32_t ia, ic, jm[MT];
+};
+
+template <int MT>
+__device__ __forceinline__ void hw_request(const EpochArgs& a, uint32_t s, uint32_t t, Requested<MT>& r) {
+    Words W(s, t, a.tag, a.key);
+    const uint64_t R = (uint64_t)W(0) | ((uint64_t)W(1) << 32);
+    r.Ue = W(2);
+    const uint64_t bkt = alias_bucket(R, a.nnz);
+    r.e = __ldg(reinterpret_cast<const uint4*>(a.etab + bkt));
+    r.j1 = __ldg(&a.etab[bkt].j1);
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+        const uint64_t Rm = (uint64_t)W(3 + 3 * m) | ((uint64_t)W(4 + 3 * m) << 32);
+        r.Uv[m] = W(5 + 3 * m);
+        r.bkt[m] = (uint32_t)alias_bucket(Rm, a.n0);
+        r.v[m] = __ldg(&a.vtab[r.bkt[m]]);
+    }
+}
+
+template <int MT, bool ANC>
+__device__ __forceinline__ void hw_resolve(const EpochArgs& a, const Requested<MT>& r, Resolved<MT>& o) {
+    const bool keep = r.Ue < r.e.x;
+    const uint32_t i = keep ? r.e.y : r.e.w;
+    const uint32_t j = keep ? r.e.z : r.j1;
+    o.ia = ANC ? __ldg(&a.anc[i]) : i;
+    o.ic = ANC ? __ldg(&a.anc[j]) : j;
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+        const uint32_t c = r.Uv[m] < r.v[m].x ? r.bkt[m] : r.v[m].y;
+        o.jm[m] = ANC ? __ldg(&a.anc[c]) : c;
+    }
+}
+
+__device__ __forceinline__ void hw_push(float2* Y, uint32_t v, float lr, float fx, float fy) {
+    atomicAdd(&Y[v], make_float2(lr * fx, lr * fy));
+}
+
+// next element of a thread's sequence: q += T
+__device__ __forceinline__ void hw_advance(uint32_t& t, uint32_t& s, uint32_t T, uint32_t nl) {
+    if (s >= nl - T) {
+        s -= nl - T;
+        ++t;
+    } else {
+        s += T;
+    }
+}
+
+// One thread's share of a run: elements g, g + T, g + 2T, ... of the sequence.
+template <int MT, bool ANC>
+__device__ __forceinline__ void hogwild_thread(const HogwildArgs& h, uint32_t g) {
+    const EpochArgs& a = h.a;
+    uint64_t left = (h.total - g + h.T - 1) / h.T;  // samples of this thread
+    if (left == 0) return;
+    uint32_t t1 = h.t_begin, s1 = g;                 // next sample to request
+    uint32_t tS = 0, tI = 0;
+    Requested<MT> S;
+    Resolved<MT> I;
+    hw_request<MT>(a, s1, t1, S);
+    tS = t1;
+    hw_advance(t1, s1, h.T, h.nl);
+    hw_resolve<MT, ANC>(a, S, I);
+    tI = tS;
+    if (left > 1) {
+        hw_request<MT>(a, s1, t1, S);
+        tS = t1;
+        hw_advance(t1, s1, h.T, h.nl);
+    }
+    for (; left > 0; --left) {
+        const float2 ya = __ldcg(&a.Y[I.ia]), yc = __ldcg(&a.Y[I.ic]);
+        float2 ym[MT];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) ym[m] = __ldcg(&a.Y[I.jm[m]]);
+        const float lr = __ldg(&h.lr_tab[tI]);
+        Resolved<MT> I2 = I;
+        const uint32_t tI2 = tS;
+        if (left > 1) hw_resolve<MT, ANC>(a, S, I2);
+        if (left > 2) {
+            hw_request<MT>(a, s1, t1, S);
+            tS = t1;
+            hw_advance(t1, s1, h.T, h.nl);
+        }
+        const float2 fa = attract(a, ya, yc);
+        float Fx = fa.x, Fy = fa.y;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            if (I.jm[m] == I.ia || I.jm[m] == I.ic) continue;
+            const float2 fr = repel(a, ya, ym[m]);
+            Fx += fr.x;
+            Fy += fr.y;
+            hw_push(a.Y, I.jm[m], lr, -fr.x, -fr.y);
+        }
+        hw_push(a.Y, I.ia, lr, Fx, Fy);
+        hw_push(a.Y, I.ic, lr, -fa.x, -fa.y);
+        I = I2;
+        tI = tI2;
+    }
+}
+
+// Runtime number of negatives: the same sequence, one sample after another.
+template <bool ANC>
+__device__ __forceinline__ void hogwild_thread_rt(const HogwildArgs& h, uint32_t g) {
+    const EpochArgs& a = h.a;
+    uint64_t left = (h.total - g + h.T - 1) / h.T;
+    uint32_t t = h.t_begin, s = g;
+    for (; left > 0; --left, hw_advance(t, s, h.T, h.nl)) {
+        Words W(s, t, a.tag, a.key);
+        uint32_t i, j;
+        draw_edge(a, W, i, j);
+        const uint32_t ia = ANC ? __ldg(&a.anc[i]) : i, ic = ANC ? __ldg(&a.anc[j]) : j;
+        const float lr = __ldg(&h.lr_tab[t]);
+        const float2 ya = __ldcg(&a.Y[ia]), yc = __ldcg(&a.Y[ic]);
+        const float2 fa = attract(a, ya, yc);
+        float Fx = fa.x, Fy = fa.y;
+        for (uint32_t m = 0; m < a.M; ++m) {
+            uint32_t cm = draw_negative(a, W, m);
+            if (ANC) cm = __ldg(&a.anc[cm]);
+            if (cm == ia || cm == ic) continue;
+            const float2 fr = repel(a, ya, __ldcg(&a.Y[cm]));
+            Fx += fr.x;
+            Fy += fr.y;
+            hw_push(a.Y, cm, lr, -fr.x, -fr.y);
+        }
+        hw_push(a.Y, ia, lr, Fx, Fy);
+        hw_push(a.Y, ic, lr, -fa.x, -fa.y);
+    }
+}
+
+template <int MT, bool ANC>
+__device__ __forceinline__ void hogwild_dispatch(const HogwildArgs& h, uint32_t g) {
+    if constexpr (MT > 0) hogwild_thread<MT, ANC>(h, g);
+    else hogwild_thread_rt<ANC>(h, g);
+}
+
+// MT > 0: compile-time number of negatives; MT == 0: runtime M.
+template <int MT, bool ANC>
+__global__ void __launch_bounds__(128) k_hogwild(HogwildArgs h) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < h.T) hogwild_dispatch<MT, ANC>(h, g);
+}
+
+// One level of each of many graphs in one launch: run x owns the threads
+// [prefix[x], prefix[x + 1]).
+template <int MT>
+__global__ void __launch_bounds__(128) k_hogwild_batch(const HogwildArgs* __restrict__ runs,
+                                                       const uint32_t* __restrict__ prefix, uint32_t nruns) {
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= prefix[nruns]) return;
+    const uint32_t x = find_job(prefix, nruns, gt);
+    const HogwildArgs& h = runs[x];
+    const uint32_t g = gt - prefix[x];
+    if (h.a.anc) hogwild_dispatch<MT, true>(h, g);
+    else hogwild_dispatch<MT, false>(h, g);
+}
+
 // ------------------------------------------------------------------ batches of graphs
 // Sub-step c of the current level of many graphs in one launch.  Blocks are
 // assigned to jobs (graph, level) by a prefix sum of each job's block count;
@@ -251,15 +449,6 @@ struct BatchArgs {
     const uint32_t* node_prefix;  // [njobs + 1] node blocks per job, prefix-summed
     uint32_t njobs;
 };
-
-__device__ __forceinline__ uint32_t find_job(const uint32_t* prefix, uint32_t njobs, uint32_t blk) {
-    uint32_t lo = 0, hi = njobs;  // last job whose prefix is <= blk
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (prefix[mid] <= blk) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 template <int MT, bool SYNC, int PREC>
 __global__ void __launch_bounds__(256) k_epoch_batch(BatchArgs ba, uint32_t c) {
@@ -444,6 +633,60 @@ static EpochKernel pick_epoch(uint32_t M, bool sync, int prec) {
 // one thread per sample
 static uint32_t epoch_grid(drg_ctx*, uint64_t count) { return (uint32_t)((count + 255) / 256); }
 
+typedef void (*HogwildKernel)(HogwildArgs);
+
+static HogwildKernel pick_hogwild(uint32_t M, bool anc) {
+    if (M == 5) return anc ? k_hogwild<5, true> : k_hogwild<5, false>;
+    return anc ? k_hogwild<0, true> : k_hogwild<0, false>;
+}
+
+// Epochs [t_begin, t_end) of an FP32 Hogwild level run in one launch: T =
+// min(ceil(n_l / substeps), resident threads) threads.
+static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p, uint32_t nl, const float* lr_tab,
+                          uint32_t t_begin, uint32_t t_end) {
+    const HogwildKernel k = pick_hogwild(p.M, a.anc != nullptr);
+    int per_sm = 0;
+    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
+    const uint64_t resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * 128u;
+    const uint64_t bound = ((uint64_t)nl + p.substeps - 1) / p.substeps;
+    HogwildArgs h{};
+    h.a = a;
+    h.lr_tab = lr_tab;
+    h.t_begin = t_begin;
+    h.T = (uint32_t)(bound < resident ? bound : resident);
+    h.nl = nl;
+    h.total = (uint64_t)(t_end - t_begin) * nl;
+    ProfSpan span(ctx, DRG_PROF_EPOCH, h.total, 1);
+    DRG_LAUNCH(ctx, k, (h.T + 127) / 128, 128, 0, h);
+}
+
+// Hogwild runs of many graphs (each with T = ceil(n_l / substeps) set) in one
+// launch.  When their threads exceed what the GPU holds at once, every run's
+// thread count is scaled down in proportion (at least one each), so that all
+// threads are resident together and the bound only tightens.
+static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& runs, uint64_t samples) {
+    if (runs.empty()) return;
+    const auto k = M == 5 ? k_hogwild_batch<5> : k_hogwild_batch<0>;
+    int per_sm = 0;
+    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
+    const uint64_t resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * 128u;
+    uint64_t want = 0;
+    for (const auto& h : runs) want += h.T;
+    const uint64_t nruns = runs.size();
+    if (want > resident) {
+        const uint64_t room = resident > nruns ? resident - nruns : 0;
+        for (auto& h : runs) h.T = (uint32_t)(1 + (uint64_t)h.T * room / want);
+    }
+    std::vector<uint32_t> prefix(nruns + 1, 0);
+    for (size_t x = 0; x < nruns; ++x) prefix[x + 1] = prefix[x] + runs[x].T;
+    DBuf<HogwildArgs> druns(ctx, nruns);
+    DBuf<uint32_t> dprefix(ctx, nruns + 1);
+    h2d(ctx, druns.p, runs.data(), nruns);
+    h2d(ctx, dprefix.p, prefix.data(), nruns + 1);
+    ProfSpan span(ctx, DRG_PROF_EPOCH, samples, 1);
+    DRG_LAUNCH(ctx, k, (prefix[nruns] + 127) / 128, 128, 0, druns.p, dprefix.p, (uint32_t)nruns);
+}
+
 // One CUDA graph for a level run: a WHILE node whose body is one epoch --
 // `body` captures its launches (sub-step runs chained by programmatic
 // dependent launch) -- closed by k_advance, which moves the epoch state on and
@@ -534,6 +777,10 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
         lr_host[t] = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
     DBuf<float> lr_tab(ctx, p.epochs);
     h2d(ctx, lr_tab.p, lr_host.data(), p.epochs);
+    if (!sync_mode && prec == DRG_PREC_FP32) {
+        hogwild_level(ctx, a, p, nl, lr_tab.p, t_begin, t_end);
+        return;
+    }
     DBuf<EpochState> st(ctx, 1);
     const EpochState st0{t_begin, t_end, lr_host[t_begin], 0u, lr_tab.p};
     h2d(ctx, st.p, &st0, 1);
@@ -725,8 +972,10 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
         const EpochState st_host{0u, p.epochs, lr_host[0], 0u, lr_tab.p};
         const EpochBatchKernel ek = pick_epoch_batch(p.M, sync_mode, prec);
         const EpochArgs proto = epoch_args(gs[0].d, nullptr, nullptr, p, p.gamma, 0);
+        const bool one_launch = !sync_mode && prec == DRG_PREC_FP32;  // Hogwild: one launch per round
         for (uint32_t r = 0; r <= Lmax; ++r) {
             std::vector<BatchJob> jobs;
+            std::vector<HogwildArgs> runs;
             std::vector<uint32_t> bpre(1, 0), npre(1, 0), owner;
             uint64_t samples = 0;
             uint32_t max_chunks = 0;
@@ -766,41 +1015,66 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                 bpre.push_back(bpre.back() + (J.chunk + 255) / 256);
                 npre.push_back(npre.back() + (nl + 255) / 256);
                 samples += nl;
+                if (one_launch) {
+                    HogwildArgs h{};
+                    h.a = proto;
+                    h.a.etab = J.etab;
+                    h.a.nnz = J.nnz;
+                    h.a.vtab = J.vtab;
+                    h.a.n0 = J.n0;
+                    h.a.anc = J.anc;
+                    h.a.Y = J.Y;
+                    h.a.tag = J.tag;
+                    h.a.gamma = J.gamma;
+                    h.a.b = J.b;
+                    h.a.twob = J.twob;
+                    h.a.bint = J.bint;
+                    h.lr_tab = lr_tab.p;
+                    h.t_begin = 0;
+                    h.T = J.chunk;
+                    h.nl = nl;
+                    h.total = (uint64_t)p.epochs * nl;
+                    runs.push_back(h);
+                }
             }
             const uint32_t njobs = (uint32_t)jobs.size();
-            DBuf<BatchJob> djobs(ctx, njobs);
-            DBuf<uint32_t> dbpre(ctx, njobs + 1), dnpre(ctx, njobs + 1);
-            h2d(ctx, djobs.p, jobs.data(), njobs);
-            h2d(ctx, dbpre.p, bpre.data(), njobs + 1);
-            h2d(ctx, dnpre.p, npre.data(), njobs + 1);
-            BatchArgs ba{};
-            ba.common = proto;
-            ba.common.st = st.p;
-            ba.jobs = djobs.p;
-            ba.block_prefix = dbpre.p;
-            ba.node_prefix = dnpre.p;
-            ba.njobs = njobs;
-            h2d(ctx, st.p, &st_host, 1);
-            if (prec) launch_apply_batch(ctx, prec, npre.back(), ba);  // first half copies (G is zero)
-            auto epoch_body = [&]() {
-                for (uint32_t c = 0; c < max_chunks; ++c) {
-                    BatchArgs bc = ba;
-                    bc.common.late = c == 0 ? 1 : 0;
-                    launch_pdl(ctx, "k_epoch_batch", ek, bpre.back(), 256, 0, bc, c);
-                    if (sync_mode) launch_apply_batch(ctx, prec, npre.back(), ba);
-                }
-                if (!sync_mode && prec) launch_apply_batch(ctx, prec, npre.back(), ba);
-            };
-            const uint64_t per_epoch = (uint64_t)max_chunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
-            if (ctx->direct_launch) {
-                ProfSpan span(ctx, DRG_PROF_EPOCH, samples * p.epochs, (uint64_t)p.epochs * max_chunks);
-                for (uint32_t t = 0; t < p.epochs; ++t) {
-                    DRG_LAUNCH(ctx, k_set_epoch, 1, 1, 0, st.p, t, p.epochs, lr_host[t]);
-                    epoch_body();
-                }
+            if (one_launch) {
+                hogwild_batch(ctx, p.M, runs, samples * p.epochs);
             } else {
-                run_epoch_loop_graph(ctx, st.p, epoch_body, (uint64_t)p.epochs * per_epoch, samples * p.epochs,
-                                     (uint64_t)p.epochs * max_chunks);
+                DBuf<BatchJob> djobs(ctx, njobs);
+                DBuf<uint32_t> dbpre(ctx, njobs + 1), dnpre(ctx, njobs + 1);
+                h2d(ctx, djobs.p, jobs.data(), njobs);
+                h2d(ctx, dbpre.p, bpre.data(), njobs + 1);
+                h2d(ctx, dnpre.p, npre.data(), njobs + 1);
+                BatchArgs ba{};
+                ba.common = proto;
+                ba.common.st = st.p;
+                ba.jobs = djobs.p;
+                ba.block_prefix = dbpre.p;
+                ba.node_prefix = dnpre.p;
+                ba.njobs = njobs;
+                h2d(ctx, st.p, &st_host, 1);
+                if (prec) launch_apply_batch(ctx, prec, npre.back(), ba);  // first half copies (G is zero)
+                auto epoch_body = [&]() {
+                    for (uint32_t c = 0; c < max_chunks; ++c) {
+                        BatchArgs bc = ba;
+                        bc.common.late = c == 0 ? 1 : 0;
+                        launch_pdl(ctx, "k_epoch_batch", ek, bpre.back(), 256, 0, bc, c);
+                        if (sync_mode) launch_apply_batch(ctx, prec, npre.back(), ba);
+                    }
+                    if (!sync_mode && prec) launch_apply_batch(ctx, prec, npre.back(), ba);
+                };
+                const uint64_t per_epoch = (uint64_t)max_chunks * (sync_mode ? 2 : 1) + 1 + (!sync_mode && prec ? 1 : 0);
+                if (ctx->direct_launch) {
+                    ProfSpan span(ctx, DRG_PROF_EPOCH, samples * p.epochs, (uint64_t)p.epochs * max_chunks);
+                    for (uint32_t t = 0; t < p.epochs; ++t) {
+                        DRG_LAUNCH(ctx, k_set_epoch, 1, 1, 0, st.p, t, p.epochs, lr_host[t]);
+                        epoch_body();
+                    }
+                } else {
+                    run_epoch_loop_graph(ctx, st.p, epoch_body, (uint64_t)p.epochs * per_epoch, samples * p.epochs,
+                                         (uint64_t)p.epochs * max_chunks);
+                }
             }
             sync(ctx);
             // refinement of every graph whose level was not its finest
