@@ -198,6 +198,8 @@ def make_params(drg, wl, args, gid):
                            precision={"fp32": 0, "fp16": 1, "bf16": 2}[args.precision], seed=args.seed, gid=gid)
     if "multilevel" in wl:
         p.multilevel = wl["multilevel"]
+    if args.substeps:
+        p.substeps = args.substeps
     return p
 
 
@@ -280,6 +282,7 @@ def main():
     ap.add_argument("--k", type=int, default=None, help="override the distance-matrix order (profiling cases)")
     ap.add_argument("--single-level", action="store_true", help="lay out G^0 only (profiling cases)")
     ap.add_argument("--once", action="store_true", help="run exactly one step and exit (for ncu captures)")
+    ap.add_argument("--substeps", type=int, default=None, help="override the in-flight bound n_l / substeps (profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -314,7 +314,7 @@ drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint
     if (Z) drg::d2h(ctx, Z, d->Z, d->n);
     if (e_alias) drg::d2h(ctx, e_alias, d->e_alias, d->nnz);
     if (e_thresh) {
-        DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), d->etab, sizeof(EdgeRec), sizeof(uint32_t), d->nnz,
+        DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), d->etab, d->erec_bytes, sizeof(uint32_t), d->nnz,
                                    cudaMemcpyDeviceToHost, ctx->stream));
     }
     if (v_thresh)
@@ -337,7 +337,8 @@ drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_b
     if (q) drg::d2h(ctx, q, d->q + e_begin, m);
     if (e_alias) drg::d2h(ctx, e_alias, d->e_alias + e_begin, m);
     if (e_thresh && m)
-        DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), d->etab + e_begin, sizeof(EdgeRec), sizeof(uint32_t), m,
+        DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), static_cast<const char*>(d->etab) + e_begin * d->erec_bytes,
+                                   d->erec_bytes, sizeof(uint32_t), m,
                                    cudaMemcpyDeviceToHost, ctx->stream));
     drg::sync(ctx);
     API_CATCH(ctx)

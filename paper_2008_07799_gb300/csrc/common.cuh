@@ -77,11 +77,21 @@ struct drg_graph {
 };
 
 // One bucket of the edge alias table: the acceptance threshold and the
-// endpoints of the bucket's own entry and of its alias entry.  32 bytes,
-// aligned, so one draw reads exactly one 32-byte sector.
+// endpoints of the bucket's own entry and of its alias entry.  Graphs with
+// fewer than 2^24 nodes use the packed 16-byte form (one 16-byte load per
+// draw): {thresh, i0 | j0 << 24, j0 >> 8 | i1 << 16, i1 >> 16 | j1 << 8}.
+// Larger graphs use this 32-byte form, aligned so that a draw reads one
+// 32-byte sector.
 struct __align__(32) EdgeRec {
     uint32_t thresh, i0, j0, i1, j1, pad0, pad1, pad2;
 };
+
+constexpr uint32_t kPackedIdLimit = 1u << 24;  // node ids of packed edge records
+
+__host__ __device__ __forceinline__ uint4 pack_edge16(uint32_t thresh, uint32_t i0, uint32_t j0, uint32_t i1,
+                                                      uint32_t j1) {
+    return make_uint4(thresh, i0 | (j0 << 24), (j0 >> 8) | (i1 << 16), (i1 >> 16) | (j1 << 8));
+}
 
 struct drg_dmat {
     drg_ctx* ctx = nullptr;
@@ -95,7 +105,8 @@ struct drg_dmat {
     uint32_t* q = nullptr;       // [nnz]
     uint64_t* r = nullptr;       // [n]
     float* Z = nullptr;          // [n]
-    EdgeRec* etab = nullptr;     // [nnz]
+    void* etab = nullptr;        // [nnz] edge records: packed 16-byte (erec_bytes 16) or EdgeRec (32)
+    uint32_t erec_bytes = 32;
     uint32_t* e_alias = nullptr; // [nnz] alias entry of each bucket
     uint2* vtab = nullptr;       // [n] {thresh, alias}
 };

@@ -631,19 +631,24 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, 
     return true;
 }
 
+template <bool PACKED>
 __global__ void k_edge_records(const uint32_t* __restrict__ thresh, const uint32_t* __restrict__ alias,
                                const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col, uint64_t nnz,
-                               EdgeRec* __restrict__ out) {
+                               void* __restrict__ out) {
     for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nnz; b += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t al = alias[b];
-        EdgeRec r;
-        r.thresh = thresh[b];
-        r.i0 = esrc[b];
-        r.j0 = col[b];
-        r.i1 = esrc[al];
-        r.j1 = col[al];
-        r.pad0 = r.pad1 = r.pad2 = 0;
-        out[b] = r;
+        if constexpr (PACKED) {
+            static_cast<uint4*>(out)[b] = pack_edge16(thresh[b], esrc[b], col[b], esrc[al], col[al]);
+        } else {
+            EdgeRec r;
+            r.thresh = thresh[b];
+            r.i0 = esrc[b];
+            r.j0 = col[b];
+            r.i1 = esrc[al];
+            r.j1 = col[al];
+            r.pad0 = r.pad1 = r.pad2 = 0;
+            static_cast<EdgeRec*>(out)[b] = r;
+        }
     }
 }
 
@@ -702,9 +707,11 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
             DBuf<uint32_t> th(ctx, nnz);
             d->e_alias = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * nnz));
             DRG_CHECK(build_alias(ctx, d->q, nnz, th.p, d->e_alias), DRG_EEMPTY, "all edge weights are zero");
-            d->etab = static_cast<EdgeRec*>(dalloc(ctx, sizeof(EdgeRec) * nnz));
-            DRG_LAUNCH(ctx, k_edge_records, grid_for(nnz, 256, 65536), 256, 0, th.p, d->e_alias, esrc.p, d->col, nnz,
-                       d->etab);
+            const bool packed = n <= kPackedIdLimit;
+            d->erec_bytes = packed ? 16u : (uint32_t)sizeof(EdgeRec);
+            d->etab = dalloc(ctx, (size_t)d->erec_bytes * nnz);
+            DRG_LAUNCH(ctx, packed ? k_edge_records<true> : k_edge_records<false>, grid_for(nnz, 256, 65536), 256, 0,
+                       th.p, d->e_alias, esrc.p, d->col, nnz, d->etab);
         }
         // node table (negative samples)
         {

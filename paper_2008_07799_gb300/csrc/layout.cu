@@ -15,6 +15,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 namespace drg {
 
@@ -29,9 +30,11 @@ struct EpochState {
 struct EpochArgs {
     const EpochState* st;               // current epoch and learning rate
     int late;                           // 1: the previous kernel may change st; wait before reading it
-    const EdgeRec* __restrict__ etab;
+    const void* __restrict__ etab;      // edge records (packed 16-byte or EdgeRec)
+    int packed;                         // 1: packed 16-byte edge records
     uint64_t nnz;
     const uint2* __restrict__ vtab;
+    const uint4* __restrict__ vtab_l;  // level node table (Hogwild kernels on coarse levels)
     uint32_t n0;
     const uint32_t* __restrict__ anc;  // level-0 node -> level node; nullptr = identity
     float2* Y;                          // positions of the level
@@ -69,15 +72,38 @@ struct Words {
     }
 };
 
+// Edge record of bucket bkt: the first 16 bytes, and j1 of the wide form.
+__device__ __forceinline__ void load_edge(const EpochArgs& a, uint64_t bkt, uint4& e, uint32_t& j1) {
+    if (a.packed) {
+        e = __ldg(static_cast<const uint4*>(a.etab) + bkt);
+        j1 = 0;
+    } else {
+        const EdgeRec* r = static_cast<const EdgeRec*>(a.etab) + bkt;
+        e = __ldg(reinterpret_cast<const uint4*>(r));
+        j1 = __ldg(&r->j1);
+    }
+}
+
+// The drawn pair: the bucket's own entry when U < thresh, else its alias.
+__device__ __forceinline__ void edge_pair(const EpochArgs& a, const uint4& e, uint32_t j1, uint32_t U, uint32_t& i,
+                                          uint32_t& j) {
+    const bool keep = U < e.x;
+    if (a.packed) {
+        i = keep ? (e.y & 0xFFFFFFu) : ((e.z >> 16) | ((e.w & 0xFFu) << 16));
+        j = keep ? ((e.y >> 24) | ((e.z & 0xFFFFu) << 8)) : (e.w >> 8);
+    } else {
+        i = keep ? e.y : e.w;
+        j = keep ? e.z : j1;
+    }
+}
+
 __device__ __forceinline__ void draw_edge(const EpochArgs& a, Words& W, uint32_t& i, uint32_t& j) {
     const uint64_t R = (uint64_t)W(0) | ((uint64_t)W(1) << 32);
     const uint32_t U = W(2);
-    const uint64_t bkt = alias_bucket(R, a.nnz);
-    const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.etab + bkt));
-    const uint32_t j1 = __ldg(&a.etab[bkt].j1);
-    const bool keep = U < r0.x;
-    i = keep ? r0.y : r0.w;
-    j = keep ? r0.z : j1;
+    uint4 e;
+    uint32_t j1;
+    load_edge(a, alias_bucket(R, a.nnz), e, j1);
+    edge_pair(a, e, j1, U, i, j);
 }
 
 __device__ __forceinline__ uint32_t draw_negative(const EpochArgs& a, Words& W, uint32_t m) {
@@ -258,12 +284,15 @@ struct HogwildArgs {
     uint64_t total;       // (t_end - t_begin) n_l
 };
 
-// A sample's table records, requested (stage 1).
-template <int MT>
+// A sample's table records, requested (stage 1).  On level 0 a negative's
+// record is the node table's {thresh, alias} and the bucket is the own item;
+// on coarser levels it is the level's node table {thresh, anc(own),
+// anc(alias), 0}, so no ancestor lookup follows.
+template <int MT, bool ANC>
 struct Requested {
-    uint4 e;             // thresh, i0, j0, i1 of the drawn edge bucket
+    uint4 e;             // first 16 bytes of the drawn edge record
     uint32_t j1, Ue;
-    uint2 v[MT];         // node-table records of the negatives' buckets
+    typename std::conditional<ANC, uint4, uint2>::type v[MT];
     uint32_t bkt[MT], Uv[MT];
 };
 
@@ -273,34 +302,41 @@ struct Resolved {
     uint32_t ia, ic, jm[MT];
 };
 
-template <int MT>
-__device__ __forceinline__ void hw_request(const EpochArgs& a, uint32_t s, uint32_t t, Requested<MT>& r) {
+template <int MT, bool ANC>
+__device__ __forceinline__ void hw_request(const EpochArgs& a, uint32_t s, uint32_t t, Requested<MT, ANC>& r) {
     Words W(s, t, a.tag, a.key);
     const uint64_t R = (uint64_t)W(0) | ((uint64_t)W(1) << 32);
     r.Ue = W(2);
-    const uint64_t bkt = alias_bucket(R, a.nnz);
-    r.e = __ldg(reinterpret_cast<const uint4*>(a.etab + bkt));
-    r.j1 = __ldg(&a.etab[bkt].j1);
+    load_edge(a, alias_bucket(R, a.nnz), r.e, r.j1);
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
         const uint64_t Rm = (uint64_t)W(3 + 3 * m) | ((uint64_t)W(4 + 3 * m) << 32);
         r.Uv[m] = W(5 + 3 * m);
         r.bkt[m] = (uint32_t)alias_bucket(Rm, a.n0);
-        r.v[m] = __ldg(&a.vtab[r.bkt[m]]);
+        if constexpr (ANC) r.v[m] = __ldg(&a.vtab_l[r.bkt[m]]);
+        else r.v[m] = __ldg(&a.vtab[r.bkt[m]]);
     }
 }
 
 template <int MT, bool ANC>
-__device__ __forceinline__ void hw_resolve(const EpochArgs& a, const Requested<MT>& r, Resolved<MT>& o) {
-    const bool keep = r.Ue < r.e.x;
-    const uint32_t i = keep ? r.e.y : r.e.w;
-    const uint32_t j = keep ? r.e.z : r.j1;
+__device__ __forceinline__ void hw_resolve(const EpochArgs& a, const Requested<MT, ANC>& r, Resolved<MT>& o) {
+    uint32_t i, j;
+    edge_pair(a, r.e, r.j1, r.Ue, i, j);
     o.ia = ANC ? __ldg(&a.anc[i]) : i;
     o.ic = ANC ? __ldg(&a.anc[j]) : j;
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
-        const uint32_t c = r.Uv[m] < r.v[m].x ? r.bkt[m] : r.v[m].y;
-        o.jm[m] = ANC ? __ldg(&a.anc[c]) : c;
+        if constexpr (ANC) o.jm[m] = r.Uv[m] < r.v[m].x ? r.v[m].y : r.v[m].z;
+        else o.jm[m] = r.Uv[m] < r.v[m].x ? r.bkt[m] : r.v[m].y;
+    }
+}
+
+// Level node table: the node table with both items mapped to the level.
+__global__ void k_level_nodes(const uint2* __restrict__ vtab, const uint32_t* __restrict__ anc, uint32_t n0,
+                              uint4* __restrict__ out) {
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < n0; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 v = vtab[b];
+        out[b] = make_uint4(v.x, anc[b], anc[v.y], 0u);
     }
 }
 
@@ -318,54 +354,79 @@ __device__ __forceinline__ void hw_advance(uint32_t& t, uint32_t& s, uint32_t T,
     }
 }
 
+// A thread's software pipeline over its samples 0, 1, 2, ...: while sample k
+// is gathered, computed and pushed, sample k + 2 is resolved (its records,
+// requested two samples earlier, have arrived; its ancestor lookups are
+// issued) and sample k + 4 is requested (Philox words, table loads).  Two
+// slots of each kind, used by sample parity, keep everything in registers.
+template <int MT, bool ANC>
+struct HwPipe {
+    Requested<MT, ANC> Q[2];
+    Resolved<MT> V[2];
+    uint32_t tQ[2], tV[2];  // epochs of the slots' samples
+    uint32_t t1, s1;        // next sample to request
+};
+
+template <int MT, bool ANC, int P>
+__device__ __forceinline__ void hw_step(const HogwildArgs& h, HwPipe<MT, ANC>& p, uint64_t k, uint64_t cnt) {
+    const EpochArgs& a = h.a;
+    const Resolved<MT> I = p.V[P];
+    const float2 ya = __ldcg(&a.Y[I.ia]), yc = __ldcg(&a.Y[I.ic]);
+    float2 ym[MT];
+#pragma unroll
+    for (int m = 0; m < MT; ++m) ym[m] = __ldcg(&a.Y[I.jm[m]]);
+    const float lr = __ldg(&h.lr_tab[p.tV[P]]);
+    if (k + 2 < cnt) {
+        hw_resolve<MT, ANC>(a, p.Q[P], p.V[P]);
+        p.tV[P] = p.tQ[P];
+    }
+    if (k + 4 < cnt) {
+        hw_request<MT, ANC>(a, p.s1, p.t1, p.Q[P]);
+        p.tQ[P] = p.t1;
+        hw_advance(p.t1, p.s1, h.T, h.nl);
+    }
+    const float2 fa = attract(a, ya, yc);
+    float Fx = fa.x, Fy = fa.y;
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+        if (I.jm[m] == I.ia || I.jm[m] == I.ic) continue;
+        const float2 fr = repel(a, ya, ym[m]);
+        Fx += fr.x;
+        Fy += fr.y;
+        hw_push(a.Y, I.jm[m], lr, -fr.x, -fr.y);
+    }
+    hw_push(a.Y, I.ia, lr, Fx, Fy);
+    hw_push(a.Y, I.ic, lr, -fa.x, -fa.y);
+}
+
+template <int MT, bool ANC, int P>
+__device__ __forceinline__ void hw_fill(const HogwildArgs& h, HwPipe<MT, ANC>& p) {
+    hw_request<MT, ANC>(h.a, p.s1, p.t1, p.Q[P]);
+    p.tQ[P] = p.t1;
+    hw_advance(p.t1, p.s1, h.T, h.nl);
+}
+
 // One thread's share of a run: elements g, g + T, g + 2T, ... of the sequence.
 template <int MT, bool ANC>
 __device__ __forceinline__ void hogwild_thread(const HogwildArgs& h, uint32_t g) {
-    const EpochArgs& a = h.a;
-    uint64_t left = (h.total - g + h.T - 1) / h.T;  // samples of this thread
-    if (left == 0) return;
-    uint32_t t1 = h.t_begin, s1 = g;                 // next sample to request
-    uint32_t tS = 0, tI = 0;
-    Requested<MT> S;
-    Resolved<MT> I;
-    hw_request<MT>(a, s1, t1, S);
-    tS = t1;
-    hw_advance(t1, s1, h.T, h.nl);
-    hw_resolve<MT, ANC>(a, S, I);
-    tI = tS;
-    if (left > 1) {
-        hw_request<MT>(a, s1, t1, S);
-        tS = t1;
-        hw_advance(t1, s1, h.T, h.nl);
+    const uint64_t cnt = (h.total - g + h.T - 1) / h.T;  // samples of this thread
+    if (cnt == 0) return;
+    HwPipe<MT, ANC> p;
+    p.t1 = h.t_begin;
+    p.s1 = g;
+    hw_fill<MT, ANC, 0>(h, p);                             // sample 0
+    if (cnt > 1) hw_fill<MT, ANC, 1>(h, p);                // sample 1
+    hw_resolve<MT, ANC>(h.a, p.Q[0], p.V[0]);
+    p.tV[0] = p.tQ[0];
+    if (cnt > 2) hw_fill<MT, ANC, 0>(h, p);                // sample 2
+    if (cnt > 1) {
+        hw_resolve<MT, ANC>(h.a, p.Q[1], p.V[1]);
+        p.tV[1] = p.tQ[1];
     }
-    for (; left > 0; --left) {
-        const float2 ya = __ldcg(&a.Y[I.ia]), yc = __ldcg(&a.Y[I.ic]);
-        float2 ym[MT];
-#pragma unroll
-        for (int m = 0; m < MT; ++m) ym[m] = __ldcg(&a.Y[I.jm[m]]);
-        const float lr = __ldg(&h.lr_tab[tI]);
-        Resolved<MT> I2 = I;
-        const uint32_t tI2 = tS;
-        if (left > 1) hw_resolve<MT, ANC>(a, S, I2);
-        if (left > 2) {
-            hw_request<MT>(a, s1, t1, S);
-            tS = t1;
-            hw_advance(t1, s1, h.T, h.nl);
-        }
-        const float2 fa = attract(a, ya, yc);
-        float Fx = fa.x, Fy = fa.y;
-#pragma unroll
-        for (int m = 0; m < MT; ++m) {
-            if (I.jm[m] == I.ia || I.jm[m] == I.ic) continue;
-            const float2 fr = repel(a, ya, ym[m]);
-            Fx += fr.x;
-            Fy += fr.y;
-            hw_push(a.Y, I.jm[m], lr, -fr.x, -fr.y);
-        }
-        hw_push(a.Y, I.ia, lr, Fx, Fy);
-        hw_push(a.Y, I.ic, lr, -fa.x, -fa.y);
-        I = I2;
-        tI = tI2;
+    if (cnt > 3) hw_fill<MT, ANC, 1>(h, p);                // sample 3
+    for (uint64_t k = 0; k < cnt; k += 2) {
+        hw_step<MT, ANC, 0>(h, p, k, cnt);
+        if (k + 1 < cnt) hw_step<MT, ANC, 1>(h, p, k + 1, cnt);
     }
 }
 
@@ -430,7 +491,8 @@ __global__ void __launch_bounds__(128) k_hogwild_batch(const HogwildArgs* __rest
 // assigned to jobs (graph, level) by a prefix sum of each job's block count;
 // each job's run c covers its own samples [c chunk, min(n_l, (c+1) chunk)).
 struct BatchJob {
-    const EdgeRec* etab;
+    const void* etab;
+    int packed;
     uint64_t nnz;
     const uint2* vtab;
     const uint32_t* anc;
@@ -458,6 +520,7 @@ __global__ void __launch_bounds__(256) k_epoch_batch(BatchArgs ba, uint32_t c) {
     const BatchJob J = ba.jobs[jb];
     EpochArgs a = ba.common;
     a.etab = J.etab;
+    a.packed = J.packed;
     a.nnz = J.nnz;
     a.vtab = J.vtab;
     a.n0 = J.n0;
@@ -602,6 +665,7 @@ static EpochArgs epoch_args(const drg_dmat* d, const uint32_t* anc, float2* Y, c
                             uint32_t level) {
     EpochArgs a{};
     a.etab = d->etab;
+    a.packed = d->erec_bytes == 16 ? 1 : 0;
     a.nnz = d->nnz;
     a.vtab = d->vtab;
     a.n0 = d->n;
@@ -656,6 +720,13 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
     h.T = (uint32_t)(bound < resident ? bound : resident);
     h.nl = nl;
     h.total = (uint64_t)(t_end - t_begin) * nl;
+    DBuf<uint4> vl;
+    if (a.anc) {
+        vl = DBuf<uint4>(ctx, a.n0);
+        DRG_LAUNCH(ctx, k_level_nodes, grid_for(a.n0, 256, (uint32_t)ctx->num_sms * 8), 256, 0, a.vtab, a.anc, a.n0,
+                   vl.p);
+        h.a.vtab_l = vl.p;
+    }
     ProfSpan span(ctx, DRG_PROF_EPOCH, h.total, 1);
     DRG_LAUNCH(ctx, k, (h.T + 127) / 128, 128, 0, h);
 }
@@ -666,6 +737,14 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
 // threads are resident together and the bound only tightens.
 static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& runs, uint64_t samples) {
     if (runs.empty()) return;
+    std::vector<DBuf<uint4>> tables;  // level node tables of the coarse runs
+    for (auto& h : runs) {
+        if (!h.a.anc) continue;
+        tables.emplace_back(ctx, h.a.n0);
+        DRG_LAUNCH(ctx, k_level_nodes, grid_for(h.a.n0, 256, (uint32_t)ctx->num_sms * 8), 256, 0, h.a.vtab, h.a.anc,
+                   h.a.n0, tables.back().p);
+        h.a.vtab_l = tables.back().p;
+    }
     const auto k = M == 5 ? k_hogwild_batch<5> : k_hogwild_batch<0>;
     int per_sm = 0;
     DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
@@ -987,6 +1066,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                 const float b = b_per_graph ? b_per_graph[g] : p.b;
                 BatchJob J{};
                 J.etab = s.d->etab;
+                J.packed = s.d->erec_bytes == 16 ? 1 : 0;
                 J.nnz = s.d->nnz;
                 J.vtab = s.d->vtab;
                 J.anc = level == 0 ? nullptr : s.h->anc[level];
@@ -1019,6 +1099,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                     HogwildArgs h{};
                     h.a = proto;
                     h.a.etab = J.etab;
+                    h.a.packed = J.packed;
                     h.a.nnz = J.nnz;
                     h.a.vtab = J.vtab;
                     h.a.n0 = J.n0;
