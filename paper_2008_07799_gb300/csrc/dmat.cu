@@ -17,11 +17,14 @@ __global__ void k_expand_rows(const uint64_t* __restrict__ rp, uint32_t n, uint3
 // taken BFS_THREADS at a time, their degrees prefix-summed, and every thread
 // walks an equal share of the concatenated adjacency lists.  The row is then
 // written sorted by node id straight from the bitmaps (the summary yields the
-// touched words in increasing order; a prefix sum of their popcounts gives
-// each word's output offset) -- no global sort.  Hop distances: for k = 2 a
-// node is at distance 1 exactly when it is in the source's adjacency, whose
-// nodes are located in the emitted row by binary search; for k > 2 the
-// block records each discovered node's level.
+// touched words in increasing order; each warp takes a contiguous range of
+// them and prefix-sums their popcounts with shuffles) -- no global sort.  Hop
+// distances: for k = 2 a node is at distance 1 exactly when it is in the
+// source's adjacency; after the row is written, each adjacency node finds its
+// word in the (shared) word list, whose output offsets were recorded, and
+// marks its entry (rows with more touched words than the shared list holds
+// search the emitted row instead); for k > 2 the block records each
+// discovered node's level.
 // Staged mode writes each row into a staging area at an offset reserved with
 // an atomic cursor (one traversal gives the counts and the rows); direct mode
 // writes at the final row offsets and is the fallback when the staging area
@@ -50,15 +53,24 @@ struct BfsArgs {
     uint8_t* out_dist;        // staging or final distance array
 };
 
-__device__ __forceinline__ void bfs_append(uint32_t v, bool isnew, uint32_t* list, uint32_t* s_len) {
+// Counts the warp's new nodes in s_len and, when `store`, appends them to the
+// discovered list (the last level's nodes are only counted).
+__device__ __forceinline__ void bfs_append(uint32_t v, bool isnew, uint32_t* list, uint32_t* s_len, bool store) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, isnew);
     if (!ballot) return;
     uint32_t base = 0;
     if (lane == (uint32_t)(__ffs(ballot) - 1)) base = atomicAdd(s_len, (uint32_t)__popc(ballot));
+    if (!store) return;
     base = __shfl_sync(0xFFFFFFFFu, base, __ffs(ballot) - 1);
     if (isnew) list[base + __popc(ballot & lanemask_lt())] = v;
 }
+
+constexpr int BFS_UNROLL = 4;          // adjacency loads in flight per thread
+constexpr uint32_t BFS_WL_SMEM = 4096;  // touched-word list (and offsets) in shared memory up to this length
+
+// Dynamic shared memory besides the bitmap: summary, word list, word offsets.
+static size_t bfs_extra_smem(uint32_t swords) { return (size_t)(swords + 2 * BFS_WL_SMEM) * 4; }
 
 // Marks v visited; true for the one thread that marked it first.  The first
 // bit set in a word also marks the word in the summary.
@@ -77,26 +89,35 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
     __shared__ uint64_t s_off[BFS_THREADS];
     __shared__ uint64_t s_start[BFS_THREADS];
     __shared__ uint64_t s_wt[BFS_THREADS / 32];
-    __shared__ uint32_t s_row, s_len;
+    __shared__ uint32_t s_row, s_len, s_next;
     __shared__ uint64_t s_base;
     __shared__ int s_skip;
+    __shared__ uint32_t s_wcnt[BFS_THREADS / 32];
     uint32_t* bm = a.gbitmaps ? a.gbitmaps + (size_t)blockIdx.x * a.words : dsm;
     uint32_t* summ = a.gbitmaps ? dsm : dsm + a.words;
+    uint32_t* s_wl = summ + a.swords;
+    uint32_t* s_woff = s_wl + BFS_WL_SMEM;  // output offset of each listed word, relative to the row
     uint32_t* list = a.lists + (size_t)blockIdx.x * a.n;
     uint32_t* wl = a.wlists + (size_t)blockIdx.x * a.words;
     uint8_t* dl = K2 ? nullptr : a.dlev + (size_t)blockIdx.x * a.n;
     for (uint32_t w = threadIdx.x; w < a.words; w += BFS_THREADS) bm[w] = 0;
     for (uint32_t w = threadIdx.x; w < a.swords; w += BFS_THREADS) summ[w] = 0;
+    if (threadIdx.x == 0) s_next = atomicAdd(a.next_row, 1u);
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) {
-            s_row = atomicAdd(a.next_row, 1u);
+            s_row = s_next;
             s_len = 0;
         }
         __syncthreads();
         const uint32_t row = s_row;
         if (row >= a.n) break;
-        if (threadIdx.x == 0) visit(bm, summ, row);
+        // the next row's index, taken now and stored once this row is done
+        uint32_t next = 0;
+        if (threadIdx.x == 0) {
+            next = atomicAdd(a.next_row, 1u);
+            visit(bm, summ, row);
+        }
         __syncthreads();
         const uint64_t ab = a.rp[row], ae = a.rp[row + 1];
         // level 1: the source's own adjacency
@@ -109,7 +130,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
                 isnew = visit(bm, summ, v);
                 if (!K2 && isnew) dl[v] = 1;
             }
-            bfs_append(v, isnew, list, &s_len);
+            bfs_append(v, isnew, list, &s_len, a.k > 1);
         }
         __syncthreads();
         uint32_t lo = 0, hi = s_len;
@@ -129,22 +150,29 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
                 s_start[threadIdx.x] = start;
                 __syncthreads();
                 const uint32_t cnt = (hi - c) < (uint32_t)BFS_THREADS ? (hi - c) : (uint32_t)BFS_THREADS;
-                for (uint64_t x0 = 0; x0 < tot; x0 += BFS_THREADS) {
-                    const uint64_t x = x0 + threadIdx.x;
-                    uint32_t v = 0;
-                    bool isnew = false;
-                    if (x < tot) {
-                        // owner: last frontier slot whose offset is <= x
-                        uint32_t lo2 = 0, hi2 = cnt;
-                        while (hi2 - lo2 > 1) {
-                            const uint32_t mid = (lo2 + hi2) >> 1;
-                            if (s_off[mid] <= x) lo2 = mid; else hi2 = mid;
+                const bool store = d < a.k;
+                for (uint64_t x0 = 0; x0 < tot; x0 += (uint64_t)BFS_UNROLL * BFS_THREADS) {
+                    uint32_t v[BFS_UNROLL];
+#pragma unroll
+                    for (int u = 0; u < BFS_UNROLL; ++u) {
+                        const uint64_t x = x0 + (uint64_t)u * BFS_THREADS + threadIdx.x;
+                        v[u] = 0xFFFFFFFFu;
+                        if (x < tot) {
+                            // owner: last frontier slot whose offset is <= x
+                            uint32_t lo2 = 0, hi2 = cnt;
+                            while (hi2 - lo2 > 1) {
+                                const uint32_t mid = (lo2 + hi2) >> 1;
+                                if (s_off[mid] <= x) lo2 = mid; else hi2 = mid;
+                            }
+                            v[u] = a.col[s_start[lo2] + (x - s_off[lo2])];
                         }
-                        v = a.col[s_start[lo2] + (x - s_off[lo2])];
-                        isnew = visit(bm, summ, v);
-                        if (!K2 && isnew) dl[v] = (uint8_t)d;
                     }
-                    bfs_append(v, isnew, list, &s_len);
+#pragma unroll
+                    for (int u = 0; u < BFS_UNROLL; ++u) {
+                        const bool isnew = v[u] != 0xFFFFFFFFu && visit(bm, summ, v[u]);
+                        if (!K2 && isnew) dl[v[u]] = (uint8_t)d;
+                        bfs_append(v[u], isnew, list, &s_len, store);
+                    }
                 }
                 __syncthreads();
             }
@@ -154,6 +182,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
         }
         const uint32_t total = s_len;
         if (threadIdx.x == 0) {
+            s_next = next;
             bm[row >> 5] &= ~(1u << (row & 31));  // the source is not its own neighbour
             a.counts[row] = total;
             uint64_t base = 0;
@@ -180,56 +209,90 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
         for (uint32_t s = s0; s < s1; ++s) mine += __popc(summ[s]);
         uint64_t nw;
         uint64_t pos = block_exclusive_scan<uint64_t, BFS_THREADS>(mine, s_wt, nw);
+        const bool wl_smem = nw <= BFS_WL_SMEM;
+        uint32_t* wlist = wl_smem ? s_wl : wl;
         for (uint32_t s = s0; s < s1; ++s) {
             uint32_t m = summ[s];
             summ[s] = 0;
             while (m) {
                 const uint32_t b = __ffs(m) - 1;
                 m &= m - 1;
-                wl[pos++] = 32 * s + b;
+                wlist[pos++] = 32 * s + b;
             }
         }
         __syncthreads();
         const bool emit = !s_skip;
-        // every touched word's bits, in order
-        uint64_t out = s_base;
-        for (uint64_t c = 0; c < nw; c += BFS_THREADS) {
-            const uint64_t idx = c + threadIdx.x;
+        // every touched word's bits, in order: warp w takes words [w0, w1)
+        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        constexpr uint32_t NW = BFS_THREADS / 32;
+        const uint64_t wper = (nw + NW - 1) / NW;
+        const uint64_t w0 = (uint64_t)warp * wper < nw ? (uint64_t)warp * wper : nw;
+        const uint64_t w1 = w0 + wper < nw ? w0 + wper : nw;
+        uint32_t cw = 0;
+        for (uint64_t x = w0 + lane; x < w1; x += 32) cw += __popc(bm[wlist[x]]);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) cw += __shfl_xor_sync(0xFFFFFFFFu, cw, off);
+        if (lane == 0) s_wcnt[warp] = cw;
+        __syncthreads();
+        uint64_t out = 0;  // relative to the row
+        for (uint32_t w = 0; w < warp; ++w) out += s_wcnt[w];
+        for (uint64_t x0 = w0; x0 < w1; x0 += 32) {
+            const uint64_t x = x0 + lane;
             uint32_t wi = 0, w = 0;
-            if (idx < nw) {
-                wi = wl[idx];
+            if (x < w1) {
+                wi = wlist[x];
                 w = bm[wi];
-                bm[wi] = 0;
             }
-            uint64_t tot;
-            uint64_t o = out + block_exclusive_scan<uint64_t, BFS_THREADS>((uint64_t)__popc(w), s_wt, tot);
+            const uint32_t c = __popc(w);
+            uint32_t incl = c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+                if (lane >= (uint32_t)off) incl += t;
+            }
+            uint64_t o = out + incl - c;
+            out += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (wl_smem && x < w1) s_woff[x] = (uint32_t)o;
             if (emit) {
                 while (w) {
                     const uint32_t b = __ffs(w) - 1;
                     w &= w - 1;
                     const uint32_t v = 32 * wi + b;
-                    a.out_col[o] = v;
-                    a.out_dist[o] = K2 ? (uint8_t)2 : dl[v];
+                    a.out_col[s_base + o] = v;
+                    a.out_dist[s_base + o] = K2 ? (uint8_t)2 : dl[v];
                     ++o;
                 }
             }
-            out += tot;
         }
+        __syncthreads();
         if (K2 && emit) {
-            __syncthreads();
-            // distance 1: the source's adjacency, located in the emitted (sorted)
-            // row by binary search
-            const uint32_t* rowc = a.out_col + s_base;
+            // distance 1: the source's adjacency
             for (uint64_t x = ab + threadIdx.x; x < ae; x += BFS_THREADS) {
                 const uint32_t v = a.col[x];
-                uint32_t lo3 = 0, hi3 = total;
-                while (lo3 < hi3) {
-                    const uint32_t mid = (lo3 + hi3) >> 1;
-                    if (rowc[mid] < v) lo3 = mid + 1; else hi3 = mid;
+                uint64_t at;
+                if (wl_smem) {
+                    // its word in the list, then its bit within the word
+                    uint32_t lo3 = 0, hi3 = (uint32_t)nw;
+                    while (lo3 < hi3) {
+                        const uint32_t mid = (lo3 + hi3) >> 1;
+                        if (s_wl[mid] < (v >> 5)) lo3 = mid + 1; else hi3 = mid;
+                    }
+                    at = s_woff[lo3] + __popc(bm[v >> 5] & ((1u << (v & 31)) - 1u));
+                } else {
+                    // in the emitted (sorted) row
+                    const uint32_t* rowc = a.out_col + s_base;
+                    uint32_t lo3 = 0, hi3 = total;
+                    while (lo3 < hi3) {
+                        const uint32_t mid = (lo3 + hi3) >> 1;
+                        if (rowc[mid] < v) lo3 = mid + 1; else hi3 = mid;
+                    }
+                    at = lo3;
                 }
-                a.out_dist[s_base + lo3] = 1;
+                a.out_dist[s_base + at] = 1;
             }
+            __syncthreads();
         }
+        for (uint64_t x = threadIdx.x; x < nw; x += BFS_THREADS) bm[wlist[x]] = 0;
         __syncthreads();
     }
 }
@@ -263,6 +326,10 @@ struct DegSq {
     }
 };
 
+// The distance array is padded to whole 16-byte words: k_row_Z reads rows in
+// aligned 16-byte pieces (bytes outside the row are masked).
+static size_t dist_bytes(uint64_t nnz) { return (size_t)((nnz + 15) / 16 + 1) * 16; }
+
 static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat* d) {
     const uint32_t n = g->n;
     d->rp = static_cast<uint64_t*>(dalloc(ctx, sizeof(uint64_t) * ((size_t)n + 1)));
@@ -270,7 +337,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         // NNG(v_i, 1) is the adjacency itself, already sorted by column
         d->nnz = g->nnz;
         d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (d->nnz ? d->nnz : 1)));
-        d->dist = static_cast<uint8_t*>(dalloc(ctx, d->nnz ? d->nnz : 1));
+        d->dist = static_cast<uint8_t*>(dalloc(ctx, dist_bytes(d->nnz)));
         d2d(ctx, d->rp, g->rp, (size_t)n + 1);
         d2d(ctx, d->col, g->col, d->nnz);
         DRG_LAUNCH(ctx, k_fill_u8, grid_for(d->nnz, 256, 65536), 256, 0, d->dist, d->nnz, (uint8_t)1);
@@ -280,10 +347,10 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     auto kern = k2 ? k_bfs<true> : k_bfs<false>;
     const uint32_t words = (n + 31) / 32;
     const uint32_t swords = (words + 31) / 32;
-    const size_t bm_bytes = (size_t)words * 4, sm_bytes = (size_t)swords * 4;
-    const bool smem_bm = bm_bytes + sm_bytes + 16384 <= (size_t)ctx->max_smem_optin;
-    DRG_CHECK(sm_bytes + 16384 <= (size_t)ctx->max_smem_optin, DRG_EUNSUPPORTED, "graph too large for the BFS");
-    const size_t dyn = (smem_bm ? bm_bytes : 0) + sm_bytes;
+    const size_t bm_bytes = (size_t)words * 4, extra = bfs_extra_smem(swords);
+    const bool smem_bm = bm_bytes + extra + 16384 <= (size_t)ctx->max_smem_optin;
+    DRG_CHECK(extra + 16384 <= (size_t)ctx->max_smem_optin, DRG_EUNSUPPORTED, "graph too large for the BFS");
+    const size_t dyn = (smem_bm ? bm_bytes : 0) + extra;
     DRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BFS_THREADS, dyn));
@@ -345,7 +412,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     DRG_CHECK(d->nnz < (1ull << 32), DRG_EUNSUPPORTED, "distance matrix has 2^32 entries or more");
     const bool overflowed = read1(ctx, overflow.p) != 0;
     d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (d->nnz ? d->nnz : 1)));
-    d->dist = static_cast<uint8_t*>(dalloc(ctx, d->nnz ? d->nnz : 1));
+    d->dist = static_cast<uint8_t*>(dalloc(ctx, dist_bytes(d->nnz)));
     if (!overflowed) {
         DRG_LAUNCH(ctx, k_unstage, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, row_off.p,
                    d->rp, n, scol.p, sdist.p, d->col, d->dist);
@@ -368,61 +435,139 @@ struct Gauss {
     float g[16];
 };
 
+// Bytes [lo, hi) of a 16-byte piece, as a mask per 32-bit word q.
+__device__ __forceinline__ uint32_t byte_mask(uint32_t q, uint32_t lo, uint32_t hi) {
+    const uint32_t b0 = 4 * q;
+    const uint32_t a = lo > b0 ? (lo - b0 < 4 ? lo - b0 : 4) : 0;   // bytes cut at the front
+    const uint32_t e = hi > b0 ? (hi - b0 < 4 ? hi - b0 : 4) : 0;   // bytes kept up to here
+    const uint64_t keep_hi = (1ull << (8 * e)) - 1;
+    const uint64_t cut_lo = (1ull << (8 * a)) - 1;
+    return (uint32_t)(keep_hi & ~cut_lo);
+}
+
 // Z_i = sum over d = 1..k of count_i(d) * g(d), in that order, FP32
-// correctly rounded with no fused multiply-add (one warp per row).
+// correctly rounded with no fused multiply-add.  One warp per row; each lane
+// reads aligned 16-byte pieces of the row's distances and counts the bytes
+// of each class with byte-wise compares.
 __global__ void k_row_Z(const uint64_t* __restrict__ rp, const uint8_t* __restrict__ dist, uint32_t n, uint32_t k,
                         Gauss gs, float* __restrict__ Z) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t i = warp0; i < n; i += nwarps) {
-        // class counts by warp ballots: every lane ends with the same totals
         uint32_t c[15];
 #pragma unroll
         for (int d = 0; d < 15; ++d) c[d] = 0;
         const uint64_t e0 = rp[i], e1 = rp[i + 1];
-        for (uint64_t b = e0; b < e1; b += 32) {
-            const uint64_t e = b + lane;
-            const uint32_t dd = e < e1 ? dist[e] : 0u;
+        for (uint64_t b = (e0 & ~15ull) + 16 * lane; b < e1; b += 512) {
+            const uint4 v = *reinterpret_cast<const uint4*>(dist + b);
+            const uint32_t lo = b < e0 ? (uint32_t)(e0 - b) : 0u;
+            const uint32_t hi = e1 - b < 16 ? (uint32_t)(e1 - b) : 16u;
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int d = 0; d < 15; ++d)
-                if ((uint32_t)d < k) c[d] += __popc(__ballot_sync(0xFFFFFFFFu, dd == (uint32_t)(d + 1)));
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t m = byte_mask(q, lo, hi);
+#pragma unroll
+                for (int d = 0; d < 15; ++d)
+                    if ((uint32_t)d < k) c[d] += __popc(__vcmpeq4(w[q], (uint32_t)(d + 1) * 0x01010101u) & m) >> 3;
+            }
         }
         float z = 0.f;
 #pragma unroll
-        for (int d = 0; d < 15; ++d)
-            if ((uint32_t)d < k) z = __fadd_rn(z, __fmul_rn(__uint2float_rn(c[d]), gs.g[d]));
+        for (int d = 0; d < 15; ++d) {
+            if ((uint32_t)d < k) {
+                uint32_t t = c[d];
+#pragma unroll
+                for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+                z = __fadd_rn(z, __fmul_rn(__uint2float_rn(t), gs.g[d]));
+            }
+        }
         if (lane == 0) Z[i] = z;
     }
 }
 
 // q_e = floor((fl(g/Z_i) + fl(g/Z_j)) * 2^30).
-__global__ void k_quantise(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
-                           const uint8_t* __restrict__ dist, const float* __restrict__ Z, Gauss gs, uint64_t nnz,
-                           uint32_t* __restrict__ q) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += (uint64_t)gridDim.x * blockDim.x) {
-        const float gd = gs.g[dist[e] - 1];
-        const float s = __fadd_rn(__fdiv_rn(gd, Z[esrc[e]]), __fdiv_rn(gd, Z[col[e]]));
-        q[e] = __float2uint_rz(__fmul_rn(s, 1073741824.0f));
+__device__ __forceinline__ uint32_t quantise1(float gd, float zi, float zj) {
+    const float s = __fadd_rn(__fdiv_rn(gd, zi), __fdiv_rn(gd, zj));
+    return __float2uint_rz(__fmul_rn(s, 1073741824.0f));
+}
+
+// q for every entry, 4 consecutive entries per thread, and the row sums r_i
+// = sum of the row's q (exact): along the entries the rows never decrease,
+// so a thread adds any run of its own entries that ends inside its four, and
+// the warp sums the open runs by row (segmented suffix sums over the lanes)
+// and adds each row's total with one atomic.  r must start at zero.
+__global__ void k_quantise_r(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
+                             const uint8_t* __restrict__ dist, const float* __restrict__ Z, Gauss gs, uint64_t nnz,
+                             uint32_t* __restrict__ q, unsigned long long* __restrict__ r) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nv = (nnz + 3) / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x - lane; w0 < nv; w0 += stride) {
+        const uint64_t v = w0 + lane;
+        uint32_t key = 0xFFFFFFFFu;
+        unsigned long long sum = 0;
+        if (v < nv) {
+            const uint64_t e = 4 * v;
+            const uint32_t cnt = nnz - e < 4 ? (uint32_t)(nnz - e) : 4u;
+            uint32_t ii[4], jj[4], dd[4], qq[4];
+            if (cnt == 4) {
+                const uint4 a4 = __ldg(reinterpret_cast<const uint4*>(esrc + e));
+                const uint4 b4 = __ldg(reinterpret_cast<const uint4*>(col + e));
+                const uint32_t dw = __ldg(reinterpret_cast<const uint32_t*>(dist + e));
+                ii[0] = a4.x; ii[1] = a4.y; ii[2] = a4.z; ii[3] = a4.w;
+                jj[0] = b4.x; jj[1] = b4.y; jj[2] = b4.z; jj[3] = b4.w;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) dd[t] = (dw >> (8 * t)) & 0xFFu;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const bool ok = (uint32_t)t < cnt;
+                    ii[t] = ok ? esrc[e + t] : 0u;
+                    jj[t] = ok ? col[e + t] : 0u;
+                    dd[t] = ok ? dist[e + t] : 1u;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) qq[t] = quantise1(gs.g[dd[t] - 1], Z[ii[t]], Z[jj[t]]);
+            if (cnt == 4) {
+                *reinterpret_cast<uint4*>(q + e) = make_uint4(qq[0], qq[1], qq[2], qq[3]);
+            } else {
+                for (uint32_t t = 0; t < cnt; ++t) q[e + t] = qq[t];
+            }
+            key = ii[0];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if ((uint32_t)t >= cnt) break;
+                if (ii[t] != key) {
+                    atomicAdd(&r[key], sum);
+                    key = ii[t];
+                    sum = 0;
+                }
+                sum += qq[t];
+            }
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t ok = __shfl_down_sync(0xFFFFFFFFu, key, off);
+            const unsigned long long ov = __shfl_down_sync(0xFFFFFFFFu, sum, off);
+            if (lane + off < 32 && ok == key) sum += ov;
+        }
+        const uint32_t pk = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+        if (key != 0xFFFFFFFFu && (lane == 0 || pk != key)) atomicAdd(&r[key], sum);
     }
 }
 
-// r_i = sum of q over row i (exact, one warp per row); also the maximum.
-__global__ void k_row_r(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ q, uint32_t n,
-                        uint64_t* __restrict__ r, unsigned long long* __restrict__ rmax) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t i = warp0; i < n; i += nwarps) {
-        uint64_t s = 0;
-        for (uint64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) s += q[e];
+__global__ void k_rmax(const uint64_t* __restrict__ r, uint32_t n, unsigned long long* __restrict__ rmax) {
+    unsigned long long m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        m = r[i] > m ? r[i] : m;
 #pragma unroll
-        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
-        if (lane == 0) {
-            r[i] = s;
-            atomicMax(rmax, (unsigned long long)s);
-        }
+    for (int off = 16; off; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, m, off);
+        m = o > m ? o : m;
     }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(rmax, m);
 }
 
 __global__ void k_shift_u32(const uint64_t* __restrict__ r, uint32_t n, uint32_t s, uint32_t* __restrict__ out) {
@@ -439,24 +584,169 @@ __global__ void k_shift_u32(const uint64_t* __restrict__ r, uint32_t n, uint32_t
 // Dl < S) gives every light the number of heavies before it -- its alias is
 // the next heavy -- and every heavy the number of lights before it, from
 // which its own remaining mass follows.
-struct LightDeficit {
-    const uint32_t* q; const uint32_t* L; uint64_t N, W;
-    __device__ __forceinline__ u128 operator()(size_t x) const { return (u128)(W - (uint64_t)q[L[x]] * N); }
-};
-struct HeavyExcess {
-    const uint32_t* q; const uint32_t* H; uint64_t N, W;
-    __device__ __forceinline__ u128 operator()(size_t y) const { return (u128)((uint64_t)q[H[y]] * N - W); }
-};
-struct LightFlag {
-    const uint32_t* q; uint64_t N, W;
-    __device__ __forceinline__ uint32_t operator()(size_t i) const { return (uint64_t)q[i] * N < W ? 1u : 0u; }
+//
+// One scan over the items in index order carries (lights so far, their
+// deficit, the heavies' excess): its exclusive prefix at item i gives i's
+// place in the light or heavy list and its Dl or S value, written straight
+// into the lists.
+
+// Running sums of the split scan.
+struct SplitAcc {
+    u128 D, E;     // lights' deficit, heavies' excess
+    uint64_t c;    // lights
+    SplitAcc() = default;  // trivial, so that it can live in shared memory
+    __host__ __device__ SplitAcc(int) : D(0), E(0), c(0) {}  // from 0
+    __host__ __device__ SplitAcc& operator+=(const SplitAcc& o) {
+        D += o.D;
+        E += o.E;
+        c += o.c;
+        return *this;
+    }
+    __host__ __device__ SplitAcc operator+(const SplitAcc& o) const { SplitAcc r = *this; r += o; return r; }
+    __host__ __device__ SplitAcc operator-(const SplitAcc& o) const {
+        SplitAcc r = *this;
+        r.D -= o.D;
+        r.E -= o.E;
+        r.c -= o.c;
+        return r;
+    }
 };
 
-__global__ void k_split(const uint32_t* __restrict__ q, const uint32_t* __restrict__ lpos, uint64_t N, uint64_t W,
-                        uint32_t* __restrict__ L, uint32_t* __restrict__ H) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-        if ((uint64_t)q[i] * N < W) L[lpos[i]] = (uint32_t)i;
-        else H[i - lpos[i]] = (uint32_t)i;
+__device__ __forceinline__ SplitAcc shfl_up(const SplitAcc& v, int d) {
+    SplitAcc r;
+    r.D = shfl_up(v.D, d);
+    r.E = shfl_up(v.E, d);
+    r.c = shfl_up(v.c, d);
+    return r;
+}
+
+__device__ __forceinline__ SplitAcc split_item(uint32_t qi, uint64_t N, uint64_t W) {
+    SplitAcc r(0);
+    const uint64_t a = (uint64_t)qi * N;
+    if (a < W) {
+        r.D = (u128)(W - a);
+        r.c = 1;
+    } else {
+        r.E = (u128)(a - W);
+    }
+    return r;
+}
+
+struct SplitLoad {
+    const uint32_t* q;
+    uint64_t N, W;
+    __device__ __forceinline__ SplitAcc operator()(size_t i) const { return split_item(q[i], N, W); }
+};
+
+// Tiles of SPLIT_TILE items; the down pass walks a tile in SPLIT_SUB-item
+// pieces (8 consecutive items per thread).
+constexpr int SPLIT_THREADS = 256, SPLIT_SUB = 2048, SPLIT_TILE = 4 * SPLIT_SUB;
+
+__device__ __forceinline__ SplitAcc warp_sum(SplitAcc v) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        SplitAcc o;
+        o.D = ((u128)__shfl_xor_sync(0xFFFFFFFFu, (uint64_t)(v.D >> 64), off) << 64) |
+              __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)v.D, off);
+        o.E = ((u128)__shfl_xor_sync(0xFFFFFFFFu, (uint64_t)(v.E >> 64), off) << 64) |
+              __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)v.E, off);
+        o.c = __shfl_xor_sync(0xFFFFFFFFu, v.c, off);
+        v += o;
+    }
+    return v;
+}
+
+// Per-tile sums (16-byte loads, 32 items per thread).
+__global__ void __launch_bounds__(SPLIT_THREADS) k_split_reduce(const uint32_t* __restrict__ q, uint64_t N,
+                                                                uint64_t W, SplitAcc* __restrict__ sums) {
+    __shared__ SplitAcc wt[SPLIT_THREADS / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * SPLIT_TILE;
+    SplitAcc acc(0);
+#pragma unroll
+    for (int r = 0; r < SPLIT_TILE / 4 / SPLIT_THREADS; ++r) {
+        const uint64_t i = base + 4 * ((uint64_t)r * SPLIT_THREADS + threadIdx.x);
+        if (i + 4 <= N) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(q + i));
+            acc += split_item(v.x, N, W);
+            acc += split_item(v.y, N, W);
+            acc += split_item(v.z, N, W);
+            acc += split_item(v.w, N, W);
+        } else {
+            for (uint64_t t = i; t < N && t < i + 4; ++t) acc += split_item(q[t], N, W);
+        }
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SplitAcc t(0);
+        for (int w = 0; w < SPLIT_THREADS / 32; ++w) t += wt[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// Lists: L[x] = x-th light, Dl[x] = deficit of the lights before it; H[y] =
+// y-th heavy, S[y] = excess of the heavies up to and including it.  Each
+// piece's lights and heavies are gathered in shared memory (lights first)
+// and written out in order.
+constexpr size_t SPLIT_DOWN_SMEM = (size_t)SPLIT_SUB * (4 + 4 + 16);
+
+__global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __restrict__ q, uint64_t N, uint64_t W,
+                                                              const SplitAcc* __restrict__ tile_pre,
+                                                              uint32_t* __restrict__ L, u128* __restrict__ Dl,
+                                                              uint32_t* __restrict__ H, u128* __restrict__ S) {
+    extern __shared__ __align__(16) unsigned char split_smem[];
+    u128* s_val = reinterpret_cast<u128*>(split_smem);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(split_smem + (size_t)SPLIT_SUB * 16);
+    uint32_t* qs = s_idx + SPLIT_SUB;
+    __shared__ SplitAcc wt[SPLIT_THREADS / 32];
+    constexpr int IT = SPLIT_SUB / SPLIT_THREADS;
+    const uint64_t base = (uint64_t)blockIdx.x * SPLIT_TILE;
+    SplitAcc run0 = tile_pre[blockIdx.x];  // everything before this piece
+    for (uint64_t sb = base; sb < base + SPLIT_TILE && sb < N; sb += SPLIT_SUB) {
+        const uint32_t cnt = N - sb < (uint64_t)SPLIT_SUB ? (uint32_t)(N - sb) : (uint32_t)SPLIT_SUB;
+#pragma unroll
+        for (int j = 0; j < IT; ++j) {
+            const uint32_t t = j * SPLIT_THREADS + threadIdx.x;
+            qs[t] = t < cnt ? q[sb + t] : 0u;
+        }
+        __syncthreads();
+        const uint32_t t0 = threadIdx.x * IT;
+        SplitAcc mine(0);
+#pragma unroll
+        for (int j = 0; j < IT; ++j)
+            if (t0 + j < cnt) mine += split_item(qs[t0 + j], N, W);
+        SplitAcc bt;
+        SplitAcc run = block_exclusive_scan<SplitAcc, SPLIT_THREADS>(mine, wt, bt);
+        const uint32_t nl = (uint32_t)bt.c;  // lights of the piece
+#pragma unroll
+        for (int j = 0; j < IT; ++j) {
+            const uint32_t t = t0 + j;
+            if (t >= cnt) break;
+            const SplitAcc it = split_item(qs[t], N, W);
+            if (it.c) {
+                s_idx[run.c] = (uint32_t)(sb + t);
+                s_val[run.c] = run0.D + run.D;
+            } else {
+                const uint32_t h = nl + (t - (uint32_t)run.c);
+                s_idx[h] = (uint32_t)(sb + t);
+                s_val[h] = run0.E + run.E + it.E;
+            }
+            run += it;
+        }
+        __syncthreads();
+        const uint64_t xb = run0.c, yb = sb - run0.c;  // lights and heavies before the piece
+        for (uint32_t t = threadIdx.x; t < cnt; t += SPLIT_THREADS) {
+            if (t < nl) {
+                L[xb + t] = s_idx[t];
+                Dl[xb + t] = s_val[t];
+            } else {
+                H[yb + t - nl] = s_idx[t];
+                S[yb + t - nl] = s_val[t];
+            }
+        }
+        run0 += bt;
+        __syncthreads();
     }
 }
 
@@ -481,39 +771,6 @@ __global__ void k_merge_partition(const u128* __restrict__ A, uint64_t nA, const
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= tiles; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t d = t * MERGE_TILE < total ? t * MERGE_TILE : total;
         part[t] = merge_path(A, nA, B, nB, d);
-    }
-}
-
-__global__ void __launch_bounds__(MERGE_THREADS) k_merge_ranks(const u128* __restrict__ A, uint64_t nA,
-                                                               const u128* __restrict__ B, uint64_t nB,
-                                                               const uint64_t* __restrict__ part,
-                                                               uint32_t* __restrict__ a_rank,
-                                                               uint32_t* __restrict__ b_rank) {
-    __shared__ u128 s[MERGE_TILE];
-    const uint64_t total = nA + nB;
-    const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_TILE;
-    const uint64_t d1 = d0 + MERGE_TILE < total ? d0 + MERGE_TILE : total;
-    const uint64_t x0 = part[blockIdx.x], x1 = part[blockIdx.x + 1], y0 = d0 - x0, y1 = d1 - x1;
-    const uint32_t na = (uint32_t)(x1 - x0), nb = (uint32_t)(y1 - y0);
-    for (uint32_t t = threadIdx.x; t < na; t += MERGE_THREADS) s[t] = A[x0 + t];
-    for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) s[na + t] = B[y0 + t];
-    __syncthreads();
-    const u128* As = s;
-    const u128* Bs = s + na;
-    const uint32_t dl = threadIdx.x * MERGE_ITEMS;
-    if (dl >= na + nb) return;
-    uint32_t xa = (uint32_t)merge_path(As, na, Bs, nb, dl);
-    uint32_t yb = dl - xa;
-#pragma unroll
-    for (int it = 0; it < MERGE_ITEMS; ++it) {
-        if (xa + yb >= na + nb) break;
-        if (xa < na && (yb >= nb || As[xa] < Bs[yb])) {
-            a_rank[x0 + xa] = (uint32_t)(y0 + yb);
-            ++xa;
-        } else {
-            b_rank[y0 + yb] = (uint32_t)(x0 + xa);
-            ++yb;
-        }
     }
 }
 
@@ -558,30 +815,62 @@ __device__ __forceinline__ uint32_t frac32(uint64_t own, const InvDiv& D) {
     return (uint32_t)q1;
 }
 
-__global__ void k_alias_lights(const uint32_t* __restrict__ q, const uint32_t* __restrict__ L, uint64_t nL,
-                               const uint32_t* __restrict__ H, const uint32_t* __restrict__ a_rank, uint64_t N,
-                               uint64_t W, InvDiv D, uint32_t* __restrict__ thresh, uint32_t* __restrict__ alias) {
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nL; x += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t b = L[x];
-        thresh[b] = frac32((uint64_t)q[b] * N, D);
-        alias[b] = H[a_rank[x]];
-    }
-}
+struct MergeArgs {
+    const u128* Dl;          // [nL + 1] (Dl[nL] = total deficit)
+    const u128* S;           // [nH]
+    const uint32_t* L;
+    const uint32_t* H;
+    const uint32_t* q;
+    uint64_t nL, nH, N, W;
+    InvDiv D;
+    const uint64_t* part;    // [tiles + 1] merge-path splits
+    uint32_t* thresh;
+    uint32_t* alias;
+};
 
-__global__ void k_alias_heavies(const uint32_t* __restrict__ H, uint64_t nH, const u128* __restrict__ S,
-                                const u128* __restrict__ Dl, const uint32_t* __restrict__ b_rank, uint64_t W,
-                                InvDiv D, uint32_t* __restrict__ thresh, uint32_t* __restrict__ alias) {
-    for (uint64_t y = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; y < nH; y += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t b = H[y];
-        const uint64_t own = (uint64_t)(S[y] + (u128)W - Dl[b_rank[y]]);
-        // exact totals make the last heavy full; the index guard only keeps a
-        // violated invariant from reading past H
-        if (own >= W || y + 1 >= nH) {
-            thresh[b] = 0xFFFFFFFFu;
-            alias[b] = b;
+// The merge, tile by tile, writing each item's table entry as it is placed:
+// light x placed after y heavies -> alias H[y], thresh floor(a 2^32 / W);
+// heavy y placed after x lights -> its own mass S[y] + W - Dl[x] fills the
+// bucket (thresh all ones, alias itself) or takes the next heavy as alias.
+__global__ void __launch_bounds__(MERGE_THREADS) k_merge_alias(MergeArgs m) {
+    __shared__ u128 s[MERGE_TILE];
+    const uint64_t total = m.nL + m.nH;
+    const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_TILE;
+    const uint64_t d1 = d0 + MERGE_TILE < total ? d0 + MERGE_TILE : total;
+    const uint64_t x0 = m.part[blockIdx.x], x1 = m.part[blockIdx.x + 1], y0 = d0 - x0, y1 = d1 - x1;
+    const uint32_t na = (uint32_t)(x1 - x0), nb = (uint32_t)(y1 - y0);
+    for (uint32_t t = threadIdx.x; t < na; t += MERGE_THREADS) s[t] = m.Dl[x0 + t];
+    for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) s[na + t] = m.S[y0 + t];
+    __syncthreads();
+    const u128* As = s;
+    const u128* Bs = s + na;
+    const uint32_t dl = threadIdx.x * MERGE_ITEMS;
+    if (dl >= na + nb) return;
+    uint32_t xa = (uint32_t)merge_path(As, na, Bs, nb, dl);
+    uint32_t yb = dl - xa;
+#pragma unroll
+    for (int it = 0; it < MERGE_ITEMS; ++it) {
+        if (xa + yb >= na + nb) break;
+        if (xa < na && (yb >= nb || As[xa] < Bs[yb])) {
+            const uint64_t x = x0 + xa, y = y0 + yb;  // light x, y heavies before it
+            const uint32_t b = m.L[x];
+            m.thresh[b] = frac32((uint64_t)m.q[b] * m.N, m.D);
+            m.alias[b] = y < m.nH ? m.H[y] : b;  // y < nH whenever the totals are exact
+            ++xa;
         } else {
-            thresh[b] = frac32(own, D);
-            alias[b] = H[y + 1];
+            const uint64_t x = x0 + xa, y = y0 + yb;  // heavy y, x lights before it
+            const uint32_t b = m.H[y];
+            const uint64_t own = (uint64_t)(Bs[yb] + (u128)m.W - m.Dl[x]);
+            // exact totals make the last heavy full; the index guard only keeps
+            // a violated invariant from reading past H
+            if (own >= m.W || y + 1 >= m.nH) {
+                m.thresh[b] = 0xFFFFFFFFu;
+                m.alias[b] = b;
+            } else {
+                m.thresh[b] = frac32(own, m.D);
+                m.alias[b] = m.H[y + 1];
+            }
+            ++yb;
         }
     }
 }
@@ -597,8 +886,6 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, 
     DRG_CHECK(N > 0 && N < (1ull << 32), DRG_EUNSUPPORTED, "alias table size must be in [1, 2^32)");
     DBuf<uint64_t> Wd(ctx, 1);
     {
-        DBuf<uint64_t> tmp(ctx, 1);
-        // reduce via the scan machinery (exclusive output discarded in a small buffer per block)
         DBuf<uint64_t> sums(ctx, (N + ScanShape<uint64_t>::TILE - 1) / ScanShape<uint64_t>::TILE);
         const uint32_t nb = (uint32_t)sums.n;
         DRG_LAUNCH(ctx, (k_scan_reduce<uint64_t, Sum64>), nb, 256, 0, Sum64{q}, (size_t)N, sums.p);
@@ -606,28 +893,29 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, 
     }
     const uint64_t W = read1(ctx, Wd.p);
     if (W == 0) return false;
-    DBuf<uint32_t> lpos(ctx, N), nLd(ctx, 1);
-    scan<uint32_t>(ctx, LightFlag{q, N, W}, N, lpos.p, false, nLd.p);
-    const uint64_t nL = read1(ctx, nLd.p);
-    const uint64_t nH = N - nL;
+    // split scan: tile sums, their exclusive prefix, then the lists
+    const uint64_t stiles = (N + SPLIT_TILE - 1) / SPLIT_TILE;
+    DBuf<SplitAcc> tsum(ctx, stiles + 1);
+    DRG_LAUNCH(ctx, k_split_reduce, (uint32_t)stiles, SPLIT_THREADS, 0, q, N, W, tsum.p);
+    scan<SplitAcc>(ctx, LoadArr<SplitAcc>{tsum.p}, stiles, tsum.p, false, tsum.p + stiles);
+    SplitAcc tot(0);
+    d2h(ctx, &tot, tsum.p + stiles, 1);
+    sync(ctx);
+    const uint64_t nL = tot.c, nH = N - nL;
     DBuf<uint32_t> L(ctx, nL), H(ctx, nH);
-    const uint32_t g = grid_for(N, 256, 65536);
-    DRG_LAUNCH(ctx, k_split, g, 256, 0, q, lpos.p, N, W, L.p, H.p);
-    lpos.reset();
     DBuf<u128> Dl(ctx, nL + 1), S(ctx, nH);
-    scan<u128>(ctx, LightDeficit{q, L.p, N, W}, nL, Dl.p, false, Dl.p + nL);
-    scan<u128>(ctx, HeavyExcess{q, H.p, N, W}, nH, S.p, true, nullptr);
-    DBuf<uint32_t> a_rank(ctx, nL), b_rank(ctx, nH);
+    DRG_CUDA(cudaFuncSetAttribute(k_split_down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPLIT_DOWN_SMEM));
+    DRG_LAUNCH(ctx, k_split_down, (uint32_t)stiles, SPLIT_THREADS, SPLIT_DOWN_SMEM, q, N, W, tsum.p, L.p, Dl.p, H.p,
+               S.p);
+    h2d(ctx, Dl.p + nL, &tot.D, 1);
+    tsum.reset();
+    // merge, writing the table
     const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
-    {
-        DBuf<uint64_t> part(ctx, tiles + 1);
-        DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, Dl.p, nL, S.p, nH, tiles, part.p);
-        DRG_LAUNCH(ctx, k_merge_ranks, (uint32_t)tiles, MERGE_THREADS, 0, Dl.p, nL, S.p, nH, part.p, a_rank.p,
-                   b_rank.p);
-    }
-    DRG_LAUNCH(ctx, k_alias_lights, grid_for(nL, 256, 65536), 256, 0, q, L.p, nL, H.p, a_rank.p, N, W, make_invdiv(W), thresh, alias);
-    DRG_LAUNCH(ctx, k_alias_heavies, grid_for(nH, 256, 65536), 256, 0, H.p, nH, S.p, Dl.p, b_rank.p, W, make_invdiv(W), thresh,
-               alias);
+    DBuf<uint64_t> part(ctx, tiles + 1);
+    DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, Dl.p, nL, S.p, nH, tiles, part.p);
+    MergeArgs m{Dl.p, S.p, L.p, H.p, q, nL, nH, N, W, make_invdiv(W), part.p, thresh, alias};
+    DRG_LAUNCH(ctx, k_merge_alias, (uint32_t)tiles, MERGE_THREADS, 0, m);
+    sync(ctx);  // `tot` is a host value read by an asynchronous copy above
     return true;
 }
 
@@ -694,10 +982,12 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
         DRG_LAUNCH(ctx, k_row_Z, gw, 256, 0, d->rp, d->dist, n, k, gs, d->Z);
         DBuf<uint32_t> esrc(ctx, nnz);
         DRG_LAUNCH(ctx, k_expand_rows, gw, 256, 0, d->rp, n, esrc.p);
-        DRG_LAUNCH(ctx, k_quantise, grid_for(nnz, 256, 65536), 256, 0, esrc.p, d->col, d->dist, d->Z, gs, nnz, d->q);
+        DRG_CUDA(cudaMemsetAsync(d->r, 0, sizeof(uint64_t) * n, ctx->stream));
+        DRG_LAUNCH(ctx, k_quantise_r, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist, d->Z, gs, nnz,
+                   d->q, reinterpret_cast<unsigned long long*>(d->r));
         DBuf<unsigned long long> rmax(ctx, 1);
         DRG_CUDA(cudaMemsetAsync(rmax.p, 0, 8, ctx->stream));
-        DRG_LAUNCH(ctx, k_row_r, gw, 256, 0, d->rp, d->q, n, d->r, rmax.p);
+        DRG_LAUNCH(ctx, k_rmax, grid_for(n, 256, (uint32_t)ctx->num_sms * 8), 256, 0, d->r, n, rmax.p);
         const uint64_t mx = read1(ctx, rmax.p);
         const int bits = bitlen(mx);
         d->shift = bits > 32 ? (uint32_t)(bits - 32) : 0u;

@@ -69,7 +69,7 @@ struct LoadConv {
 template <typename T>
 struct ScanShape {
     static constexpr int THREADS = 256;
-    static constexpr int ITEMS = sizeof(T) >= 16 ? 4 : 8;
+    static constexpr int ITEMS = sizeof(T) > 16 ? 2 : (sizeof(T) == 16 ? 4 : 8);  // tile <= 32 KB of shared memory
     static constexpr int TILE = THREADS * ITEMS;
 };
 

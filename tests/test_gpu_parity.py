@@ -271,13 +271,14 @@ def _quality(orc, rp, col, Y):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_whole_run_grid32(drg, ctx, orc, mode):
     # 32 x 32 grid, k = 3, M = 5, 500 epochs, lr from 1.0, single level, b = 3.
-    # Runs diverge chaotically from the oracle's, so quality is compared as a
-    # statistic over seeds: medians within 1 % plus twice the oracle's
-    # seed-to-seed spread of the median.
+    # Runs diverge chaotically from the oracle's and end in one of a few
+    # basins (an unfolded grid, NP ~ .68, or a folded one, NP ~ .47-.55, on
+    # both sides), so quality is compared as a statistic over seeds: means
+    # within 1 % plus twice the combined standard error of the two means.
     g = _graphs()["grid32"]
     orp, ocol = _oracle_csr(orc, g)
     nps, sts, onps, osts = [], [], [], []
-    for seed in range(7):
+    for seed in range(12):
         op = orc.Params(k=3, M=5, epochs=500, b=3.0, mode=mode, multilevel=False, seed=seed)
         a, b_ = _quality(orc, orp, ocol, orc.run(*g, op))
         onps.append(a)
@@ -294,11 +295,14 @@ def test_whole_run_grid32(drg, ctx, orc, mode):
         nps.append(a)
         sts.append(b_)
 
-    def spread(x):
-        return 1.2533 * np.std(x) / np.sqrt(len(x))   # standard error of a median
+    def se(x):
+        return np.std(x, ddof=1) / np.sqrt(len(x))   # standard error of a mean
 
-    assert abs(np.median(nps) - np.median(onps)) <= 0.01 * np.median(onps) + 2 * spread(onps), (nps, onps)
-    assert abs(np.median(sts) - np.median(osts)) <= 0.01 * np.median(osts) + 2 * spread(osts), (sts, osts)
+    def close(a, b):
+        return abs(np.mean(a) - np.mean(b)) <= 0.01 * np.mean(b) + 2 * np.hypot(se(a), se(b))
+
+    assert close(nps, onps), (nps, onps)
+    assert close(sts, osts), (sts, osts)
 
 
 def test_layout_edges_host_buffers(drg, ctx):
