@@ -188,8 +188,10 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
             uint64_t base = 0;
             int skip = 0;
             if (a.staged) {
-                base = atomicAdd(a.cursor, (unsigned long long)total);
-                if (base + total > a.cap) {
+                // staged rows start at multiples of 16 entries (aligned copies later)
+                const uint64_t span = ((uint64_t)total + 15) & ~15ull;
+                base = atomicAdd(a.cursor, (unsigned long long)span);
+                if (base + span > a.cap) {
                     skip = 1;
                     atomicExch(a.overflow, 1u);
                 }
@@ -297,7 +299,24 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
     }
 }
 
-// Moves staged rows to their final place (one warp per row).
+// Moves staged rows to their final place, one warp per row.  A staged row
+// starts at a multiple of 16 entries; the destination does not, so each
+// lane writes aligned 16-byte groups of the destination, assembled from two
+// aligned 16-byte loads of the source shifted by the row's phase (the same
+// for every group of a row).  Head and tail entries are copied one by one.
+__device__ __forceinline__ uint32_t pick4(uint4 a, uint4 b, uint32_t k) {
+    switch (k) {
+        case 0: return a.x;
+        case 1: return a.y;
+        case 2: return a.z;
+        case 3: return a.w;
+        case 4: return b.x;
+        case 5: return b.y;
+        case 6: return b.z;
+        default: return b.w;
+    }
+}
+
 __global__ void k_unstage(const uint64_t* __restrict__ row_off, const uint64_t* __restrict__ rp, uint32_t n,
                           const uint32_t* __restrict__ scol, const uint8_t* __restrict__ sdist,
                           uint32_t* __restrict__ col, uint8_t* __restrict__ dist) {
@@ -305,10 +324,41 @@ __global__ void k_unstage(const uint64_t* __restrict__ row_off, const uint64_t* 
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t r = warp0; r < n; r += nwarps) {
-        const uint64_t src = row_off[r], dst = rp[r], cnt = rp[r + 1] - rp[r];
-        for (uint64_t e = lane; e < cnt; e += 32) {
-            col[dst + e] = scol[src + e];
-            dist[dst + e] = sdist[src + e];
+        const uint64_t src = row_off[r], dst = rp[r], cnt = rp[r + 1] - dst;
+        // columns: groups of 4 entries
+        {
+            const uint64_t head = ((4 - (dst & 3)) & 3) < cnt ? ((4 - (dst & 3)) & 3) : cnt;
+            const uint64_t groups = (cnt - head) / 4;
+            const uint64_t done = head + 4 * groups;
+            if (lane < head) col[dst + lane] = scol[src + lane];
+            if (lane < cnt - done) col[dst + done + lane] = scol[src + done + lane];
+            const uint32_t ph = (uint32_t)((src + head) & 3);
+            for (uint64_t g = lane; g < groups; g += 32) {
+                const uint64_t sx = src + head + 4 * g, al = sx & ~3ull;
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(scol + al));
+                const uint4 b = ph ? __ldg(reinterpret_cast<const uint4*>(scol + al + 4)) : a;
+                *reinterpret_cast<uint4*>(col + dst + head + 4 * g) =
+                    make_uint4(pick4(a, b, ph), pick4(a, b, ph + 1), pick4(a, b, ph + 2), pick4(a, b, ph + 3));
+            }
+        }
+        // distances: groups of 16 bytes
+        {
+            const uint64_t head = ((16 - (dst & 15)) & 15) < cnt ? ((16 - (dst & 15)) & 15) : cnt;
+            const uint64_t groups = (cnt - head) / 16;
+            const uint64_t done = head + 16 * groups;
+            if (lane < head) dist[dst + lane] = sdist[src + lane];
+            if (lane < cnt - done) dist[dst + done + lane] = sdist[src + done + lane];
+            const uint32_t ph = (uint32_t)((src + head) & 15), wsh = ph >> 2, bsh = 8 * (ph & 3);
+            for (uint64_t g = lane; g < groups; g += 32) {
+                const uint64_t sx = src + head + 16 * g, al = sx & ~15ull;
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(sdist + al));
+                const uint4 b = ph ? __ldg(reinterpret_cast<const uint4*>(sdist + al + 16)) : a;
+                uint32_t o[4];
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k)
+                    o[k] = __funnelshift_r(pick4(a, b, wsh + k), pick4(a, b, wsh + k + 1), bsh);
+                *reinterpret_cast<uint4*>(dist + dst + head + 16 * g) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
         }
     }
 }
@@ -378,11 +428,13 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     }
     if (!k2) cap *= 4;  // a guess: rows that overflow it are traversed again
     if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
+    cap += 16ull * n;  // each staged row is padded to a multiple of 16 entries
     DBuf<uint32_t> scol;
     DBuf<uint8_t> sdist;
     try {
-        scol = DBuf<uint32_t>(ctx, cap ? cap : 1);
-        sdist = DBuf<uint8_t>(ctx, cap ? cap : 1);
+        // 32 spare entries: the aligned copies read up to one group past a row
+        scol = DBuf<uint32_t>(ctx, cap + 32);
+        sdist = DBuf<uint8_t>(ctx, cap + 32);
     } catch (const Error& e) {
         if (e.status != DRG_ENOMEM) throw;
         scol.reset();
@@ -685,16 +737,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_reduce(const uint32_t* 
     }
 }
 
-// Lists: L[x] = x-th light, Dl[x] = deficit of the lights before it; H[y] =
-// y-th heavy, S[y] = excess of the heavies up to and including it.  Each
-// piece's lights and heavies are gathered in shared memory (lights first)
-// and written out in order.
+// Lists: Dl[x] = deficit of the lights before the x-th light; H[y] = y-th
+// heavy, S[y] = excess of the heavies up to and including it.  Each piece's
+// lights and heavies are gathered in shared memory (lights first) and written
+// out in order.
 constexpr size_t SPLIT_DOWN_SMEM = (size_t)SPLIT_SUB * (4 + 4 + 16);
 
 __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __restrict__ q, uint64_t N, uint64_t W,
                                                               const SplitAcc* __restrict__ tile_pre,
-                                                              uint32_t* __restrict__ L, u128* __restrict__ Dl,
-                                                              uint32_t* __restrict__ H, u128* __restrict__ S) {
+                                                              u128* __restrict__ Dl, uint32_t* __restrict__ H,
+                                                              u128* __restrict__ S) {
     extern __shared__ __align__(16) unsigned char split_smem[];
     u128* s_val = reinterpret_cast<u128*>(split_smem);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(split_smem + (size_t)SPLIT_SUB * 16);
@@ -738,7 +790,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __
         const uint64_t xb = run0.c, yb = sb - run0.c;  // lights and heavies before the piece
         for (uint32_t t = threadIdx.x; t < cnt; t += SPLIT_THREADS) {
             if (t < nl) {
-                L[xb + t] = s_idx[t];
                 Dl[xb + t] = s_val[t];
             } else {
                 H[yb + t - nl] = s_idx[t];
@@ -818,20 +869,21 @@ __device__ __forceinline__ uint32_t frac32(uint64_t own, const InvDiv& D) {
 struct MergeArgs {
     const u128* Dl;          // [nL + 1] (Dl[nL] = total deficit)
     const u128* S;           // [nH]
-    const uint32_t* L;
     const uint32_t* H;
-    const uint32_t* q;
-    uint64_t nL, nH, N, W;
+    uint64_t nL, nH, W;
     InvDiv D;
     const uint64_t* part;    // [tiles + 1] merge-path splits
-    uint32_t* thresh;
-    uint32_t* alias;
+    uint32_t* l_alias;       // [nL] alias of each light (kSelf: itself)
+    uint32_t* h_thresh;      // [nH] threshold of each heavy
+    uint32_t* h_alias;       // [nH] alias of each heavy (kSelf: itself)
 };
 
-// The merge, tile by tile, writing each item's table entry as it is placed:
-// light x placed after y heavies -> alias H[y], thresh floor(a 2^32 / W);
-// heavy y placed after x lights -> its own mass S[y] + W - Dl[x] fills the
-// bucket (thresh all ones, alias itself) or takes the next heavy as alias.
+constexpr uint32_t kSelf = 0xFFFFFFFFu;
+
+// The merge, tile by tile, recording each list element's result in list
+// order: light x placed after y heavies -> alias H[y]; heavy y placed after x
+// lights -> its own mass S[y] + W - Dl[x] fills the bucket (thresh all ones,
+// alias itself) or takes the next heavy as alias.
 __global__ void __launch_bounds__(MERGE_THREADS) k_merge_alias(MergeArgs m) {
     __shared__ u128 s[MERGE_TILE];
     const uint64_t total = m.nL + m.nH;
@@ -851,27 +903,93 @@ __global__ void __launch_bounds__(MERGE_THREADS) k_merge_alias(MergeArgs m) {
 #pragma unroll
     for (int it = 0; it < MERGE_ITEMS; ++it) {
         if (xa + yb >= na + nb) break;
+        const uint64_t x = x0 + xa, y = y0 + yb;
         if (xa < na && (yb >= nb || As[xa] < Bs[yb])) {
-            const uint64_t x = x0 + xa, y = y0 + yb;  // light x, y heavies before it
-            const uint32_t b = m.L[x];
-            m.thresh[b] = frac32((uint64_t)m.q[b] * m.N, m.D);
-            m.alias[b] = y < m.nH ? m.H[y] : b;  // y < nH whenever the totals are exact
+            m.l_alias[x] = y < m.nH ? m.H[y] : kSelf;  // y < nH whenever the totals are exact
             ++xa;
         } else {
-            const uint64_t x = x0 + xa, y = y0 + yb;  // heavy y, x lights before it
-            const uint32_t b = m.H[y];
-            const uint64_t own = (uint64_t)(Bs[yb] + (u128)m.W - m.Dl[x]);
-            // exact totals make the last heavy full; the index guard only keeps
-            // a violated invariant from reading past H
+            // own mass = S[y] + W - Dl[x]; exact totals make the last heavy
+            // full, the index guard only keeps a violated invariant from
+            // reading past H
+            const uint64_t own = (uint64_t)(Bs[yb] + (u128)m.W - (xa < na ? As[xa] : m.Dl[x]));
             if (own >= m.W || y + 1 >= m.nH) {
-                m.thresh[b] = 0xFFFFFFFFu;
-                m.alias[b] = b;
+                m.h_thresh[y] = 0xFFFFFFFFu;
+                m.h_alias[y] = kSelf;
             } else {
-                m.thresh[b] = frac32(own, m.D);
-                m.alias[b] = m.H[y + 1];
+                m.h_thresh[y] = frac32(own, m.D);
+                m.h_alias[y] = m.H[y + 1];
             }
             ++yb;
         }
+    }
+}
+
+// Where the table goes: the node table as {thresh, alias} pairs, or the edge
+// table as packed 16-byte or wide 32-byte records with the endpoints of the
+// bucket's own entry and of its alias (and the alias of every bucket).
+enum AliasOutKind { kOutNodes = 0, kOutEdges16 = 1, kOutEdges32 = 2 };
+
+struct AliasOut {
+    int kind;
+    uint2* nodes;            // kOutNodes: [N]
+    void* edges;             // kOutEdges*: [N] records
+    uint32_t* e_alias;       // kOutEdges*: [N] alias of each bucket
+    const uint32_t* esrc;    // kOutEdges*: row of each entry
+    const uint32_t* col;     // kOutEdges*: column of each entry
+};
+
+// Each item's table entry, in item order: its place in the light or heavy
+// list comes from the split scan's tile prefix and a scan of the light flags
+// inside the tile.
+template <int KIND>
+__global__ void __launch_bounds__(SPLIT_THREADS) k_alias_items(const uint32_t* __restrict__ q, uint64_t N,
+                                                               uint64_t W, InvDiv D,
+                                                               const SplitAcc* __restrict__ tile_pre,
+                                                               const uint32_t* __restrict__ l_alias,
+                                                               const uint32_t* __restrict__ h_thresh,
+                                                               const uint32_t* __restrict__ h_alias, AliasOut o) {
+    __shared__ uint32_t wt[SPLIT_THREADS / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * SPLIT_TILE;
+    uint64_t lights = tile_pre[blockIdx.x].c;  // lights before the piece
+    for (uint64_t sb = base; sb < base + SPLIT_TILE && sb < N; sb += SPLIT_THREADS) {
+        const uint64_t i = sb + threadIdx.x;
+        const bool in = i < N;
+        const uint32_t qi = in ? q[i] : 0u;
+        const uint64_t a = (uint64_t)qi * N;
+        const bool light = in && a < W;
+        uint32_t tot;
+        const uint32_t before = block_exclusive_scan<uint32_t, SPLIT_THREADS>(light ? 1u : 0u, wt, tot);
+        if (in) {
+            uint32_t th, al;
+            if (light) {
+                th = frac32(a, D);
+                al = l_alias[lights + before];
+            } else {
+                const uint64_t y = i - (lights + before);
+                th = h_thresh[y];
+                al = h_alias[y];
+            }
+            if (al == kSelf) al = (uint32_t)i;
+            if constexpr (KIND == kOutNodes) {
+                o.nodes[i] = make_uint2(th, al);
+            } else {
+                const uint32_t i0 = o.esrc[i], j0 = o.col[i], i1 = o.esrc[al], j1 = o.col[al];
+                o.e_alias[i] = al;
+                if constexpr (KIND == kOutEdges16) {
+                    static_cast<uint4*>(o.edges)[i] = pack_edge16(th, i0, j0, i1, j1);
+                } else {
+                    EdgeRec r;
+                    r.thresh = th;
+                    r.i0 = i0;
+                    r.j0 = j0;
+                    r.i1 = i1;
+                    r.j1 = j1;
+                    r.pad0 = r.pad1 = r.pad2 = 0;
+                    static_cast<EdgeRec*>(o.edges)[i] = r;
+                }
+            }
+        }
+        lights += tot;
     }
 }
 
@@ -880,9 +998,9 @@ struct Sum64 {
     __device__ __forceinline__ uint64_t operator()(size_t i) const { return q[i]; }
 };
 
-// Alias table over N items with 32-bit weights q; thresh/alias are [N].
-// Returns false (tables untouched) when the weights sum to zero.
-bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, uint32_t* alias) {
+// Alias table over N items with 32-bit weights q, written as `out` says.
+// Returns false (nothing written) when the weights sum to zero.
+bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& out) {
     DRG_CHECK(N > 0 && N < (1ull << 32), DRG_EUNSUPPORTED, "alias table size must be in [1, 2^32)");
     DBuf<uint64_t> Wd(ctx, 1);
     {
@@ -902,48 +1020,30 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, uint32_t* thresh, 
     d2h(ctx, &tot, tsum.p + stiles, 1);
     sync(ctx);
     const uint64_t nL = tot.c, nH = N - nL;
-    DBuf<uint32_t> L(ctx, nL), H(ctx, nH);
-    DBuf<u128> Dl(ctx, nL + 1), S(ctx, nH);
-    DRG_CUDA(cudaFuncSetAttribute(k_split_down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPLIT_DOWN_SMEM));
-    DRG_LAUNCH(ctx, k_split_down, (uint32_t)stiles, SPLIT_THREADS, SPLIT_DOWN_SMEM, q, N, W, tsum.p, L.p, Dl.p, H.p,
-               S.p);
-    h2d(ctx, Dl.p + nL, &tot.D, 1);
-    tsum.reset();
-    // merge, writing the table
-    const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
-    DBuf<uint64_t> part(ctx, tiles + 1);
-    DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, Dl.p, nL, S.p, nH, tiles, part.p);
-    MergeArgs m{Dl.p, S.p, L.p, H.p, q, nL, nH, N, W, make_invdiv(W), part.p, thresh, alias};
-    DRG_LAUNCH(ctx, k_merge_alias, (uint32_t)tiles, MERGE_THREADS, 0, m);
+    const InvDiv D = make_invdiv(W);
+    DBuf<uint32_t> l_alias(ctx, nL), h_thresh(ctx, nH), h_alias(ctx, nH);
+    {
+        DBuf<uint32_t> H(ctx, nH);
+        DBuf<u128> Dl(ctx, nL + 1), S(ctx, nH);
+        DRG_CUDA(cudaFuncSetAttribute(k_split_down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPLIT_DOWN_SMEM));
+        DRG_LAUNCH(ctx, k_split_down, (uint32_t)stiles, SPLIT_THREADS, SPLIT_DOWN_SMEM, q, N, W, tsum.p, Dl.p, H.p,
+                   S.p);
+        h2d(ctx, Dl.p + nL, &tot.D, 1);
+        // merge, recording each list element's result
+        const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
+        DBuf<uint64_t> part(ctx, tiles + 1);
+        DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, Dl.p, nL, S.p, nH, tiles,
+                   part.p);
+        MergeArgs m{Dl.p, S.p, H.p, nL, nH, W, D, part.p, l_alias.p, h_thresh.p, h_alias.p};
+        DRG_LAUNCH(ctx, k_merge_alias, (uint32_t)tiles, MERGE_THREADS, 0, m);
+    }
+    // the table in item order
+    auto kern = out.kind == kOutNodes ? k_alias_items<kOutNodes>
+                                      : (out.kind == kOutEdges16 ? k_alias_items<kOutEdges16> : k_alias_items<kOutEdges32>);
+    DRG_LAUNCH(ctx, kern, (uint32_t)stiles, SPLIT_THREADS, 0, q, N, W, D, tsum.p, l_alias.p, h_thresh.p, h_alias.p,
+               out);
     sync(ctx);  // `tot` is a host value read by an asynchronous copy above
     return true;
-}
-
-template <bool PACKED>
-__global__ void k_edge_records(const uint32_t* __restrict__ thresh, const uint32_t* __restrict__ alias,
-                               const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col, uint64_t nnz,
-                               void* __restrict__ out) {
-    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nnz; b += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t al = alias[b];
-        if constexpr (PACKED) {
-            static_cast<uint4*>(out)[b] = pack_edge16(thresh[b], esrc[b], col[b], esrc[al], col[al]);
-        } else {
-            EdgeRec r;
-            r.thresh = thresh[b];
-            r.i0 = esrc[b];
-            r.j0 = col[b];
-            r.i1 = esrc[al];
-            r.j1 = col[al];
-            r.pad0 = r.pad1 = r.pad2 = 0;
-            static_cast<EdgeRec*>(out)[b] = r;
-        }
-    }
-}
-
-__global__ void k_node_records(const uint32_t* __restrict__ thresh, const uint32_t* __restrict__ alias, uint32_t n,
-                               uint2* __restrict__ out) {
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
-        out[v] = make_uint2(thresh[v], alias[v]);
 }
 
 void dmat_free(drg_dmat* d) {
@@ -994,22 +1094,20 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
         ss.reopen(DRG_PROF_ALIAS, nnz + n);
         // edge table over the entries (positive samples)
         {
-            DBuf<uint32_t> th(ctx, nnz);
-            d->e_alias = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * nnz));
-            DRG_CHECK(build_alias(ctx, d->q, nnz, th.p, d->e_alias), DRG_EEMPTY, "all edge weights are zero");
             const bool packed = n <= kPackedIdLimit;
             d->erec_bytes = packed ? 16u : (uint32_t)sizeof(EdgeRec);
             d->etab = dalloc(ctx, (size_t)d->erec_bytes * nnz);
-            DRG_LAUNCH(ctx, packed ? k_edge_records<true> : k_edge_records<false>, grid_for(nnz, 256, 65536), 256, 0,
-                       th.p, d->e_alias, esrc.p, d->col, nnz, d->etab);
+            d->e_alias = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * nnz));
+            AliasOut out{packed ? kOutEdges16 : kOutEdges32, nullptr, d->etab, d->e_alias, esrc.p, d->col};
+            DRG_CHECK(build_alias(ctx, d->q, nnz, out), DRG_EEMPTY, "all edge weights are zero");
         }
         // node table (negative samples)
         {
-            DBuf<uint32_t> r32(ctx, n), th(ctx, n), al(ctx, n);
+            DBuf<uint32_t> r32(ctx, n);
             DRG_LAUNCH(ctx, k_shift_u32, grid_for(n, 256, 65536), 256, 0, d->r, n, d->shift, r32.p);
-            DRG_CHECK(build_alias(ctx, r32.p, n, th.p, al.p), DRG_EEMPTY, "all node weights are zero");
             d->vtab = static_cast<uint2*>(dalloc(ctx, sizeof(uint2) * n));
-            DRG_LAUNCH(ctx, k_node_records, grid_for(n, 256, 65536), 256, 0, th.p, al.p, n, d->vtab);
+            AliasOut out{kOutNodes, d->vtab, nullptr, nullptr, nullptr, nullptr};
+            DRG_CHECK(build_alias(ctx, r32.p, n, out), DRG_EEMPTY, "all node weights are zero");
         }
         sync(ctx);
     } catch (...) {
