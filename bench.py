@@ -94,16 +94,22 @@ class Job:
         self._run(*self.host)
         return self.host[1]
 
-ALGO_BYTES_NOTE = ("per sample: edge record 20 B + M node records 8 B + (2+M) position gathers "
-                   "(8 B FP32; negatives 4 B with half copies) + (2+M) 8-B atomic adds; "
-                   "+ (2+M) 4-B ancestor reads on coarse levels")
+ALGO_BYTES_NOTE = ("per sample: edge record (16 B packed below 2^24 nodes, else 20 B read of the 32-B record) + "
+                   "M negative records (node table 8 B on level 0; the Hogwild kernel's level node table 16 B on "
+                   "coarse levels, the sub-step kernel's node table 8 B + ancestor 4 B) + (2+M) position gathers "
+                   "(8 B; 4 B for negatives with half copies) + (2+M) 8-B atomic adds; + 2 ancestor reads of 4 B "
+                   "for the endpoints on coarse levels")
 
 
-def algo_bytes_per_sample(M, precision, coarse):
-    neg = 4 if precision else 8
-    b = 20 + 8 * M + 2 * 8 + M * neg + (2 + M) * 8
+def algo_bytes_per_sample(kernel, M, precision, coarse, packed=True):
+    edge = 16 if packed else 20
+    neg_rec = 16 if (coarse and kernel in ("k_hogwild", "k_hogwild_batch")) else 8
+    if coarse and kernel not in ("k_hogwild", "k_hogwild_batch"):
+        neg_rec += 4  # ancestor of each negative
+    neg_pos = 4 if precision else 8
+    b = edge + M * neg_rec + 2 * 8 + M * neg_pos + (2 + M) * 8
     if coarse:
-        b += (2 + M) * 4
+        b += 2 * 4
     return b
 
 
@@ -127,9 +133,10 @@ def kernel_hash():
 def epoch_kernel(graph, mode, precision):
     """The kernel that runs a level's samples: one persistent launch per level
     for FP32 Hogwild on one graph, sub-step launches otherwise."""
+    one_launch = mode == "hogwild" and precision == "fp32"
     if graph == "batch256":
-        return "k_epoch_batch"
-    return "k_hogwild" if mode == "hogwild" and precision == "fp32" else "k_epoch"
+        return "k_hogwild_batch" if one_launch else "k_epoch_batch"
+    return "k_hogwild" if one_launch else "k_epoch"
 
 
 def ncu_traffic_per_sample(kernel):
@@ -393,9 +400,11 @@ def main():
     s0 = n0 * wl["epochs"]
     coarse = max(ep_samples - s0, 0)
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
-    bytes_total = s0 * algo_bytes_per_sample(wl["M"], prec, False) + coarse * algo_bytes_per_sample(wl["M"], prec, True)
-    achieved = bytes_total / (ep_ms / 1000.0) / 1e9
     kname = epoch_kernel(wl["graph"], args.mode, args.precision)
+    packed = n < (1 << 24)
+    bytes_total = (s0 * algo_bytes_per_sample(kname, wl["M"], prec, False, packed)
+                   + coarse * algo_bytes_per_sample(kname, wl["M"], prec, True, packed))
+    achieved = bytes_total / (ep_ms / 1000.0) / 1e9
     tps = ncu_traffic_per_sample(kname)
     avg_launch_samples = ep_samples / max(ep_launches, 1)
     line = {

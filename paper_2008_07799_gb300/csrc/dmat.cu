@@ -42,6 +42,8 @@ struct BfsArgs {
     uint32_t* wlists;         // [gridDim.x * words] touched words
     uint8_t* dlev;            // [gridDim.x * n] hop distance of discovered nodes (k > 2)
     uint32_t* next_row;       // work counter
+    const uint32_t* rows;     // rows to traverse (nullptr: all rows 0 .. n-1)
+    uint32_t nrows;
     uint64_t* counts;         // row sizes (written in both modes)
     int staged;               // 1: write at a reserved staging offset
     unsigned long long* cursor;  // staged: next free staging entry
@@ -106,12 +108,12 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) {
-            s_row = s_next;
+            s_row = s_next < a.nrows ? (a.rows ? a.rows[s_next] : s_next) : 0xFFFFFFFFu;
             s_len = 0;
         }
         __syncthreads();
         const uint32_t row = s_row;
-        if (row >= a.n) break;
+        if (row == 0xFFFFFFFFu) break;
         // the next row's index, taken now and stored once this row is done
         uint32_t next = 0;
         if (threadIdx.x == 0) {
@@ -299,6 +301,154 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ small rows, k = 2
+// Rows whose candidate count (the source's degree plus its neighbours'
+// degrees) is at most SMALL_CAP are built by one warp each, with no block
+// barrier: the warp copies the source's adjacency (key v << 1) and every
+// neighbour's adjacency except the source (key v << 1 | 1) into shared
+// memory, load-balanced over its lanes; sorts the keys (bitonic); keeps the
+// first key of each node -- its distance is 1 + its low bit -- and writes the
+// row to the staging area.
+constexpr uint32_t SMALL_CAP = 2048;
+constexpr int SMALL_WARPS = 8;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, off);
+        if (lane >= (uint32_t)off) v += t;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
+    extern __shared__ uint32_t small_smem[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* buf = small_smem + (size_t)warp * SMALL_CAP;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(a.next_row, 1u);
+        idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+        if (idx >= a.nrows) break;
+        const uint32_t row = a.rows[idx];
+        const uint64_t ab = a.rp[row], ae = a.rp[row + 1];
+        const uint32_t deg = (uint32_t)(ae - ab);
+        for (uint32_t x = lane; x < deg; x += 32) buf[x] = a.col[ab + x] << 1;
+        uint32_t m = deg;
+        // neighbours' adjacencies, 32 neighbours at a time
+        for (uint32_t c = 0; c < deg; c += 32) {
+            uint64_t st = 0;
+            uint32_t d = 0;
+            if (c + lane < deg) {
+                const uint32_t u = a.col[ab + c + lane];
+                st = a.rp[u];
+                d = (uint32_t)(a.rp[u + 1] - st);
+            }
+            const uint32_t incl = warp_incl_scan(d, lane);
+            const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            const uint32_t excl = incl - d;
+            for (uint32_t x0 = 0; x0 < tot; x0 += 32) {
+                const uint32_t x = x0 + lane;
+                // owner: last lane whose exclusive offset is <= x (five steps on every lane)
+                uint32_t lo = 0, hi = 32;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
+                }
+                const uint64_t so = __shfl_sync(0xFFFFFFFFu, st, lo);
+                const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                uint32_t key = 0xFFFFFFFFu;
+                if (x < tot) {
+                    const uint32_t v = a.col[so + (x - eo)];
+                    if (v != row) key = (v << 1) | 1u;
+                }
+                const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
+                if (key != 0xFFFFFFFFu) buf[m + __popc(keep & lanemask_lt())] = key;
+                m += __popc(keep);
+            }
+        }
+        // bitonic sort of buf[0, P), padded with the largest key
+        uint32_t P = 1;
+        while (P < m) P <<= 1;
+        for (uint32_t x = m + lane; x < P; x += 32) buf[x] = 0xFFFFFFFFu;
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t t = lane; t < P / 2; t += 32) {
+                    const uint32_t i = (t / j) * 2 * j + (t % j), l = i + j;
+                    const uint32_t u = buf[i], w = buf[l];
+                    if ((u > w) == ((i & k) == 0)) {
+                        buf[i] = w;
+                        buf[l] = u;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // first key of each node, counted and written in order
+        uint32_t total = 0;
+        for (uint32_t x0 = 0; x0 < m; x0 += 32) {
+            const uint32_t x = x0 + lane;
+            const bool first = x < m && (x == 0 || (buf[x] >> 1) != (buf[x - 1] >> 1));
+            total += __popc(__ballot_sync(0xFFFFFFFFu, first));
+        }
+        uint64_t base = 0;
+        int skip = 0;
+        if (lane == 0) {
+            a.counts[row] = total;
+            const uint64_t span = ((uint64_t)total + 15) & ~15ull;
+            base = atomicAdd(a.cursor, (unsigned long long)span);
+            if (base + span > a.cap) {
+                skip = 1;
+                atomicExch(a.overflow, 1u);
+            }
+            a.row_off[row] = base;
+        }
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        skip = __shfl_sync(0xFFFFFFFFu, skip, 0);
+        if (!skip) {
+            uint64_t o = base;
+            for (uint32_t x0 = 0; x0 < m; x0 += 32) {
+                const uint32_t x = x0 + lane;
+                const bool first = x < m && (x == 0 || (buf[x] >> 1) != (buf[x - 1] >> 1));
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
+                if (first) {
+                    const uint64_t at = o + __popc(bal & lanemask_lt());
+                    a.out_col[at] = buf[x] >> 1;
+                    a.out_dist[at] = (uint8_t)(1 + (buf[x] & 1u));
+                }
+                o += __popc(bal);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Splits the rows into those of at most SMALL_CAP candidates (small) and the
+// rest (big), as two lists (in no particular order).
+__global__ void k_bfs_classify(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col, uint32_t n,
+                               uint32_t* __restrict__ small, uint32_t* __restrict__ big,
+                               uint32_t* __restrict__ counters) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp0; i < n; i += nwarps) {
+        const uint64_t ab = rp[i], ae = rp[i + 1];
+        uint64_t w = 0;
+        for (uint64_t x = ab + lane; x < ae; x += 32) {
+            const uint32_t u = col[x];
+            w += rp[u + 1] - rp[u];
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, off);
+        w += ae - ab;
+        if (lane == 0) {
+            if (w <= SMALL_CAP) small[atomicAdd(&counters[0], 1u)] = (uint32_t)i;
+            else big[atomicAdd(&counters[1], 1u)] = (uint32_t)i;
+        }
+    }
+}
+
 // Moves staged rows to their final place, one warp per row.  A staged row
 // starts at a multiple of 16 entries; the destination does not, so each
 // lane writes aligned 16-byte groups of the destination, assembled from two
@@ -445,6 +595,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     }
     BfsArgs a{};
     a.rp = g->rp; a.col = g->col; a.n = n; a.k = k; a.words = words; a.swords = swords;
+    a.rows = nullptr; a.nrows = n;
     a.gbitmaps = smem_bm ? nullptr : gbm.p;
     a.lists = lists.p; a.wlists = wlists.p; a.dlev = dlev.p;
     a.next_row = counter.p; a.counts = counts.p;
@@ -454,7 +605,32 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     DRG_CUDA(cudaMemsetAsync(overflow.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(cursor.p, 0, 8, ctx->stream));
     {
-        ProfSpan sb(ctx, DRG_PROF_BFS, 0);
+        ProfSpan sb(ctx, DRG_PROF_BFS, 0, 3);
+        DBuf<uint32_t> small, big;
+        if (k2 && n < 0x80000000u && cap > 0) {  // keys v << 1 | 1 stay below 0xFFFFFFFF
+            // k = 2: rows of few candidates by one warp each, the rest by blocks
+            small = DBuf<uint32_t>(ctx, n);
+            big = DBuf<uint32_t>(ctx, n);
+            DBuf<uint32_t> ctr(ctx, 2);
+            DRG_CUDA(cudaMemsetAsync(ctr.p, 0, 8, ctx->stream));
+            DRG_LAUNCH(ctx, k_bfs_classify, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, g->rp,
+                       g->col, n, small.p, big.p, ctr.p);
+            uint32_t nc[2];
+            d2h(ctx, nc, ctr.p, 2);
+            sync(ctx);
+            const size_t ssm = (size_t)SMALL_WARPS * SMALL_CAP * 4;
+            DRG_CUDA(cudaFuncSetAttribute(k_bfs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+            int sper = 0;
+            DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, k_bfs_small, SMALL_WARPS * 32, ssm));
+            BfsArgs as = a;
+            as.rows = small.p;
+            as.nrows = nc[0];
+            DRG_LAUNCH(ctx, k_bfs_small, (uint32_t)ctx->num_sms * (uint32_t)(sper > 0 ? sper : 1), SMALL_WARPS * 32,
+                       ssm, as);
+            DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
+            a.rows = big.p;
+            a.nrows = nc[1];
+        }
         DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
     }
     DBuf<uint64_t> tot(ctx, 1);
@@ -474,6 +650,8 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     scol.reset();
     sdist.reset();
     a.staged = 0;
+    a.rows = nullptr;
+    a.nrows = n;
     a.gd_rp = d->rp;
     a.out_col = d->col;
     a.out_dist = d->dist;
