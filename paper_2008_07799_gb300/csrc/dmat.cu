@@ -85,6 +85,15 @@ __device__ __forceinline__ bool visit(uint32_t* bm, uint32_t* summ, uint32_t v) 
     return true;
 }
 
+// Marks v visited and its word touched, without asking who was first.
+__device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t v) {
+    const uint32_t w = v >> 5, bit = 1u << (v & 31);
+    if (*(volatile uint32_t*)&bm[w] & bit) return;
+    atomicOr(&bm[w], bit);
+    const uint32_t sbit = 1u << (w & 31);
+    if (!(*(volatile uint32_t*)&summ[w >> 5] & sbit)) atomicOr(&summ[w >> 5], sbit);
+}
+
 template <bool K2>
 __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
     extern __shared__ uint32_t dsm[];
@@ -169,11 +178,19 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
                             v[u] = a.col[s_start[lo2] + (x - s_off[lo2])];
                         }
                     }
+                    if (K2 && !store) {
+                        // last level of k = 2: only mark (the row is counted from the
+                        // bitmap when it is written)
 #pragma unroll
-                    for (int u = 0; u < BFS_UNROLL; ++u) {
-                        const bool isnew = v[u] != 0xFFFFFFFFu && visit(bm, summ, v[u]);
-                        if (!K2 && isnew) dl[v[u]] = (uint8_t)d;
-                        bfs_append(v[u], isnew, list, &s_len, store);
+                        for (int u = 0; u < BFS_UNROLL; ++u)
+                            if (v[u] != 0xFFFFFFFFu) mark(bm, summ, v[u]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < BFS_UNROLL; ++u) {
+                            const bool isnew = v[u] != 0xFFFFFFFFu && visit(bm, summ, v[u]);
+                            if (!K2 && isnew) dl[v[u]] = (uint8_t)d;
+                            bfs_append(v[u], isnew, list, &s_len, store);
+                        }
                     }
                 }
                 __syncthreads();
@@ -182,27 +199,9 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
             hi = s_len;
             __syncthreads();
         }
-        const uint32_t total = s_len;
         if (threadIdx.x == 0) {
             s_next = next;
             bm[row >> 5] &= ~(1u << (row & 31));  // the source is not its own neighbour
-            a.counts[row] = total;
-            uint64_t base = 0;
-            int skip = 0;
-            if (a.staged) {
-                // staged rows start at multiples of 16 entries (aligned copies later)
-                const uint64_t span = ((uint64_t)total + 15) & ~15ull;
-                base = atomicAdd(a.cursor, (unsigned long long)span);
-                if (base + span > a.cap) {
-                    skip = 1;
-                    atomicExch(a.overflow, 1u);
-                }
-                a.row_off[row] = base;
-            } else {
-                base = a.gd_rp[row];
-            }
-            s_base = base;
-            s_skip = skip;
         }
         __syncthreads();
         // touched words in increasing order (summary words split in equal ranges)
@@ -225,7 +224,6 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
             }
         }
         __syncthreads();
-        const bool emit = !s_skip;
         // every touched word's bits, in order: warp w takes words [w0, w1)
         const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         constexpr uint32_t NW = BFS_THREADS / 32;
@@ -240,6 +238,32 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
         __syncthreads();
         uint64_t out = 0;  // relative to the row
         for (uint32_t w = 0; w < warp; ++w) out += s_wcnt[w];
+        // the row's size, and its place
+        if (threadIdx.x == 0) {
+            uint32_t total = 0;
+            for (uint32_t w = 0; w < NW; ++w) total += s_wcnt[w];
+            s_len = total;
+            a.counts[row] = total;
+            uint64_t base = 0;
+            int skip = 0;
+            if (a.staged) {
+                // staged rows start at multiples of 16 entries (aligned copies later)
+                const uint64_t span = ((uint64_t)total + 15) & ~15ull;
+                base = atomicAdd(a.cursor, (unsigned long long)span);
+                if (base + span > a.cap) {
+                    skip = 1;
+                    atomicExch(a.overflow, 1u);
+                }
+                a.row_off[row] = base;
+            } else {
+                base = a.gd_rp[row];
+            }
+            s_base = base;
+            s_skip = skip;
+        }
+        __syncthreads();
+        const uint32_t total = s_len;
+        const bool emit = !s_skip;
         for (uint64_t x0 = w0; x0 < w1; x0 += 32) {
             const uint64_t x = x0 + lane;
             uint32_t wi = 0, w = 0;
@@ -254,19 +278,32 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
                 const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
                 if (lane >= (uint32_t)off) incl += t;
             }
-            uint64_t o = out + incl - c;
-            out += __shfl_sync(0xFFFFFFFFu, incl, 31);
-            if (wl_smem && x < w1) s_woff[x] = (uint32_t)o;
+            const uint32_t excl = incl - c;
+            const uint32_t ctot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (wl_smem && x < w1) s_woff[x] = (uint32_t)(out + excl);
             if (emit) {
+                uint64_t o = out + excl;
                 while (w) {
                     const uint32_t b = __ffs(w) - 1;
                     w &= w - 1;
                     const uint32_t v = 32 * wi + b;
                     a.out_col[s_base + o] = v;
-                    a.out_dist[s_base + o] = K2 ? (uint8_t)2 : dl[v];
+                    if (!K2) a.out_dist[s_base + o] = dl[v];
                     ++o;
                 }
             }
+            out += ctot;
+        }
+        if (K2 && emit) {
+            // every distance 2 (aligned 16-byte stores), then the adjacency's 1s
+            uint8_t* dd = a.out_dist + s_base;
+            const uint64_t head = ((16 - ((uintptr_t)dd & 15)) & 15) < total ? ((16 - ((uintptr_t)dd & 15)) & 15) : total;
+            if (threadIdx.x < head) dd[threadIdx.x] = 2;
+            const uint64_t body = (total - head) / 16;
+            uint4* dv = reinterpret_cast<uint4*>(dd + head);
+            for (uint64_t t = threadIdx.x; t < body; t += BFS_THREADS)
+                dv[t] = make_uint4(0x02020202u, 0x02020202u, 0x02020202u, 0x02020202u);
+            for (uint64_t t = head + 16 * body + threadIdx.x; t < total; t += BFS_THREADS) dd[t] = 2;
         }
         __syncthreads();
         if (K2 && emit) {
