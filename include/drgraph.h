@@ -205,12 +205,17 @@ drg_status drg_init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const dr
  * each component clipped to [-clip, clip], zero at distance 0, and
  * lr = p->lr0 (1 - t / p->epochs).  Synchronous mode cuts each epoch into
  * p->substeps runs of ceil(n_l / substeps) consecutive samples whose forces
- * all read the positions at the start of the run; Hogwild mode processes the
- * same runs one after another, each sample applying its updates at once with
- * atomic adds, in no fixed order within a run (bounding the concurrency to
- * one run keeps asynchronous SGD close to the sequential method).  pos (device,
- * float[2 n_level]) is read and updated in place.  `gamma` overrides
- * p->gamma (use p->gamma_coarsest on the coarsest level). */
+ * all read the positions at the start of the run.  Hogwild mode (Sec. 4.3)
+ * applies each sample's updates at once with atomic adds and keeps at most
+ * ceil(n_l / substeps) samples in flight at any moment (bounding the
+ * concurrency keeps asynchronous SGD close to the sequential method): with
+ * FP32 positions, T <= ceil(n_l / substeps) threads each take every T-th
+ * sample of an epoch, one at a time, in one cooperative launch with a grid
+ * barrier between epochs; with half-precision copies, the synchronous runs'
+ * structure.  pos (device, float[2 n_level]) is read and updated in place.
+ * `gamma` overrides p->gamma (use p->gamma_coarsest on the coarsest level).
+ * DRG_ETIMEOUT: an epoch barrier waited longer than 2 s (the positions are
+ * then partly updated). */
 drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                             const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end);
 
@@ -256,17 +261,30 @@ drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
  * streams, distance matrix, tables and hierarchy; in synchronous mode its
  * result equals drg_layout of that graph alone with those parameters up to
  * the order of FP32 atomic additions.  Levels run in rounds aligned at every
- * graph's coarsest level; within a round, sub-step run c of every active
- * graph is one kernel launch, and all epochs of the round are one CUDA graph
- * launch.  pos[g] are device float[2 n_g].  Synchronises. */
+ * graph's coarsest level; in FP32 Hogwild mode all epochs of a round are one
+ * cooperative launch (threads of every active graph, a grid barrier between
+ * epochs); otherwise sub-step run c of every active graph is one kernel
+ * launch and all epochs of the round are one CUDA graph launch.  pos[g] are
+ * device float[2 n_g].  Synchronises. */
 drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
                             const float* b, float* const* pos);
+
+/* Self-check of the epoch barrier of the Hogwild level runs (no counterpart
+ * in the paper).  `blocks` thread blocks (1 .. number of SMs), launched so
+ * that all are resident at once, meet `rounds` times at a grid barrier that
+ * completes after `arrivals` arrivals, each wait limited to timeout_ms (1 ..
+ * 10000).  arrivals == blocks: DRG_OK.  arrivals > blocks: no barrier can
+ * complete, every wait runs out, the blocks leave and the call returns
+ * DRG_ETIMEOUT (the GPU stays usable).  DRG_EUNSUPPORTED when the blocks
+ * cannot be resident together. */
+drg_status drg_check_epoch_barrier(drg_ctx* ctx, uint32_t blocks, uint32_t arrivals, uint32_t rounds,
+                                   uint32_t timeout_ms);
 
 /* ---------------------------------------------------------------- profiling */
 /* Per-kernel timing with CUDA events recorded on the context stream around
  * every launch of the named kernel family (costs a few microseconds per
  * launch; off by default).  Counters accumulate until reset. */
-#define DRG_PROF_EPOCH 0   /* k_epoch: the sampling / gradient kernel; units = samples */
+#define DRG_PROF_EPOCH 0   /* the sampling / gradient kernels (level runs); units = samples */
 #define DRG_PROF_APPLY 1   /* k_apply: synchronous sub-step apply; units = nodes */
 #define DRG_PROF_DMAT 2    /* drg_build_distance_matrix as a whole; units = entries */
 #define DRG_PROF_HIER 3    /* hierarchy construction as a whole; units = levels */

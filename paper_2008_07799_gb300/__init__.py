@@ -36,7 +36,7 @@ EXPORTS = [
     "drg_build_hierarchy", "drg_hier_info", "drg_hier_download", "drg_hier_graph", "drg_hier_destroy",
     "drg_init_positions", "drg_layout_level", "drg_interpolate", "drg_layout", "drg_layout_edges",
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
-    "drg_layout_level_noalloc", "drg_dmat_download_range",
+    "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
 ]
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
@@ -117,6 +117,7 @@ def lib():
         "drg_init_positions": (st, [VP, C.c_uint32, C.c_uint32, PP, VP]),
         "drg_layout_level": (st, [VP, VP, VP, C.c_uint32, VP, PP, C.c_float, C.c_uint32, C.c_uint32]),
         "drg_layout_level_noalloc": (st, [VP, VP, VP, C.c_uint32, VP, PP, C.c_float, C.c_uint32, C.c_uint32]),
+        "drg_check_epoch_barrier": (st, [VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
         "drg_interpolate": (st, [VP, VP, C.c_uint32, VP, VP]),
         "drg_layout": (st, [VP, VP, PP, VP]),
         "drg_layout_edges": (st, [VP, C.c_uint32, C.c_uint64, VP, VP, C.c_int, PP, VP, C.c_int]),
@@ -376,6 +377,11 @@ def layout_level(ctx: Context, d: DistanceMatrix, h: Hierarchy | None, level, po
 
 def interpolate(ctx: Context, h: Hierarchy, coarse_level, coarse_pos, fine_pos):
     ctx.check(lib().drg_interpolate(ctx.h, h.h, int(coarse_level), _ptr(coarse_pos), _ptr(fine_pos)))
+
+
+def check_epoch_barrier(ctx: Context, blocks, arrivals, rounds=1, timeout_ms=50) -> int:
+    """Status (0 ok, 4 timed out, ...) of the epoch-barrier self-check; does not raise."""
+    return int(lib().drg_check_epoch_barrier(ctx.h, int(blocks), int(arrivals), int(rounds), int(timeout_ms)))
 
 
 def layout(ctx: Context, g: Graph, p: Params, pos):

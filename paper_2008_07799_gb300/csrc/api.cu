@@ -428,6 +428,14 @@ drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_h
     API_CATCH(ctx)
 }
 
+drg_status drg_check_epoch_barrier(drg_ctx* ctx, uint32_t blocks, uint32_t arrivals, uint32_t rounds,
+                                   uint32_t timeout_ms) {
+    if (!ctx) return DRG_EINVAL;
+    API_TRY
+    drg::check_epoch_barrier(ctx, blocks, arrivals, rounds, timeout_ms);
+    API_CATCH(ctx)
+}
+
 drg_status drg_interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos,
                            float* fine_pos) {
     if (!ctx) return DRG_EINVAL;

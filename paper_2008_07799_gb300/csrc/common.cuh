@@ -285,6 +285,7 @@ void check_params(const drg_params& p);
 void init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const drg_params& p, float* pos);
 void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                   const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end);
+void check_epoch_barrier(drg_ctx* ctx, uint32_t blocks, uint32_t arrivals, uint32_t rounds, uint32_t timeout_ms);
 void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                           const drg_params& p, float gamma, uint32_t t_begin, uint32_t t_end);
 void interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_level, const float* coarse_pos, float* fine_pos);

@@ -265,24 +265,86 @@ __device__ __forceinline__ uint32_t find_job(const uint32_t* prefix, uint32_t nj
 }
 
 // ------------------------------------------------------------------ Hogwild level run in one launch
-// Asynchronous mode (Sec. 4.3) as one persistent grid of T threads.  The
-// samples of the run, epoch after epoch, form the sequence q = (t - t_begin)
-// n_l + s; thread g takes q = g, g + T, g + 2T, ... one at a time.  A sample
-// is in flight from its position gathers to its atomic adds, so at most T <=
-// ceil(n_l / substeps) samples are in flight at any moment -- the bound the
-// sub-step runs give -- but no thread ever waits for another.  Each thread
-// keeps two samples ahead of the one it updates: the next sample's table
-// records are resolved (and mapped through the ancestors) and the one after
-// has its Philox words drawn and its records requested while the current
-// sample's gathers are in flight.  Positions are read through L2 only
+// Asynchronous mode (Sec. 4.3) as one persistent grid of T threads.  In every
+// epoch thread g takes the samples g, g + T, g + 2T, ... < n_l one at a time,
+// so at most T <= ceil(n_l / substeps) samples are in flight (between their
+// position gathers and their atomic adds) at any moment -- the bound the
+// sub-step runs give -- and no thread waits for another inside an epoch.
+// Epochs stay in step: a warp starts epoch e only when every warp of the
+// grid has finished epoch e - kEpochLag (the grid is launched cooperatively,
+// so all its warps are resident).  Without this fast threads finish the
+// low-learning-rate epochs while slow ones are epochs behind, which costs
+// local quality (1M-node DC-SBM: NP .024 instead of .039); with a lag of two
+// epochs and no block-wide wait only warps running ahead ever pause.
+// Each thread keeps two samples ahead of the one it updates: the next
+// sample's table records are resolved (and mapped through the ancestors) and
+// the one after has its Philox words drawn and its records requested while
+// the current sample's gathers are in flight; this position-independent work
+// runs on across the epoch gates.  Positions are read through L2 only
 // (ld.global.cg), since other SMs change them for the whole launch.
 struct HogwildArgs {
     EpochArgs a;
     const float* lr_tab;  // [epochs] learning rate of each epoch
-    uint32_t t_begin, T;  // first epoch; number of threads
+    uint32_t t_begin;     // first epoch
+    uint32_t epochs;      // epochs of this launch
+    uint32_t T;           // threads of the run
     uint32_t nl;          // samples per epoch
-    uint64_t total;       // (t_end - t_begin) n_l
 };
+
+// Epoch gates of one launch: done[e] counts the warps that finished epoch e
+// (zero before the launch; nullptr: no gates); an error flag set when a wait
+// runs out (then every warp leaves the kernel).  All lanes of a warp pass the
+// gates together (they contain warp-wide shuffles).
+struct GridSync {
+    unsigned int* done;   // [epochs]
+    int* err;
+    uint32_t nwarps;      // warps that complete an epoch
+    uint32_t lag;         // epoch e waits for epoch e - lag
+    uint64_t timeout_ns;  // longest wait at one gate
+};
+
+constexpr uint32_t kEpochLag = 2;
+constexpr uint64_t kGateTimeoutNs = 2000000000ull;  // 2 s, far above any epoch
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Before epoch e (e >= lag): wait until every warp finished epoch e - lag.
+// False (on every lane) when the wait ran out or another warp gave up.
+__device__ __forceinline__ bool epoch_gate(const GridSync& gs, uint32_t e) {
+    __syncwarp();
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        volatile unsigned int* d = gs.done + (e - gs.lag);
+        volatile int* err = gs.err;
+        if (*d < gs.nwarps) {
+            const uint64_t t0 = global_ns();
+            uint32_t nap = 64;
+            while (*d < gs.nwarps) {
+                if (*err || global_ns() - t0 > gs.timeout_ns) {
+                    atomicExch(gs.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(nap);
+                nap = nap < 1024 ? 2 * nap : nap;
+            }
+        }
+        ok = ok && !*err;
+    }
+    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+}
+
+// After epoch e: the warp reports it done.  No fence: the gates bound how far
+// warps drift apart; the positions themselves are shared without ordering, as
+// asynchronous SGD allows.
+__device__ __forceinline__ void epoch_done(const GridSync& gs, uint32_t e) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) atomicAdd(gs.done + e, 1u);
+}
 
 // A sample's table records, requested (stage 1).  On level 0 a negative's
 // record is the node table's {thresh, alias} and the bucket is the own item;
@@ -344,10 +406,10 @@ __device__ __forceinline__ void hw_push(float2* Y, uint32_t v, float lr, float f
     atomicAdd(&Y[v], make_float2(lr * fx, lr * fy));
 }
 
-// next element of a thread's sequence: q += T
-__device__ __forceinline__ void hw_advance(uint32_t& t, uint32_t& s, uint32_t T, uint32_t nl) {
+// a thread's next sample: s += T within the epoch, else sample g of the next epoch
+__device__ __forceinline__ void hw_advance(uint32_t& t, uint32_t& s, uint32_t g, uint32_t T, uint32_t nl) {
     if (s >= nl - T) {
-        s -= nl - T;
+        s = g;
         ++t;
     } else {
         s += T;
@@ -364,7 +426,7 @@ struct HwPipe {
     Requested<MT, ANC> Q[2];
     Resolved<MT> V[2];
     uint32_t tQ[2], tV[2];  // epochs of the slots' samples
-    uint32_t t1, s1;        // next sample to request
+    uint32_t t1, s1, g;     // next sample to request; the thread's first sample
 };
 
 template <int MT, bool ANC, int P>
@@ -383,7 +445,7 @@ __device__ __forceinline__ void hw_step(const HogwildArgs& h, HwPipe<MT, ANC>& p
     if (k + 4 < cnt) {
         hw_request<MT, ANC>(a, p.s1, p.t1, p.Q[P]);
         p.tQ[P] = p.t1;
-        hw_advance(p.t1, p.s1, h.T, h.nl);
+        hw_advance(p.t1, p.s1, p.g, h.T, h.nl);
     }
     const float2 fa = attract(a, ya, yc);
     float Fx = fa.x, Fy = fa.y;
@@ -403,87 +465,122 @@ template <int MT, bool ANC, int P>
 __device__ __forceinline__ void hw_fill(const HogwildArgs& h, HwPipe<MT, ANC>& p) {
     hw_request<MT, ANC>(h.a, p.s1, p.t1, p.Q[P]);
     p.tQ[P] = p.t1;
-    hw_advance(p.t1, p.s1, h.T, h.nl);
+    hw_advance(p.t1, p.s1, p.g, h.T, h.nl);
 }
 
-// One thread's share of a run: elements g, g + T, g + 2T, ... of the sequence.
+// Samples of thread g in each epoch (0 for threads past the run's T).
+__device__ __forceinline__ uint32_t hw_share(const HogwildArgs& h, uint32_t g) {
+    return g < h.T ? (h.nl - g + h.T - 1) / h.T : 0u;
+}
+
+// One thread's share of a run: in each epoch the samples g, g + T, ... < n_l;
+// every thread of the grid takes part in every epoch barrier.
 template <int MT, bool ANC>
-__device__ __forceinline__ void hogwild_thread(const HogwildArgs& h, uint32_t g) {
-    const uint64_t cnt = (h.total - g + h.T - 1) / h.T;  // samples of this thread
-    if (cnt == 0) return;
+__device__ __forceinline__ bool hogwild_thread(const HogwildArgs& h, const GridSync& gs, uint32_t g,
+                                               uint32_t t_begin, uint32_t epochs) {
+    const uint32_t share = hw_share(h, g);
+    const uint64_t cnt = (uint64_t)share * epochs;  // samples of this thread
     HwPipe<MT, ANC> p;
-    p.t1 = h.t_begin;
+    p.t1 = t_begin;
     p.s1 = g;
-    hw_fill<MT, ANC, 0>(h, p);                             // sample 0
+    p.g = g;
+    if (cnt > 0) hw_fill<MT, ANC, 0>(h, p);                // sample 0
     if (cnt > 1) hw_fill<MT, ANC, 1>(h, p);                // sample 1
-    hw_resolve<MT, ANC>(h.a, p.Q[0], p.V[0]);
-    p.tV[0] = p.tQ[0];
+    if (cnt > 0) {
+        hw_resolve<MT, ANC>(h.a, p.Q[0], p.V[0]);
+        p.tV[0] = p.tQ[0];
+    }
     if (cnt > 2) hw_fill<MT, ANC, 0>(h, p);                // sample 2
     if (cnt > 1) {
         hw_resolve<MT, ANC>(h.a, p.Q[1], p.V[1]);
         p.tV[1] = p.tQ[1];
     }
     if (cnt > 3) hw_fill<MT, ANC, 1>(h, p);                // sample 3
-    for (uint64_t k = 0; k < cnt; k += 2) {
-        hw_step<MT, ANC, 0>(h, p, k, cnt);
-        if (k + 1 < cnt) hw_step<MT, ANC, 1>(h, p, k + 1, cnt);
-    }
-}
-
-// Runtime number of negatives: the same sequence, one sample after another.
-template <bool ANC>
-__device__ __forceinline__ void hogwild_thread_rt(const HogwildArgs& h, uint32_t g) {
-    const EpochArgs& a = h.a;
-    uint64_t left = (h.total - g + h.T - 1) / h.T;
-    uint32_t t = h.t_begin, s = g;
-    for (; left > 0; --left, hw_advance(t, s, h.T, h.nl)) {
-        Words W(s, t, a.tag, a.key);
-        uint32_t i, j;
-        draw_edge(a, W, i, j);
-        const uint32_t ia = ANC ? __ldg(&a.anc[i]) : i, ic = ANC ? __ldg(&a.anc[j]) : j;
-        const float lr = __ldg(&h.lr_tab[t]);
-        const float2 ya = __ldcg(&a.Y[ia]), yc = __ldcg(&a.Y[ic]);
-        const float2 fa = attract(a, ya, yc);
-        float Fx = fa.x, Fy = fa.y;
-        for (uint32_t m = 0; m < a.M; ++m) {
-            uint32_t cm = draw_negative(a, W, m);
-            if (ANC) cm = __ldg(&a.anc[cm]);
-            if (cm == ia || cm == ic) continue;
-            const float2 fr = repel(a, ya, __ldcg(&a.Y[cm]));
-            Fx += fr.x;
-            Fy += fr.y;
-            hw_push(a.Y, cm, lr, -fr.x, -fr.y);
+    uint64_t k = 0;
+    for (uint32_t e = 0; e < epochs; ++e) {
+        if (gs.done && e >= gs.lag && !epoch_gate(gs, e)) return false;
+        // samples [k, end) of this epoch, two at a time (slot parity = sample
+        // parity; the pair body lets one sample's compute fill the other's waits)
+        const uint64_t end = k + share;
+        if (k < end && (k & 1)) hw_step<MT, ANC, 1>(h, p, k++, cnt);
+        for (; k + 1 < end; k += 2) {
+            hw_step<MT, ANC, 0>(h, p, k, cnt);
+            hw_step<MT, ANC, 1>(h, p, k + 1, cnt);
         }
-        hw_push(a.Y, ia, lr, Fx, Fy);
-        hw_push(a.Y, ic, lr, -fa.x, -fa.y);
+        if (k < end) hw_step<MT, ANC, 0>(h, p, k++, cnt);
+        if (gs.done) epoch_done(gs, e);
     }
+    return true;
+}
+
+// Runtime number of negatives: the same samples, one after another.
+template <bool ANC>
+__device__ __forceinline__ bool hogwild_thread_rt(const HogwildArgs& h, const GridSync& gs, uint32_t g,
+                                                  uint32_t t_begin, uint32_t epochs) {
+    const EpochArgs& a = h.a;
+    const uint32_t share = hw_share(h, g);
+    for (uint32_t e = 0; e < epochs; ++e) {
+        if (gs.done && e >= gs.lag && !epoch_gate(gs, e)) return false;
+        const uint32_t t = t_begin + e;
+        const float lr = __ldg(&h.lr_tab[t]);
+        for (uint32_t i = 0, s = g; i < share; ++i, s += h.T) {
+            Words W(s, t, a.tag, a.key);
+            uint32_t ii, jj;
+            draw_edge(a, W, ii, jj);
+            const uint32_t ia = ANC ? __ldg(&a.anc[ii]) : ii, ic = ANC ? __ldg(&a.anc[jj]) : jj;
+            const float2 ya = __ldcg(&a.Y[ia]), yc = __ldcg(&a.Y[ic]);
+            const float2 fa = attract(a, ya, yc);
+            float Fx = fa.x, Fy = fa.y;
+            for (uint32_t m = 0; m < a.M; ++m) {
+                uint32_t cm = draw_negative(a, W, m);
+                if (ANC) cm = __ldg(&a.anc[cm]);
+                if (cm == ia || cm == ic) continue;
+                const float2 fr = repel(a, ya, __ldcg(&a.Y[cm]));
+                Fx += fr.x;
+                Fy += fr.y;
+                hw_push(a.Y, cm, lr, -fr.x, -fr.y);
+            }
+            hw_push(a.Y, ia, lr, Fx, Fy);
+            hw_push(a.Y, ic, lr, -fa.x, -fa.y);
+        }
+        if (gs.done) epoch_done(gs, e);
+    }
+    return true;
 }
 
 template <int MT, bool ANC>
-__device__ __forceinline__ void hogwild_dispatch(const HogwildArgs& h, uint32_t g) {
-    if constexpr (MT > 0) hogwild_thread<MT, ANC>(h, g);
-    else hogwild_thread_rt<ANC>(h, g);
+__device__ __forceinline__ void hogwild_dispatch(const HogwildArgs& h, const GridSync& gs, uint32_t g,
+                                                 uint32_t t_begin, uint32_t epochs) {
+    if constexpr (MT > 0) hogwild_thread<MT, ANC>(h, gs, g, t_begin, epochs);
+    else hogwild_thread_rt<ANC>(h, gs, g, t_begin, epochs);
 }
 
-// MT > 0: compile-time number of negatives; MT == 0: runtime M.
+// MT > 0: compile-time number of negatives; MT == 0: runtime M.  Every
+// thread of the grid (also those past T) runs, for the epoch barriers.
 template <int MT, bool ANC>
-__global__ void __launch_bounds__(128) k_hogwild(HogwildArgs h) {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < h.T) hogwild_dispatch<MT, ANC>(h, g);
+__global__ void __launch_bounds__(128, 4) k_hogwild(HogwildArgs h, GridSync gs) {
+    hogwild_dispatch<MT, ANC>(h, gs, blockIdx.x * blockDim.x + threadIdx.x, h.t_begin, h.epochs);
 }
 
 // One level of each of many graphs in one launch: run x owns the threads
-// [prefix[x], prefix[x + 1]).
+// [prefix[x], prefix[x + 1]); threads past the last run only pass the epoch
+// gates (all runs have the same number of epochs).  Every run has an
+// ancestor map (level-0 runs the identity), so all threads of a block take
+// the same code path through the gates.
 template <int MT>
 __global__ void __launch_bounds__(128) k_hogwild_batch(const HogwildArgs* __restrict__ runs,
-                                                       const uint32_t* __restrict__ prefix, uint32_t nruns) {
+                                                       const uint32_t* __restrict__ prefix, uint32_t nruns,
+                                                       GridSync gs, uint32_t t_begin, uint32_t epochs) {
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gt >= prefix[nruns]) return;
     const uint32_t x = find_job(prefix, nruns, gt);
     const HogwildArgs& h = runs[x];
     const uint32_t g = gt - prefix[x];
-    if (h.a.anc) hogwild_dispatch<MT, true>(h, g);
-    else hogwild_dispatch<MT, false>(h, g);
+    hogwild_dispatch<MT, true>(h, gs, g, t_begin, epochs);
+}
+
+__global__ void k_iota(uint32_t* __restrict__ out, uint32_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        out[v] = (uint32_t)v;
 }
 
 // ------------------------------------------------------------------ batches of graphs
@@ -697,15 +794,58 @@ static EpochKernel pick_epoch(uint32_t M, bool sync, int prec) {
 // one thread per sample
 static uint32_t epoch_grid(drg_ctx*, uint64_t count) { return (uint32_t)((count + 255) / 256); }
 
-typedef void (*HogwildKernel)(HogwildArgs);
+typedef void (*HogwildKernel)(HogwildArgs, GridSync);
 
 static HogwildKernel pick_hogwild(uint32_t M, bool anc) {
     if (M == 5) return anc ? k_hogwild<5, true> : k_hogwild<5, false>;
     return anc ? k_hogwild<0, true> : k_hogwild<0, false>;
 }
 
-// Epochs [t_begin, t_end) of an FP32 Hogwild level run in one launch: T =
-// min(ceil(n_l / substeps), resident threads) threads.
+// Cooperative launch (all blocks resident together); false when the grid
+// cannot be resident at once, with nothing launched.
+template <typename... KArgs, typename... Args>
+static bool launch_cooperative(drg_ctx* ctx, const char* name, void (*kernel)(KArgs...), uint32_t grid,
+                               uint32_t block, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    DRG_CUDA(e);
+    after_launch(ctx, name);
+    return true;
+}
+
+// The epoch-gate state of a launch: one counter per epoch and the error
+// flag, zeroed on the stream.
+struct SyncBuf {
+    DBuf<unsigned int> done;
+    DBuf<int> err;
+    SyncBuf(drg_ctx* ctx, uint32_t epochs) : done(ctx, epochs), err(ctx, 1) {
+        DRG_CUDA(cudaMemsetAsync(done.p, 0, (size_t)(epochs ? epochs : 1) * sizeof(unsigned int), ctx->stream));
+        DRG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), ctx->stream));
+    }
+    GridSync sync(uint32_t nwarps, uint32_t lag, uint64_t timeout_ns) const {
+        return GridSync{done.p, err.p, nwarps, lag, timeout_ns};
+    }
+    void check(drg_ctx* ctx) {
+        DRG_CHECK(read1(ctx, err.p) == 0, DRG_ETIMEOUT, "an epoch gate of a Hogwild level run timed out");
+    }
+};
+
+// Epochs [t_begin, t_end) of an FP32 Hogwild level run in one cooperative
+// launch of T = min(ceil(n_l / substeps), resident threads) threads (one
+// launch per epoch when the grid cannot be resident at once).
 static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p, uint32_t nl, const float* lr_tab,
                           uint32_t t_begin, uint32_t t_end) {
     const HogwildKernel k = pick_hogwild(p.M, a.anc != nullptr);
@@ -717,9 +857,9 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
     h.a = a;
     h.lr_tab = lr_tab;
     h.t_begin = t_begin;
+    h.epochs = t_end - t_begin;
     h.T = (uint32_t)(bound < resident ? bound : resident);
     h.nl = nl;
-    h.total = (uint64_t)(t_end - t_begin) * nl;
     DBuf<uint4> vl;
     if (a.anc) {
         vl = DBuf<uint4>(ctx, a.n0);
@@ -727,19 +867,39 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
                    vl.p);
         h.a.vtab_l = vl.p;
     }
-    ProfSpan span(ctx, DRG_PROF_EPOCH, h.total, 1);
-    DRG_LAUNCH(ctx, k, (h.T + 127) / 128, 128, 0, h);
+    const uint32_t grid = (h.T + 127) / 128;
+    SyncBuf sb(ctx, h.epochs);
+    {
+        ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)h.epochs * nl, 1);
+        if (!launch_cooperative(ctx, "k_hogwild", k, grid, 128, h, sb.sync(grid * 4, kEpochLag, kGateTimeoutNs))) {
+            span.count = h.epochs;
+            for (uint32_t t = t_begin; t < t_end; ++t) {
+                HogwildArgs h1 = h;
+                h1.t_begin = t;
+                h1.epochs = 1;
+                DRG_LAUNCH(ctx, k, grid, 128, 0, h1, GridSync{nullptr, nullptr, grid, 0, 0});
+            }
+        }
+    }
+    sb.check(ctx);
 }
 
 // Hogwild runs of many graphs (each with T = ceil(n_l / substeps) set) in one
 // launch.  When their threads exceed what the GPU holds at once, every run's
 // thread count is scaled down in proportion (at least one each), so that all
 // threads are resident together and the bound only tightens.
-static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& runs, uint64_t samples) {
+static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& runs, uint32_t epochs,
+                          uint64_t samples) {
     if (runs.empty()) return;
-    std::vector<DBuf<uint4>> tables;  // level node tables of the coarse runs
+    std::vector<DBuf<uint4>> tables;     // level node tables
+    std::vector<DBuf<uint32_t>> idmaps;  // identity ancestor maps of level-0 runs
     for (auto& h : runs) {
-        if (!h.a.anc) continue;
+        if (!h.a.anc) {
+            idmaps.emplace_back(ctx, h.a.n0);
+            DRG_LAUNCH(ctx, k_iota, grid_for(h.a.n0, 256, (uint32_t)ctx->num_sms * 8), 256, 0, idmaps.back().p,
+                       h.a.n0);
+            h.a.anc = idmaps.back().p;
+        }
         tables.emplace_back(ctx, h.a.n0);
         DRG_LAUNCH(ctx, k_level_nodes, grid_for(h.a.n0, 256, (uint32_t)ctx->num_sms * 8), 256, 0, h.a.vtab, h.a.anc,
                    h.a.n0, tables.back().p);
@@ -762,8 +922,41 @@ static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& ru
     DBuf<uint32_t> dprefix(ctx, nruns + 1);
     h2d(ctx, druns.p, runs.data(), nruns);
     h2d(ctx, dprefix.p, prefix.data(), nruns + 1);
-    ProfSpan span(ctx, DRG_PROF_EPOCH, samples, 1);
-    DRG_LAUNCH(ctx, k, (prefix[nruns] + 127) / 128, 128, 0, druns.p, dprefix.p, (uint32_t)nruns);
+    const uint32_t grid = (prefix[nruns] + 127) / 128;
+    SyncBuf sb(ctx, epochs);
+    {
+        ProfSpan span(ctx, DRG_PROF_EPOCH, samples, 1);
+        if (!launch_cooperative(ctx, "k_hogwild_batch", k, grid, 128, druns.p, dprefix.p, (uint32_t)nruns,
+                                sb.sync(grid * 4, kEpochLag, kGateTimeoutNs), 0u, epochs)) {
+            span.count = epochs;
+            for (uint32_t t = 0; t < epochs; ++t)
+                DRG_LAUNCH(ctx, k, grid, 128, 0, druns.p, dprefix.p, (uint32_t)nruns,
+                           GridSync{nullptr, nullptr, grid, 0, 0}, t, 1u);
+        }
+    }
+    sb.check(ctx);
+}
+
+// Gate check: `blocks` one-warp blocks run `rounds` empty epochs through
+// gates (lag one) that open when `arrivals` warps have finished the previous
+// epoch.  With arrivals > blocks no gate opens and every wait runs out after
+// timeout_ms: DRG_ETIMEOUT.
+__global__ void k_gate_probe(GridSync gs, uint32_t rounds) {
+    for (uint32_t e = 0; e < rounds; ++e) {
+        if (e >= gs.lag && !epoch_gate(gs, e)) return;
+        epoch_done(gs, e);
+    }
+}
+
+void check_epoch_barrier(drg_ctx* ctx, uint32_t blocks, uint32_t arrivals, uint32_t rounds, uint32_t timeout_ms) {
+    DRG_CHECK(blocks >= 1 && blocks <= (uint32_t)ctx->num_sms && arrivals >= 1 && rounds >= 1 && rounds <= 100000 &&
+                  timeout_ms >= 1 && timeout_ms <= 10000,
+              DRG_EINVAL, "blocks in [1, SMs], arrivals >= 1, rounds in [1, 100000], timeout in [1, 10000] ms");
+    SyncBuf sb(ctx, rounds);
+    DRG_CHECK(launch_cooperative(ctx, "k_gate_probe", k_gate_probe, blocks, 32,
+                                 sb.sync(arrivals, 1, (uint64_t)timeout_ms * 1000000ull), rounds),
+              DRG_EUNSUPPORTED, "the probe grid cannot be resident at once");
+    sb.check(ctx);
 }
 
 // One CUDA graph for a level run: a WHILE node whose body is one epoch --
@@ -1112,15 +1305,15 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                     h.a.bint = J.bint;
                     h.lr_tab = lr_tab.p;
                     h.t_begin = 0;
+                    h.epochs = p.epochs;
                     h.T = J.chunk;
                     h.nl = nl;
-                    h.total = (uint64_t)p.epochs * nl;
                     runs.push_back(h);
                 }
             }
             const uint32_t njobs = (uint32_t)jobs.size();
             if (one_launch) {
-                hogwild_batch(ctx, p.M, runs, samples * p.epochs);
+                hogwild_batch(ctx, p.M, runs, p.epochs, samples * p.epochs);
             } else {
                 DBuf<BatchJob> djobs(ctx, njobs);
                 DBuf<uint32_t> dbpre(ctx, njobs + 1), dnpre(ctx, njobs + 1);

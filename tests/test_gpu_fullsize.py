@@ -156,3 +156,25 @@ def test_rmat22_k1_mixed_hogwild(env, orc):
     # isolated nodes are never drawn, so they keep their coarsest-level start
     assert np.all(np.abs(Y[iso]) <= 1e-4)
     assert np.ptp(Y[~iso], axis=0).max() > 10.0
+
+
+def test_dcsbm1m_hogwild_matches_sync_quality(env, orc):
+    """Whole runs on the benchmark graph: the one-launch Hogwild levels keep the
+    local quality of the synchronous method (NP on 2000 sampled nodes within
+    10 %).  Epochs must stay in step: without the epoch barrier NP fell to .024
+    against .039."""
+    drg, ctx = env
+    g = gg.workload("dcsbm1m")
+    n = g[0]
+    rp, col = orc.canonical_graph(*g)
+    deg = np.diff(rp)
+    nodes = np.random.default_rng(0).choice(np.nonzero(deg > 0)[0], 2000, replace=False).astype(np.uint32)
+    G = drg.graph_from_edges(ctx, *g)
+    nps = {}
+    for mode in (0, 1):
+        p = drg.Params.default(k=2, M=5, epochs=500, b=1.0, mode=mode, stop_nodes=1000, seed=0)
+        pos = torch.zeros(2 * n, device="cuda")
+        drg.layout(ctx, G, p, pos)
+        Y = pos.cpu().numpy().astype(np.float64).reshape(-1, 2)
+        nps[mode] = orc.neighbourhood_preservation(rp, col, Y, 2, nodes)
+    assert nps[1] >= 0.9 * nps[0], nps
