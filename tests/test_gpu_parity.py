@@ -211,6 +211,40 @@ def test_sync_epoch_parity(drg, ctx, orc, name, k, b, level, t):
     assert np.max(np.abs(ref - Y0)) > 1e-3  # the epoch moved the layout
 
 
+@pytest.mark.parametrize("name,k,b,level,t,M", [("grid32", 3, 3.0, 0, 10, 5), ("ba2000", 2, 1.0, 2, 3, 5),
+                                                ("ba2000", 2, 1.0, 0, 100, 3)])
+def test_hogwild_one_sample_in_flight_is_sequential(drg, ctx, orc, name, k, b, level, t, M):
+    # substeps = n_l bounds the Hogwild run to one sample in flight: one
+    # thread takes the epoch's samples in order, applying each at once -- the
+    # oracle's sequential loop.  Rounding differences propagate along the
+    # chain of samples, so the bar is the oracle's own sensitivity to an
+    # FP32-rounding-size perturbation (as for chained epochs) plus 1e-5 extent.
+    g = _graphs()[name]
+    orp, ocol, gd, tab = _device_tables(orc, g, k)
+    op = orc.Params(k=k, M=M, epochs=500, b=b, mode=1, stop_nodes=100, seed=7)
+    levels = orc.hierarchy(orp, ocol, op)
+    level = min(level, len(levels) - 1)
+    nl = levels[level].n
+    rng = np.random.default_rng(17 + level)
+    Y0 = (rng.normal(size=(nl, 2)) * np.sqrt(nl) * 0.3).astype(np.float32).astype(np.float64)
+    ref = orc.layout_level(tab, Y0.copy(), level, levels[level].anc, op, 0.1, t, t + 1)
+    sens = 0.0
+    for _ in range(3):
+        Yp = Y0 * (1 + 6e-8 * rng.standard_normal(Y0.shape))
+        sens = max(sens, np.max(np.abs(orc.layout_level(tab, Yp, level, levels[level].anc, op, 0.1, t, t + 1) - ref)))
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, k)
+    p = drg.Params.default(k=k, M=M, epochs=500, b=b, mode=1, substeps=nl, stop_nodes=100, seed=7)
+    H = drg.build_hierarchy(ctx, G, p)
+    Y = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
+    drg.layout_level(ctx, D, H, level, Y, p, 0.1, t, t + 1)
+    torch.cuda.synchronize()
+    got = Y.cpu().numpy().astype(np.float64).reshape(nl, 2)
+    err = np.max(np.abs(got - ref))
+    assert err <= 10 * sens + 1e-5 * _extent(ref), (err, sens, _extent(ref))
+    assert np.max(np.abs(ref - Y0)) > 1e-3
+
+
 @pytest.mark.parametrize("t0", [100, 480])
 def test_sync_epochs_chain(drg, ctx, orc, t0):
     # Five consecutive epochs from the oracle's state after t0 epochs.  The
