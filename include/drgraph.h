@@ -210,12 +210,15 @@ drg_status drg_init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const dr
  * ceil(n_l / substeps) samples in flight at any moment (bounding the
  * concurrency keeps asynchronous SGD close to the sequential method): with
  * FP32 positions, T <= ceil(n_l / substeps) threads each take every T-th
- * sample of an epoch, one at a time, in one cooperative launch with a grid
- * barrier between epochs; with half-precision copies, the synchronous runs'
- * structure.  pos (device, float[2 n_level]) is read and updated in place.
- * `gamma` overrides p->gamma (use p->gamma_coarsest on the coarsest level).
- * DRG_ETIMEOUT: an epoch barrier waited longer than 2 s (the positions are
- * then partly updated). */
+ * sample of an epoch, one at a time, in one cooperative launch in which a
+ * warp starts epoch t only when every warp has finished epoch t - 2 (epochs
+ * stay in step as in Sec. 4.3's shared epoch loop); with half-precision
+ * copies, the synchronous runs' structure.  With substeps >= n_level one
+ * sample is in flight and the run is the sequential method.  pos (device,
+ * float[2 n_level]) is read and updated in place.  `gamma` overrides
+ * p->gamma (use p->gamma_coarsest on the coarsest level).  DRG_ETIMEOUT: a
+ * wait for the other warps exceeded 2 s (the positions are then partly
+ * updated). */
 drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                             const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end);
 
@@ -269,14 +272,14 @@ drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
 drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
                             const float* b, float* const* pos);
 
-/* Self-check of the epoch barrier of the Hogwild level runs (no counterpart
- * in the paper).  `blocks` thread blocks (1 .. number of SMs), launched so
- * that all are resident at once, meet `rounds` times at a grid barrier that
- * completes after `arrivals` arrivals, each wait limited to timeout_ms (1 ..
- * 10000).  arrivals == blocks: DRG_OK.  arrivals > blocks: no barrier can
- * complete, every wait runs out, the blocks leave and the call returns
- * DRG_ETIMEOUT (the GPU stays usable).  DRG_EUNSUPPORTED when the blocks
- * cannot be resident together. */
+/* Self-check of the epoch gates of the Hogwild level runs (no counterpart in
+ * the paper).  `blocks` one-warp thread blocks (1 .. number of SMs), launched
+ * so that all are resident at once, run `rounds` (1 .. 100000) empty epochs;
+ * epoch e starts when `arrivals` warps have finished epoch e - 1, each wait
+ * limited to timeout_ms (1 .. 10000).  arrivals == blocks: DRG_OK.
+ * arrivals > blocks: no gate can open, every wait runs out, the warps leave
+ * and the call returns DRG_ETIMEOUT (the GPU stays usable).
+ * DRG_EUNSUPPORTED when the blocks cannot be resident together. */
 drg_status drg_check_epoch_barrier(drg_ctx* ctx, uint32_t blocks, uint32_t arrivals, uint32_t rounds,
                                    uint32_t timeout_ms);
 
