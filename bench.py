@@ -113,6 +113,21 @@ def algo_bytes_per_sample(kernel, M, precision, coarse, packed=True):
     return b
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's figure: whole-job timings are the maximum over ranks."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed (independent replicas, weak scaling) per second of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -250,7 +265,7 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    per_step = max(0.5, min(args.cpu_budget, 60.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
         oracle_sample(wl, per_step / 4)
     vals = []
@@ -284,7 +299,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle work for cpu_baseline; also caps each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--k", type=int, default=None, help="override the distance-matrix order (profiling cases)")
     ap.add_argument("--single-level", action="store_true", help="lay out G^0 only (profiling cases)")
@@ -370,14 +386,11 @@ def main():
     torch.cuda.synchronize()
     launches = ctx.launches - launches0
     clk = clocks.stop()
-    ms = sum(times) / len(times)
+    ms = max_over_ranks(sum(times) / len(times), dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     samples_per_step = ep_samples
-    value = samples_per_step * world / (ms / 1000.0)
+    value = whole_job_rate(samples_per_step, world, ms / 1000.0)
 
     # end to end through the public API from pinned host buffers
     e2e_times = []
@@ -389,8 +402,8 @@ def main():
         hpos = job.e2e()  # host pointers: the copies happen inside the calls
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times) / len(e2e_times)
-    e2e_value = samples_per_step * world / e2e_s
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), dist, "cuda")
+    e2e_value = whole_job_rate(samples_per_step, world, e2e_s)
     assert all(np.isfinite(x.numpy()).all() for x in hpos)
 
     if rank != 0:
