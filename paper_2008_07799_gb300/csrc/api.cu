@@ -3,6 +3,8 @@
 // turns any failure into a status code plus the context's error message.
 #include "prims.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <chrono>
 #include <cstdlib>
 #include <new>
@@ -42,13 +44,27 @@ static cudaEvent_t take_event(drg_ctx* ctx) {
     return e;
 }
 
+static const char* const kSpanNames[DRG_PROF_COUNT] = {
+    "drg level runs", "drg sync apply", "drg distance matrix", "drg hierarchy", "drg graph",
+    "drg k-order traversal", "drg similarity", "drg alias tables", "drg host allocations"};
+
+static void nvtx_push(int which) {
+    nvtxRangePushA(which >= 0 && which < DRG_PROF_COUNT ? kSpanNames[which] : "drg");
+}
+
 ProfSpan::ProfSpan(drg_ctx* c, int w, uint64_t u, uint64_t launches) : ctx(c), which(w), units(u), count(launches) {
+    nvtx_push(which);
+    nvtx_open = true;
     if (!ctx->prof) return;
     start = take_event(ctx);
     DRG_CUDA(cudaEventRecord(start, ctx->stream));
 }
 
 void ProfSpan::close() {
+    if (nvtx_open) {
+        nvtxRangePop();
+        nvtx_open = false;
+    }
     if (!start) return;
     cudaEvent_t stop = nullptr;
     if (!ctx->free_events.empty()) {
@@ -69,6 +85,8 @@ void ProfSpan::reopen(int w, uint64_t u) {
     which = w;
     units = u;
     count = 1;
+    nvtx_push(which);
+    nvtx_open = true;
     if (!ctx->prof) return;
     start = take_event(ctx);
     DRG_CUDA(cudaEventRecord(start, ctx->stream));
@@ -165,6 +183,8 @@ drg_status drg_create(drg_ctx** out, int device, void* stream) {
     {
         const char* env = std::getenv("DRG_DIRECT_LAUNCH");
         c->direct_launch = env && env[0] == '1';
+        const char* lim = std::getenv("DRG_BFS_STAGE_LIMIT");
+        if (lim && lim[0]) c->bfs_stage_limit = std::strtoll(lim, nullptr, 10);
     }
     DRG_CUDA(cudaSetDevice(device));
     DRG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));

@@ -58,6 +58,8 @@ struct drg_ctx {
     std::string err;
     uint64_t launches = 0;
     bool direct_launch = false;             // DRG_DIRECT_LAUNCH=1: no level graphs (for profilers)
+    int64_t bfs_stage_limit = -1;           // DRG_BFS_STAGE_LIMIT=<entries>: cap the k-order staging
+                                            // area (rows past it take the direct traversal); -1: none
     // profiling (drg_profile_*)
     bool prof = false;
     std::vector<drg_prof_span> spans;       // recorded, not yet read
@@ -152,12 +154,14 @@ struct DBuf {
 // Launch accounting: every kernel launch of the library goes through here.
 void after_launch(drg_ctx* ctx, const char* name);
 
-// Profiling spans (no-ops unless profiling is enabled on the context).
+// Profiling spans: an NVTX range always (free unless a tool listens), CUDA
+// events on the context stream when profiling is enabled on the context.
 struct ProfSpan {
     drg_ctx* ctx;
     int which;
     uint64_t units, count;
     cudaEvent_t start = nullptr;
+    bool nvtx_open = false;
     ProfSpan(drg_ctx* c, int w, uint64_t u, uint64_t launches = 1);
     ~ProfSpan() { close(); }
     void close();                          // end the span now (idempotent)

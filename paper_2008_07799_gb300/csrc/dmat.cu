@@ -616,6 +616,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     if (!k2) cap *= 4;  // a guess: rows that overflow it are traversed again
     if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
     cap += 16ull * n;  // each staged row is padded to a multiple of 16 entries
+    if (ctx->bfs_stage_limit >= 0 && (uint64_t)ctx->bfs_stage_limit < cap) cap = (uint64_t)ctx->bfs_stage_limit;
     DBuf<uint32_t> scol;
     DBuf<uint8_t> sdist;
     try {
