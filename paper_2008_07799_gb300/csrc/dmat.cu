@@ -588,7 +588,15 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     const bool smem_bm = bm_bytes + extra + 16384 <= (size_t)ctx->max_smem_optin;
     DRG_CHECK(extra + 16384 <= (size_t)ctx->max_smem_optin, DRG_EUNSUPPORTED, "graph too large for the BFS");
     const size_t dyn = (smem_bm ? bm_bytes : 0) + extra;
-    DRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    // The limit is process-wide per kernel and graphs differ in size (and may
+    // be built by several host threads at once): allow the kernel's maximum
+    // always; each launch passes its own size, which sets the occupancy.
+    {
+        cudaFuncAttributes fa;
+        DRG_CUDA(cudaFuncGetAttributes(&fa, kern));
+        DRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ctx->max_smem_optin - (int)fa.sharedSizeBytes));
+    }
     int per_sm = 0;
     DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BFS_THREADS, dyn));
     if (per_sm < 1) per_sm = 1;

@@ -13,8 +13,12 @@
 // throughput, not by arithmetic.
 #include "prims.cuh"
 
+#include <atomic>
 #include <cmath>
+#include <exception>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 
 namespace drg {
@@ -1188,6 +1192,29 @@ static void launch_apply_batch(drg_ctx* ctx, int prec, uint32_t grid, const Batc
 // lays out its level L_g - r.  A round is one CUDA graph: a WHILE loop over
 // the epochs whose body launches, for each sub-step run c, one batched
 // k_epoch over all active graphs (and the batched apply in synchronous mode).
+// A context for a host worker thread: the parent's device and settings, its
+// own stream, no profiling events.
+struct WorkerCtx {
+    drg_ctx c;
+    explicit WorkerCtx(const drg_ctx* parent) {
+        c.device = parent->device;
+        c.num_sms = parent->num_sms;
+        c.max_smem_optin = parent->max_smem_optin;
+        c.direct_launch = parent->direct_launch;
+        c.bfs_stage_limit = parent->bfs_stage_limit;
+        DRG_CUDA(cudaSetDevice(c.device));
+        DRG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        c.own_stream = true;
+    }
+    ~WorkerCtx() {
+        if (c.stream) cudaStreamDestroy(c.stream);  // released once its queued work is done
+    }
+    WorkerCtx(const WorkerCtx&) = delete;
+    WorkerCtx& operator=(const WorkerCtx&) = delete;
+};
+
+constexpr uint32_t kBatchPrepThreads = 8;
+
 void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
                   const float* b_per_graph, float* const* pos) {
     check_params(p);
@@ -1197,6 +1224,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
         DRG_CHECK(!b_per_graph || b_per_graph[g] > 0.f, DRG_EINVAL, "b must be positive");
     }
     if (count == 0) return;
+    std::vector<std::unique_ptr<WorkerCtx>> workers;  // outlive the tables they own (freed in free_all)
     struct GS {
         drg_dmat* d = nullptr;
         drg_hier* h = nullptr;
@@ -1219,11 +1247,52 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
         const bool sync_mode = p.mode == DRG_MODE_SYNC;
         const int prec = p.precision;
         uint32_t Lmax = 0;
+        // Distance matrices, tables and hierarchies of the graphs are
+        // independent: host worker threads build them concurrently, each on
+        // its own stream (sequentially when profiling, so that the phase
+        // timers stay meaningful).
+        const uint32_t nthreads = ctx->prof ? 1u : (count < kBatchPrepThreads ? count : kBatchPrepThreads);
+        if (nthreads <= 1) {
+            for (uint32_t g = 0; g < count; ++g) {
+                drg_params q = p;
+                q.gid = g;
+                gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma);
+                gs[g].h = build_hierarchy(ctx, graphs[g], q);
+            }
+        } else {
+            for (uint32_t w = 0; w < nthreads; ++w) workers.emplace_back(new WorkerCtx(ctx));
+            std::atomic<uint32_t> next{0};
+            std::atomic<bool> failed{false};
+            std::vector<std::exception_ptr> errs(nthreads);
+            std::vector<std::thread> th;
+            for (uint32_t w = 0; w < nthreads; ++w) {
+                th.emplace_back([&, w]() {
+                    try {
+                        DRG_CUDA(cudaSetDevice(ctx->device));
+                        drg_ctx* wc = &workers[w]->c;
+                        for (;;) {
+                            const uint32_t g = next.fetch_add(1);
+                            if (g >= count || failed.load()) break;
+                            drg_params q = p;
+                            q.gid = g;
+                            gs[g].d = build_dmat(wc, graphs[g], p.k, p.sigma);
+                            gs[g].h = build_hierarchy(wc, graphs[g], q);
+                        }
+                        sync(wc);
+                    } catch (...) {
+                        errs[w] = std::current_exception();
+                        failed.store(true);
+                    }
+                });
+            }
+            for (auto& t : th) t.join();
+            for (auto& w : workers) ctx->launches += w->c.launches;
+            for (auto& e : errs)
+                if (e) std::rethrow_exception(e);
+        }
         for (uint32_t g = 0; g < count; ++g) {
             drg_params q = p;
             q.gid = g;
-            gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma);
-            gs[g].h = build_hierarchy(ctx, graphs[g], q);
             gs[g].L = (uint32_t)gs[g].h->g.size() - 1;
             const uint32_t nL = gs[g].h->g[gs[g].L]->n;
             if (gs[g].L > 0) {
@@ -1373,6 +1442,10 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
         }
         sync(ctx);
     } catch (...) {
+        // tables owned by worker contexts are freed on their streams: let the
+        // main stream finish with them first
+        cudaStreamSynchronize(ctx->stream);
+        (void)cudaGetLastError();
         free_all();
         throw;
     }
