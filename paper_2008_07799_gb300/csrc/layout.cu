@@ -1126,16 +1126,64 @@ void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, u
     DRG_LAUNCH(ctx, k_draws, grid_for(s_end - s_begin, 256, (uint32_t)ctx->num_sms * 8), 256, 0, a, oi, oj, oneg);
 }
 
+// A context for a host worker thread: the parent's device and settings, its
+// own stream, no profiling events.
+struct WorkerCtx {
+    drg_ctx c;
+    explicit WorkerCtx(const drg_ctx* parent) {
+        c.device = parent->device;
+        c.num_sms = parent->num_sms;
+        c.max_smem_optin = parent->max_smem_optin;
+        c.direct_launch = parent->direct_launch;
+        c.bfs_stage_limit = parent->bfs_stage_limit;
+        DRG_CUDA(cudaSetDevice(c.device));
+        DRG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        c.own_stream = true;
+    }
+    ~WorkerCtx() {
+        if (c.stream) cudaStreamDestroy(c.stream);  // released once its queued work is done
+    }
+    WorkerCtx(const WorkerCtx&) = delete;
+    WorkerCtx& operator=(const WorkerCtx&) = delete;
+};
+
 // The whole path of Fig. 1: distance matrix and sampling tables on G^0,
 // hierarchy, random coarsest layout, then coarse to fine: all epochs of a
 // level, refinement to the next finer level.
 void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* pos) {
     check_params(p);
     DRG_CHECK(g && pos, DRG_EINVAL, "null argument");
-    drg_dmat* d = build_dmat(ctx, g, p.k, p.sigma);
+    drg_dmat* d = nullptr;
     drg_hier* h = nullptr;
+    std::unique_ptr<WorkerCtx> hw;  // owns h when built concurrently; freed after h
     try {
-        h = build_hierarchy(ctx, g, p);
+        if (ctx->prof) {
+            d = build_dmat(ctx, g, p.k, p.sigma);
+            h = build_hierarchy(ctx, g, p);
+        } else {
+            // the hierarchy does not need the distance matrix: a worker thread
+            // builds it on its own stream meanwhile
+            hw.reset(new WorkerCtx(ctx));
+            std::exception_ptr herr;
+            std::thread th([&]() {
+                try {
+                    DRG_CUDA(cudaSetDevice(ctx->device));
+                    h = build_hierarchy(&hw->c, g, p);
+                    sync(&hw->c);
+                } catch (...) {
+                    herr = std::current_exception();
+                }
+            });
+            try {
+                d = build_dmat(ctx, g, p.k, p.sigma);
+            } catch (...) {
+                th.join();
+                throw;
+            }
+            th.join();
+            ctx->launches += hw->c.launches;
+            if (herr) std::rethrow_exception(herr);
+        }
         const uint32_t L = (uint32_t)h->g.size() - 1;
         DBuf<float2> cur, nxt;
         float* cur_pos = pos;
@@ -1160,6 +1208,8 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
         }
         sync(ctx);
     } catch (...) {
+        cudaStreamSynchronize(ctx->stream);
+        (void)cudaGetLastError();
         hier_free(h);
         dmat_free(d);
         throw;
@@ -1192,27 +1242,6 @@ static void launch_apply_batch(drg_ctx* ctx, int prec, uint32_t grid, const Batc
 // lays out its level L_g - r.  A round is one CUDA graph: a WHILE loop over
 // the epochs whose body launches, for each sub-step run c, one batched
 // k_epoch over all active graphs (and the batched apply in synchronous mode).
-// A context for a host worker thread: the parent's device and settings, its
-// own stream, no profiling events.
-struct WorkerCtx {
-    drg_ctx c;
-    explicit WorkerCtx(const drg_ctx* parent) {
-        c.device = parent->device;
-        c.num_sms = parent->num_sms;
-        c.max_smem_optin = parent->max_smem_optin;
-        c.direct_launch = parent->direct_launch;
-        c.bfs_stage_limit = parent->bfs_stage_limit;
-        DRG_CUDA(cudaSetDevice(c.device));
-        DRG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
-        c.own_stream = true;
-    }
-    ~WorkerCtx() {
-        if (c.stream) cudaStreamDestroy(c.stream);  // released once its queued work is done
-    }
-    WorkerCtx(const WorkerCtx&) = delete;
-    WorkerCtx& operator=(const WorkerCtx&) = delete;
-};
-
 constexpr uint32_t kBatchPrepThreads = 8;
 
 void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
