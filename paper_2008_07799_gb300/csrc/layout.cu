@@ -1,16 +1,20 @@
 // The layout optimisation of DRGraph (Sec. 3.2.2, Eqs. 11-12) on one level
 // of the hierarchy (Sec. 3.2.3), and the whole coarse-to-fine run.
 //
-// Hot kernel k_epoch: one thread per edge sample.  It draws the sample's
-// random words from Philox (counter = sample, epoch, stream tag, call), reads
-// one 32-byte edge-table record (positive pair) and M node-table records
-// (negatives), maps the drawn level-0 nodes to the level through the
-// ancestor map, gathers 2 + M positions, forms the attractive and repulsive
-// pair forces and adds them, with vector atomics, to the gradient buffer
-// (synchronous mode) or straight into the positions (Hogwild mode).  Every
-// access after the Philox step is a random 8- to 32-byte read or atomic; the
-// kernel is bound by L2 (positions, node table) and HBM (edge table) request
-// throughput, not by arithmetic.
+// A sample draws its random words from Philox (counter = sample, epoch,
+// stream tag, call), reads one edge-table record (positive pair) and M
+// node-table records (negatives), maps the drawn level-0 nodes to the level
+// through the ancestor map, gathers 2 + M positions, forms the attractive and
+// repulsive pair forces and adds them, with vector atomics, to the gradient
+// buffer (synchronous mode) or straight into the positions (Hogwild mode).
+// Every access after the Philox step is a random 8- to 16-byte read or
+// atomic: the kernels are bound by L2 (positions, node tables) and HBM (edge
+// table) request rate and latency, not by arithmetic.
+//
+// Two kernel families run the samples: k_hogwild (FP32 Hogwild: one
+// cooperative launch per level run, each thread walking its share of every
+// epoch) and k_epoch (synchronous mode and half-precision copies: one thread
+// per sample of a sub-step run, the runs of an epoch chained in a CUDA graph).
 #include "prims.cuh"
 
 #include <atomic>
