@@ -442,6 +442,8 @@ def main():
                    "l2": "1 GiB buffer written between timed steps (flush)",
                    "parallelism": f"replicas x{world}"},
         "phases_ms": {"distance_matrix_and_tables": dm_ms, "hierarchy": hi_ms, "layout_levels": ep_ms, **sub_ms},
+        "phases_note": "CUDA-event timers of one profiled step, in which builds that the timed steps run "
+                       "concurrently (hierarchy beside the distance matrix; a batch's graphs) run one after another",
         "gpu_launches": launches,
         "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
