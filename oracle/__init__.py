@@ -95,6 +95,11 @@ def lib():
                                 C.c_uint32, U32P]
     L.orc_cluster_ids.argtypes = [C.c_uint32, U32P, U32P]
     L.orc_cluster_ids.restype = C.c_uint32
+    L.orc_star_group.argtypes = [C.c_uint32, U64P, U32P, U32P, U32P]
+    L.orc_star_priorities.argtypes = [C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, U32P]
+    L.orc_star_priorities.restype = None
+    L.orc_star_cluster_ids.argtypes = [C.c_uint32, U32P, U32P]
+    L.orc_star_cluster_ids.restype = C.c_uint32
     L.orc_contract.argtypes = [C.c_uint32, U64P, U32P, C.c_void_p, U32P, C.c_uint32, U64P, C.c_void_p, C.c_void_p]
     L.orc_contract.restype = C.c_int64
     L.orc_neighbourhood_preservation.argtypes = [C.c_uint32, U64P, U32P, F64P, C.c_uint32, C.c_uint32,
@@ -130,6 +135,7 @@ class Params:
     stop_nodes: int = 1000     # coarsen while the level has at least this many nodes
     rho: float = 0.8           # stop when a coarser level keeps more than rho of the nodes
     match_rounds: int = 8      # handshake rounds of heavy-edge matching
+    coarsen: int = 0           # 0 heavy-edge matching, 1 the paper's star grouping (Sec. 3.2.3)
     max_levels: int = 32
     init_scale: float = 1e-4   # coarsest positions uniform in [-s, s]^2
     multilevel: bool = True
@@ -351,6 +357,39 @@ def cluster_ids(match):
     return cid[:len(match)], int(nc)
 
 
+def star_priorities(n, p: Params, level):
+    """The random order of the star grouping at `level` (Philox purpose 3)."""
+    prio = np.zeros(max(n, 1), np.uint32)
+    lib().orc_star_priorities(n, p.seed, p.gid, level, prio)
+    return prio[:n]
+
+
+def star_group(rp, col, prio):
+    """Sec. 3.2.3 grouping walked in the order (prio[v], v): centre[v] is the
+    picked node whose group v joined."""
+    n = len(rp) - 1
+    centre = np.zeros(max(n, 1), np.uint32)
+    assert lib().orc_star_group(n, np.ascontiguousarray(rp, np.uint64),
+                                col if len(col) else np.zeros(1, np.uint32),
+                                np.ascontiguousarray(prio, np.uint32) if n else np.zeros(1, np.uint32),
+                                centre) == 0
+    return centre[:n]
+
+
+def star_cluster_ids(centre):
+    cid = np.zeros(max(len(centre), 1), np.uint32)
+    nc = lib().orc_star_cluster_ids(len(centre), np.ascontiguousarray(centre, np.uint32), cid)
+    return cid[:len(centre)], int(nc)
+
+
+def cluster(rp, col, w, p: Params, level):
+    """Coarse node id of every node of a level, and their number, under the
+    rule p.coarsen selects."""
+    if p.coarsen == 1:
+        return star_cluster_ids(star_group(rp, col, star_priorities(len(rp) - 1, p, level)))
+    return cluster_ids(hem_match(rp, col, w, p, level))
+
+
 def contract(rp, col, w, cid, nc):
     n = len(rp) - 1
     L = lib()
@@ -386,8 +425,7 @@ def hierarchy(rp, col, p: Params):
     while p.multilevel and len(levels) < p.max_levels and levels[-1].n >= p.stop_nodes:
         cur = levels[-1]
         lvl = len(levels) - 1
-        match = hem_match(cur.rp, cur.col, cur.w, p, lvl)
-        cid, nc = cluster_ids(match)
+        cid, nc = cluster(cur.rp, cur.col, cur.w, p, lvl)
         if nc > p.rho * cur.n:
             break
         crp, ccol, cw = contract(cur.rp, cur.col, cur.w, cid, nc)

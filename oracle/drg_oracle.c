@@ -58,7 +58,8 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 }
 
 /* Stream tag of the Philox counter's third word: purpose (0 = layout
- * samples, 1 = initial positions, 2 = matching tie-break), graph id, level. */
+ * samples, 1 = initial positions, 2 = matching tie-break, 3 = order of the
+ * star grouping), graph id, level. */
 uint32_t orc_tag(uint32_t purpose, uint32_t gid, uint32_t level)
 {
     return (purpose << 28) | ((gid & 0xFFFFFu) << 8) | (level & 0xFFu);
@@ -585,6 +586,63 @@ uint32_t orc_cluster_ids(uint32_t n, const uint32_t* match, uint32_t* cid)
         uint32_t m = match[v];
         if (m < v) cid[v] = cid[m];
     }
+    return nc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2.3 "Coarsening" as the paper states it (Fig. 3): pick a node at
+ * random among those not yet grouped, make it and its still ungrouped
+ * first-order neighbours one node of the coarser graph, and repeat until no
+ * node is left.  Picking uniformly among the ungrouped nodes is the same as
+ * walking one uniformly random order of all nodes and skipping the grouped
+ * ones; the order is increasing (prio[v], v).  prio comes in as an input
+ * (orc_star_priorities draws it) so that tests can set it by hand.
+ * centre[v] = the picked node whose group v joined (centre[c] = c for a
+ * picked node).  Pinned by hand-worked paths, stars, cycles and cliques and
+ * by the independent-set characterisation on random graphs.               */
+static int orc_cmp_u64(const void* a, const void* b)
+{
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+int orc_star_group(uint32_t n, const uint64_t* rp, const uint32_t* col, const uint32_t* prio, uint32_t* centre)
+{
+    uint64_t* order = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n ? n : 1));
+    if (!order) return -1;
+    for (uint32_t v = 0; v < n; ++v) {
+        order[v] = ((uint64_t)prio[v] << 32) | v;
+        centre[v] = ORC_NONE;
+    }
+    qsort(order, n, sizeof(uint64_t), orc_cmp_u64);
+    for (uint32_t x = 0; x < n; ++x) {
+        uint32_t v = (uint32_t)order[x];
+        if (centre[v] != ORC_NONE) continue;      /* already grouped: skipped */
+        centre[v] = v;
+        for (uint64_t e = rp[v]; e < rp[v + 1]; ++e)
+            if (centre[col[e]] == ORC_NONE) centre[col[e]] = v;
+    }
+    free(order);
+    return 0;
+}
+
+/* The random order of the grouping at `level`: word 0 of the Philox stream
+ * (v, 0, tag) with purpose 3.                                              */
+void orc_star_priorities(uint32_t n, uint64_t seed, uint32_t gid, uint32_t level, uint32_t* prio)
+{
+    uint32_t tag = orc_tag(3, gid, level);
+    for (uint32_t v = 0; v < n; ++v) prio[v] = orc_word(seed, v, 0, tag, 0);
+}
+
+/* Coarse node ids of a grouping: picked nodes numbered in increasing id
+ * order, every node takes its centre's number.  Returns the number of groups. */
+uint32_t orc_star_cluster_ids(uint32_t n, const uint32_t* centre, uint32_t* cid)
+{
+    uint32_t nc = 0;
+    for (uint32_t v = 0; v < n; ++v)
+        if (centre[v] == v) cid[v] = nc++;
+    for (uint32_t v = 0; v < n; ++v)
+        if (centre[v] != v) cid[v] = cid[centre[v]];
     return nc;
 }
 

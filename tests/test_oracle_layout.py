@@ -246,6 +246,110 @@ def test_hierarchy_bounds(orc):
         assert np.array_equal(anc, levels[l - 1].parent[prev])
 
 
+# ------------------------------------------------- star grouping (Sec. 3.2.3)
+def _graph(n, edges):
+    import oracle as orc
+    e = np.array(edges, np.int64).reshape(-1, 2)
+    return orc.canonical_graph(n, e[:, 0], e[:, 1])
+
+
+def test_star_group_path_by_hand(orc):
+    # order 1, 3, 4, 0, 2: picking 1 groups {0, 1, 2}; 3 then takes 4
+    rp, col = _graph(5, [(0, 1), (1, 2), (2, 3), (3, 4)])
+    centre = orc.star_group(rp, col, np.array([3, 0, 4, 1, 2], np.uint32))
+    assert centre.tolist() == [1, 1, 1, 3, 3]
+    cid, nc = orc.star_cluster_ids(centre)
+    assert cid.tolist() == [0, 0, 0, 1, 1] and nc == 2
+
+
+@pytest.mark.parametrize("first", ["hub", "leaf"])
+def test_star_group_star_graph(orc, first):
+    # K_{1,5}: the hub picked first swallows every leaf; a leaf picked first
+    # takes the hub and leaves the other four leaves alone
+    rp, col = _graph(6, [(0, v) for v in range(1, 6)])
+    prio = np.array([0, 1, 2, 3, 4, 5] if first == "hub" else [1, 0, 2, 3, 4, 5], np.uint32)
+    centre = orc.star_group(rp, col, prio)
+    if first == "hub":
+        assert centre.tolist() == [0] * 6
+    else:
+        assert centre.tolist() == [1, 1, 2, 3, 4, 5]
+    assert orc.star_cluster_ids(centre)[1] == (1 if first == "hub" else 5)
+
+
+@pytest.mark.parametrize("n", range(3, 13))
+def test_star_group_cycle_in_id_order(orc, n):
+    # C_n walked 0, 1, 2, ...: 0 takes n-1 and 1, then every second node
+    # takes its successor; 1 + ceil((n - 3) / 2) groups
+    rp, col = _graph(n, [(v, (v + 1) % n) for v in range(n)])
+    centre = orc.star_group(rp, col, np.arange(n, dtype=np.uint32))
+    assert orc.star_cluster_ids(centre)[1] == 1 + (n - 3 + 1) // 2
+    assert centre[0] == 0 and centre[1] == 0 and centre[n - 1] == 0
+    if n == 6:
+        assert centre.tolist() == [0, 0, 2, 2, 4, 0]
+
+
+def test_star_group_clique_and_edgeless(orc):
+    n = 9
+    prio = np.array([7, 3, 9, 1, 8, 1, 5, 6, 2], np.uint32)    # tie 3 / 5 goes to the smaller id
+    rp, col = _graph(n, [(a, b) for a in range(n) for b in range(a + 1, n)])
+    assert orc.star_group(rp, col, prio).tolist() == [3] * n
+    rp0, col0 = _graph(n, np.zeros((0, 2)))
+    centre = orc.star_group(rp0, col0, prio)
+    assert centre.tolist() == list(range(n))
+    assert orc.star_cluster_ids(centre)[0].tolist() == list(range(n))
+
+
+def test_star_priorities_stream(orc):
+    p = orc.Params(seed=0x1234_5678_9ABC, gid=7)
+    prio = orc.star_priorities(50, p, 2)
+    key = [p.seed & 0xFFFFFFFF, p.seed >> 32]
+    tag = (3 << 28) | (7 << 8) | 2
+    assert [int(x) for x in prio[:5]] == [int(orc.philox([v, 0, tag, 0], key)[0]) for v in range(5)]
+    assert not np.array_equal(prio, orc.star_priorities(50, p, 3))
+
+
+@pytest.mark.parametrize("gen", [lambda: gg.grid(20, 17), lambda: gg.barabasi_albert(500, 3, 2),
+                                 lambda: gg.random_binary_tree(300, 1), lambda: gg.erdos_renyi(200, 150, 3)])
+def test_star_group_is_first_maximal_independent_set(orc, gen):
+    # The walk picks exactly the nodes none of whose earlier neighbours was
+    # picked (the lexicographically first maximal independent set of the
+    # order), and every other node joins its earliest picked neighbour.
+    n, s, d = gen()
+    rp, col = orc.canonical_graph(n, s, d)
+    prio = orc.star_priorities(n, orc.Params(seed=5), 0)
+    centre = orc.star_group(rp, col, prio).astype(np.int64)
+    order = (prio.astype(np.uint64) << np.uint64(32)) | np.arange(n, dtype=np.uint64)
+    rows = np.repeat(np.arange(n), np.diff(rp.astype(np.int64)))
+    cols = col.astype(np.int64)
+    picked = centre == np.arange(n)
+    assert not np.any(picked[rows] & picked[cols])                 # independent
+    earlier_picked = np.zeros(n, bool)
+    np.logical_or.at(earlier_picked, rows, picked[cols] & (order[cols] < order[rows]))
+    assert np.array_equal(picked, ~earlier_picked)                # first in the order
+    none = np.iinfo(np.uint64).max
+    best = np.full(n, none, np.uint64)
+    np.minimum.at(best, rows[picked[cols]], order[cols[picked[cols]]])
+    non = ~picked
+    assert np.all(best[non] < none)                                # maximal
+    assert np.array_equal(centre[non], (best[non] & np.uint64(0xFFFFFFFF)).astype(np.int64))  # earliest picked
+    cid, nc = orc.star_cluster_ids(centre.astype(np.uint32))
+    assert nc == picked.sum()
+    assert np.array_equal(cid[picked], np.arange(nc))             # numbered by centre id
+    assert np.array_equal(cid, cid[centre])
+
+
+def test_star_hierarchy_bounds(orc):
+    n, s, d = gg.barabasi_albert(3000, 3, 1)
+    rp, col = orc.canonical_graph(n, s, d)
+    star = [lv.n for lv in orc.hierarchy(rp, col, orc.Params(stop_nodes=100, coarsen=1))]
+    hem = [lv.n for lv in orc.hierarchy(rp, col, orc.Params(stop_nodes=100))]
+    assert star[0] == n and len(star) > 2
+    for a, b in zip(star, star[1:]):
+        assert b <= 0.8 * a
+    assert star[1] < hem[1]              # groups of a node and all its neighbours shrink faster than pairs
+    assert sum(star) <= 5 * n
+
+
 # ---------------------------------------------------------------- metrics
 def test_metrics_of_a_path_on_a_line(orc):
     n, s, d = gg.path(40)
