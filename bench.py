@@ -225,6 +225,7 @@ def make_params(drg, wl, args, gid):
         p.multilevel = wl["multilevel"]
     if args.substeps:
         p.substeps = args.substeps
+    p.coarsen = {"hem": 0, "star": 1}[args.coarsen]
     return p
 
 
@@ -308,6 +309,8 @@ def main():
     ap.add_argument("--k", type=int, default=None, help="override the distance-matrix order (profiling cases)")
     ap.add_argument("--single-level", action="store_true", help="lay out G^0 only (profiling cases)")
     ap.add_argument("--once", action="store_true", help="run exactly one step and exit (for ncu captures)")
+    ap.add_argument("--coarsen", default="hem", choices=["hem", "star"],
+                    help="coarsening rule: heavy-edge matching or the paper's star grouping (Sec. 3.2.3)")
     ap.add_argument("--substeps", type=int, default=None, help="override the in-flight bound n_l / substeps (profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -337,6 +340,8 @@ def main():
     if args.single_level:
         wl["multilevel"] = 0
         wl["desc"] += " (single level)"
+    if args.coarsen == "star":
+        wl["desc"] = wl["desc"].replace("multilevel HEM", "multilevel star grouping")
     stream = torch.cuda.current_stream()
     ctx = drg.Context(local, stream.cuda_stream)
     p = make_params(drg, wl, args, gid=rank)
@@ -437,7 +442,7 @@ def main():
         "dtype": "f32" if prec == 0 else ("f32+f16" if prec == 1 else "f32+bf16"),
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "mode": args.mode, "precision": args.precision,
-                   "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
+                   "coarsen": args.coarsen, "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
                    "samples_per_step": samples_per_step, "layout_time_ms": ms,
                    "l2": "1 GiB buffer written between timed steps (flush)",
                    "parallelism": f"replicas x{world}"},

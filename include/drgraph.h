@@ -11,7 +11,8 @@
  *                                          similarity (Eqs. 4, 9) and the
  *                                          sampling tables of Sec. 3.2.2
  *   drg_coarsen / drg_build_hierarchy
- *                              Sec. 3.2.3 coarsening (heavy-edge matching)
+ *                              Sec. 3.2.3 coarsening (the paper's star grouping
+ *                                          or heavy-edge matching)
  *   drg_layout_level           Sec. 3.2.2-3.2.3  epochs of negative-sampling SGD
  *                                          (Eqs. 11-12) at one level, samples
  *                                          drawn on G^0, gradients forwarded to
@@ -87,6 +88,7 @@ typedef struct {
     uint32_t match_rounds;   /* handshake rounds of heavy-edge matching */
     uint32_t max_levels;     /* at most this many levels, 1..64 */
     int32_t multilevel;      /* 0: lay out G^0 only */
+    int32_t coarsen;         /* DRG_COARSEN_HEM or DRG_COARSEN_STAR (Sec. 3.2.3) */
 } drg_params;
 
 /* Mode and precision values. */
@@ -95,6 +97,14 @@ typedef struct {
 #define DRG_PREC_FP32 0
 #define DRG_PREC_FP16 1
 #define DRG_PREC_BF16 2
+
+/* Coarsening rules.  HEM: heavy-edge matching, handshake rounds (pairs of
+ * nodes).  STAR: the paper's grouping (Sec. 3.2.3, Fig. 3): nodes taken in a
+ * random order (Philox word 0 of counter (v, 0, tag), ties by id); each node
+ * not yet grouped when taken forms a coarse node with its ungrouped
+ * neighbours. */
+#define DRG_COARSEN_HEM 0
+#define DRG_COARSEN_STAR 1
 
 void drg_params_default(drg_params* p);
 const char* drg_status_string(drg_status s);
@@ -160,14 +170,20 @@ drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_b
 drg_status drg_dmat_destroy(drg_dmat* d);
 
 /* ---------------------------------------------------------------- hierarchy */
-/* Sec. 3.2.3 "Coarsening", with heavy-edge matching in place of the paper's
- * star grouping: `rounds` deterministic handshake rounds (each unmatched node
- * proposes to its unmatched neighbour of largest (edge weight, Philox hash of
- * the pair and round, smaller id); mutual proposals match), unmatched nodes
- * stay single; representative min(v, mate(v)), coarse ids numbered in
- * representative order; coarse edge weights are sums of fine edge weights.
- * `level` selects the hash stream.  parent (device, n_fine uint32) receives
- * the coarse id of every fine node.  Synchronises. */
+/* Sec. 3.2.3 "Coarsening": one coarser level under the rule p->coarsen picks.
+ * DRG_COARSEN_HEM: heavy-edge matching, p->match_rounds deterministic
+ * handshake rounds (each unmatched node proposes to its unmatched neighbour of
+ * largest (edge weight, Philox hash of the pair and round, smaller id); mutual
+ * proposals match), unmatched nodes stay single; representative
+ * min(v, mate(v)).  DRG_COARSEN_STAR: the paper's grouping (Fig. 3): nodes
+ * taken in the order (Philox word 0 of counter (v, 0, tag), v) with purpose
+ * 3; a node not yet grouped when taken becomes a centre and takes its
+ * ungrouped neighbours, so every other node joins its neighbour centre
+ * earliest in the order; representative = the centre.  Coarse ids are
+ * numbered in representative id order; coarse edge weights are sums of fine
+ * edge weights.  `level` selects the random stream.  parent (device, n_fine
+ * uint32) receives the coarse id of every fine node.  DRG_EINVAL for an
+ * unknown rule.  Synchronises. */
 drg_status drg_coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params* p,
                        drg_graph** coarse, uint32_t* parent);
 /* Repeated drg_coarsen from G^0 while the level has >= p->stop_nodes nodes,

@@ -56,7 +56,7 @@ class Params(C.Structure):
         ("sigma", C.c_float), ("clip", C.c_float), ("init_scale", C.c_float), ("rho", C.c_float),
         ("seed", C.c_uint64), ("gid", C.c_uint32), ("mode", C.c_int32), ("precision", C.c_int32),
         ("substeps", C.c_uint32), ("stop_nodes", C.c_uint32), ("match_rounds", C.c_uint32),
-        ("max_levels", C.c_uint32), ("multilevel", C.c_int32),
+        ("max_levels", C.c_uint32), ("multilevel", C.c_int32), ("coarsen", C.c_int32),
     ]
 
     @classmethod

@@ -158,6 +158,7 @@ void drg_params_default(drg_params* p) {
     p->match_rounds = 8;
     p->max_levels = 32;
     p->multilevel = 1;
+    p->coarsen = DRG_COARSEN_HEM;
 }
 
 const char* drg_status_string(drg_status s) {
@@ -376,6 +377,8 @@ drg_status drg_coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, cons
     if (!ctx || !fine || !p || !coarse || !parent) return DRG_EINVAL;
     *coarse = nullptr;
     API_TRY
+    DRG_CHECK(p->coarsen == DRG_COARSEN_HEM || p->coarsen == DRG_COARSEN_STAR, DRG_EINVAL,
+              "coarsen must be DRG_COARSEN_HEM or DRG_COARSEN_STAR");
     *coarse = drg::coarsen(ctx, fine, level, *p, parent);
     API_CATCH(ctx)
 }

@@ -17,7 +17,7 @@ namespace drg {
 typedef unsigned __int128 u128;
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr uint32_t kPurposeSample = 0, kPurposeInit = 1, kPurposeMatch = 2;
+constexpr uint32_t kPurposeSample = 0, kPurposeInit = 1, kPurposeMatch = 2, kPurposeStar = 3;
 
 // ------------------------------------------------------------------ errors
 struct Error {

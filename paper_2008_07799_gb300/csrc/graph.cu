@@ -1,6 +1,6 @@
 // Graphs on the device: the canonical CSR of Sec. 3.1 and the multilevel
-// hierarchy of Sec. 3.2.3 (heavy-edge-matching coarsening, contraction and
-// ancestor maps).
+// hierarchy of Sec. 3.2.3 (coarsening by heavy-edge matching or by the
+// paper's star grouping, contraction and ancestor maps).
 #include "prims.cuh"
 
 namespace drg {
@@ -245,6 +245,128 @@ uint32_t hem_cluster(drg_ctx* ctx, const drg_graph* g, uint32_t level, const drg
     return read1(ctx, nc.p);
 }
 
+// ------------------------------------------------------------------ star grouping
+// Sec. 3.2.3 as the paper states it: walk a random order of the nodes; a node
+// not yet grouped when reached becomes a centre and takes its ungrouped
+// neighbours.  The centres are the first maximal independent set of the
+// order (v is a centre iff none of its earlier neighbours is), and every other
+// node joins its earliest centre neighbour.  Rounds decide each open node
+// whose earlier neighbours are all decided; a decided state never changes,
+// so a stale read only delays a decision, and the earliest open node always
+// decides, so at most n rounds run (a handful on random orders).
+constexpr uint8_t kStarOpen = 0, kStarCentre = 1, kStarCovered = 2;
+
+__device__ __forceinline__ uint64_t star_key(const uint32_t* prio, uint32_t v) {
+    return ((uint64_t)prio[v] << 32) | v;
+}
+
+__global__ void k_star_prio(uint32_t* __restrict__ prio, uint32_t n, uint2 key, uint32_t tag) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        prio[v] = philox(make_uint4((uint32_t)v, 0u, tag, 0u), key).x;
+}
+
+// One warp per open node; `open` counts the nodes still open after the round.
+__global__ void k_star_round(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                             const uint32_t* __restrict__ prio, uint8_t* state, uint32_t n,
+                             uint32_t* __restrict__ open) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const volatile uint8_t* vstate = state;
+    for (uint64_t vv = warp0; vv < n; vv += nwarps) {
+        const uint32_t v = (uint32_t)vv;
+        if (state[v] != kStarOpen) continue;
+        const uint64_t kv = star_key(prio, v);
+        bool centre = false, pending = false;
+        for (uint64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+            const uint32_t u = col[e];
+            if (star_key(prio, u) >= kv) continue;
+            const uint8_t s = vstate[u];
+            centre |= s == kStarCentre;
+            pending |= s == kStarOpen;
+        }
+        const bool any_centre = __any_sync(0xFFFFFFFFu, centre);
+        const bool any_pending = __any_sync(0xFFFFFFFFu, pending);
+        if (lane == 0) {
+            if (any_centre) state[v] = kStarCovered;
+            else if (!any_pending) state[v] = kStarCentre;
+            else atomicAdd(open, 1u);
+        }
+    }
+}
+
+// centre[v]: v for a centre, else the neighbour centre earliest in the order.
+// A covered node always has a centre neighbour; `bad` records one without
+// (v keeps itself, so every later index stays in range).
+__global__ void k_star_assign(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                              const uint32_t* __restrict__ prio, const uint8_t* __restrict__ state,
+                              uint32_t* __restrict__ centre, uint32_t n, uint32_t* __restrict__ bad) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t vv = warp0; vv < n; vv += nwarps) {
+        const uint32_t v = (uint32_t)vv;
+        if (state[v] == kStarCentre) {
+            if (lane == 0) centre[v] = v;
+            continue;
+        }
+        uint64_t best = ~0ull;
+        for (uint64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+            const uint32_t u = col[e];
+            if (state[u] != kStarCentre) continue;
+            const uint64_t ku = star_key(prio, u);
+            best = ku < best ? ku : best;
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+            best = o < best ? o : best;
+        }
+        if (lane == 0) {
+            if (best == ~0ull || state[v] != kStarCovered) {
+                *bad = 1u;
+                centre[v] = v;
+            } else {
+                centre[v] = (uint32_t)best;
+            }
+        }
+    }
+}
+
+struct CentreFlag {
+    const uint8_t* state;
+    __device__ __forceinline__ uint32_t operator()(size_t v) const { return state[v] == kStarCentre ? 1u : 0u; }
+};
+
+__global__ void k_star_ids(const uint32_t* __restrict__ centre, const uint32_t* __restrict__ rank,
+                           uint32_t* __restrict__ cid, uint32_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+        cid[v] = rank[centre[v]];
+}
+
+uint32_t star_cluster(drg_ctx* ctx, const drg_graph* g, uint32_t level, const drg_params& p, uint32_t* cid) {
+    const uint32_t n = g->n;
+    DBuf<uint32_t> prio(ctx, n), centre(ctx, n), rank(ctx, n), open(ctx, 1), nc(ctx, 1), bad(ctx, 1);
+    DBuf<uint8_t> state(ctx, n);
+    DRG_CUDA(cudaMemsetAsync(state.p, kStarOpen, n, ctx->stream));
+    const uint2 key = seed_key(p.seed);
+    const uint32_t gw = grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16);
+    const uint32_t gt = grid_for(n, 256, (uint32_t)ctx->num_sms * 32);
+    DRG_LAUNCH(ctx, k_star_prio, gt, 256, 0, prio.p, n, key, stream_tag(kPurposeStar, p.gid, level));
+    for (uint64_t round = 0;; ++round) {
+        DRG_CHECK(round <= n, DRG_ECUDA, "star grouping made no progress");
+        DRG_CUDA(cudaMemsetAsync(open.p, 0, sizeof(uint32_t), ctx->stream));
+        DRG_LAUNCH(ctx, k_star_round, gw, 256, 0, g->rp, g->col, prio.p, state.p, n, open.p);
+        if (n == 0 || read1(ctx, open.p) == 0) break;
+    }
+    DRG_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(uint32_t), ctx->stream));
+    DRG_LAUNCH(ctx, k_star_assign, gw, 256, 0, g->rp, g->col, prio.p, state.p, centre.p, n, bad.p);
+    DRG_CHECK(read1(ctx, bad.p) == 0, DRG_ECUDA, "star grouping left a node without a centre");
+    scan<uint32_t>(ctx, CentreFlag{state.p}, n, rank.p, false, nc.p);
+    DRG_LAUNCH(ctx, k_star_ids, gt, 256, 0, centre.p, rank.p, cid, n);
+    return read1(ctx, nc.p);
+}
+
 drg_graph* contract(drg_ctx* ctx, const drg_graph* g, const uint32_t* cid, uint32_t nc) {
     drg_graph* c = new drg_graph();
     c->ctx = ctx;
@@ -271,11 +393,13 @@ drg_graph* contract(drg_ctx* ctx, const drg_graph* g, const uint32_t* cid, uint3
     return c;
 }
 
-// Sec. 3.2.3 coarsening step.  With rho > 0 a candidate keeping more than rho
+// Sec. 3.2.3 coarsening step (heavy-edge matching or the paper's star
+// grouping, as p.coarsen selects).  With rho > 0 a candidate keeping more than rho
 // of the nodes is rejected (nullptr returned, parent left written).
 static drg_graph* coarsen_impl(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params& p,
                                uint32_t* parent, double rho) {
-    const uint32_t nc = hem_cluster(ctx, fine, level, p, parent);
+    const uint32_t nc = p.coarsen == DRG_COARSEN_STAR ? star_cluster(ctx, fine, level, p, parent)
+                                                      : hem_cluster(ctx, fine, level, p, parent);
     if (rho > 0.0 && (double)nc > rho * (double)fine->n) return nullptr;
     return contract(ctx, fine, parent, nc);
 }

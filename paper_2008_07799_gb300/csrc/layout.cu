@@ -757,6 +757,8 @@ void check_params(const drg_params& p) {
     DRG_CHECK(p.substeps >= 1, DRG_EINVAL, "substeps must be >= 1");
     DRG_CHECK(p.max_levels >= 1 && p.max_levels <= 64, DRG_EINVAL, "max_levels must be in [1, 64]");
     DRG_CHECK(p.rho > 0.f && p.rho <= 1.f, DRG_EINVAL, "rho must be in (0, 1]");
+    DRG_CHECK(p.coarsen == DRG_COARSEN_HEM || p.coarsen == DRG_COARSEN_STAR, DRG_EINVAL,
+              "coarsen must be DRG_COARSEN_HEM or DRG_COARSEN_STAR");
 }
 
 static int int_b(float b) {

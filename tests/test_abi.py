@@ -45,8 +45,23 @@ def test_params_layout_and_defaults(drg):
     assert abs(p.gamma - 0.1) < 1e-7 and abs(p.gamma_coarsest - 0.01) < 1e-9
     assert p.b == 1.0 and p.lr0 == 1.0 and p.sigma == 1.0 and p.clip == 5.0 and abs(p.rho - 0.8) < 1e-7
     assert p.init_scale == float(np.float32(1e-4))
-    assert p.seed == 0 and p.mode == 0 and p.precision == 0 and p.multilevel == 1
-    assert C.sizeof(drg.Params) == 88
+    assert p.seed == 0 and p.mode == 0 and p.precision == 0 and p.multilevel == 1 and p.coarsen == 0
+    assert C.sizeof(drg.Params) == 96
+
+
+def test_params_mirror_matches_the_header(drg, tmp_path):
+    # the ctypes mirror against the C compiler's own layout of drg_params
+    fields = [f for f, _ in drg.Params._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("%zu\\n", offsetof(drg_params, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "drgraph.h"\nint main(void) {\n'
+                   '    printf("%zu\\n", sizeof(drg_params));\n' + body + '    return 0;\n}\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == C.sizeof(drg.Params)
+    assert got[1:] == [getattr(drg.Params, f).offset for f in fields]
 
 
 def test_status_strings_and_null_arguments(drg):

@@ -178,3 +178,37 @@ def test_dcsbm1m_hogwild_matches_sync_quality(env, orc):
         Y = pos.cpu().numpy().astype(np.float64).reshape(-1, 2)
         nps[mode] = orc.neighbourhood_preservation(rp, col, Y, 2, nodes)
     assert nps[1] >= 0.9 * nps[0], nps
+
+
+def test_dcsbm1m_star_hierarchy_and_quality(env, orc):
+    """The paper's star grouping on the benchmark graph: the whole hierarchy
+    exactly as the oracle's walk gives it, and a whole Hogwild run on it.
+    Groups of a node with all its ungrouped neighbours shrink the graph faster
+    than pairs (4 levels, 1.96M samples per epoch over all levels against 5
+    levels and 2.64M) and refinement starts each neighbourhood at one point:
+    NP on 2000 sampled nodes measured .0293 against .0395 with heavy-edge
+    matching.  The bar keeps that ratio (0.74) with margin and stays far above
+    a random layout (NP ~ 1e-4)."""
+    drg, ctx = env
+    g = gg.workload("dcsbm1m")
+    n = g[0]
+    rp, col = orc.canonical_graph(*g)
+    G = drg.graph_from_edges(ctx, *g)
+    H = drg.build_hierarchy(ctx, G, drg.Params.default(k=2, stop_nodes=1000, seed=0, coarsen=1))
+    levels = orc.hierarchy(rp, col, orc.Params(stop_nodes=1000, seed=0, coarsen=1))
+    assert H.sizes() == [lv.n for lv in levels]
+    for l in range(1, len(levels)):
+        assert np.array_equal(H.parent(l - 1), levels[l - 1].parent)
+        crp, ccol, cw = H.graph(l).download()
+        assert np.array_equal(crp, levels[l].rp) and np.array_equal(ccol, levels[l].col)
+        assert np.array_equal(cw, levels[l].w)
+    deg = np.diff(rp)
+    nodes = np.random.default_rng(0).choice(np.nonzero(deg > 0)[0], 2000, replace=False).astype(np.uint32)
+    nps = {}
+    for rule in (0, 1):
+        p = drg.Params.default(k=2, M=5, epochs=500, b=1.0, mode=1, stop_nodes=1000, seed=0, coarsen=rule)
+        pos = torch.zeros(2 * n, device="cuda")
+        drg.layout(ctx, G, p, pos)
+        Y = pos.cpu().numpy().astype(np.float64).reshape(-1, 2)
+        nps[rule] = orc.neighbourhood_preservation(rp, col, Y, 2, nodes)
+    assert nps[1] >= 0.65 * nps[0] and nps[1] > 0.02, nps

@@ -139,14 +139,16 @@ def test_init_positions(drg, ctx, orc):
 
 
 # ---------------------------------------------------------------- hierarchy
+@pytest.mark.parametrize("coarsen", [0, 1])
 @pytest.mark.parametrize("name,stop", [("ba2000", 100), ("grid32", 50), ("tree3000", 200), ("er_ragged", 100)])
-def test_hierarchy(drg, ctx, orc, name, stop):
+def test_hierarchy(drg, ctx, orc, name, stop, coarsen):
+    # coarsen 0: heavy-edge matching; 1: the paper's star grouping
     g = _graphs()[name]
     G = drg.graph_from_edges(ctx, *g)
-    p = drg.Params.default(stop_nodes=stop, seed=7, gid=2)
+    p = drg.Params.default(stop_nodes=stop, seed=7, gid=2, coarsen=coarsen)
     H = drg.build_hierarchy(ctx, G, p)
     orp, ocol = _oracle_csr(orc, g)
-    levels = orc.hierarchy(orp, ocol, orc.Params(stop_nodes=stop, seed=7, gid=2))
+    levels = orc.hierarchy(orp, ocol, orc.Params(stop_nodes=stop, seed=7, gid=2, coarsen=coarsen))
     assert H.sizes() == [lv.n for lv in levels]
     for l, lv in enumerate(levels):
         if l + 1 < len(levels):
@@ -177,6 +179,42 @@ def test_coarsen_and_interpolate(drg, ctx, orc):
     torch.cuda.synchronize()
     par = H.parent(0).astype(np.int64)
     assert np.array_equal(Yf.cpu().numpy().reshape(-1, 2), Yc.cpu().numpy().reshape(-1, 2)[par])
+
+
+@pytest.mark.parametrize("name", ["path7", "ba2000", "er_ragged", "hub"])
+def test_star_coarsen_one_level(drg, ctx, orc, name):
+    # one star-grouping level, every fine node's coarse id exactly; "hub" is a
+    # 1 + 3000 star plus a 40-clique, the cases of one huge and one dense group
+    if name == "hub":
+        s = np.r_[np.zeros(3000, np.uint32), np.repeat(np.arange(3001, 3041), 40)].astype(np.uint32)
+        d = np.r_[np.arange(1, 3001), np.tile(np.arange(3001, 3041), 40)].astype(np.uint32)
+        g = (3041, s, d)
+    else:
+        g = _graphs()[name]
+    n = g[0]
+    G = drg.graph_from_edges(ctx, *g)
+    orp, ocol = _oracle_csr(orc, g)
+    seeds = [0, 9]
+    if name == "hub":
+        # also a seed whose order takes the hub before all its leaves: one
+        # group of 3001 nodes
+        seeds.append(next(sd for sd in range(1, 10 ** 6)
+                          if (lambda pr: pr[0] < pr[1:3001].min())(orc.star_priorities(n, orc.Params(seed=sd), 1))))
+    for seed in seeds:
+        p = drg.Params.default(seed=seed, coarsen=1)
+        parent = torch.zeros(n, dtype=torch.int32, device="cuda")
+        C1 = drg.coarsen(ctx, G, 1, p, parent)
+        op = orc.Params(seed=seed, coarsen=1)
+        cid, nc = orc.star_cluster_ids(orc.star_group(orp, ocol, orc.star_priorities(n, op, 1)))
+        assert np.array_equal(parent.cpu().numpy().astype(np.uint32), cid)
+        crp, ccol, cw = orc.contract(orp, ocol, None, cid, nc)
+        rp, col, w = C1.download()
+        assert np.array_equal(rp, crp) and np.array_equal(col, ccol) and np.array_equal(w, cw)
+    if name == "hub":
+        assert np.bincount(cid).max() == 3001
+    bad = drg.Params.default(coarsen=2)
+    with pytest.raises(drg.DrgError):
+        drg.coarsen(ctx, G, 0, bad, torch.zeros(n, dtype=torch.int32, device="cuda"))
 
 
 # ---------------------------------------------------------------- epochs
