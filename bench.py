@@ -157,14 +157,15 @@ def epoch_kernel(graph, mode, precision):
     return "k_hogwild" if one_launch else "k_epoch"
 
 
-def ncu_traffic_per_sample(kernel):
+def ncu_traffic_per_sample(kernel, cfg):
     """DRAM bytes per sample of the level kernel from the committed ncu
-    summary, or None when the kernel source has changed since that capture."""
+    summary, or None when the kernel source has changed since that capture or
+    the run's configuration is not the captured one."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("kernel_hash") != kernel_hash():
+        if d.get("kernel_hash") != kernel_hash() or d.get("config") != cfg:
             return None
         return float(d["dram_bytes_per_sample"])
     except Exception:
@@ -426,7 +427,9 @@ def main():
     bytes_total = (s0 * algo_bytes_per_sample(kname, wl["M"], prec, False, packed)
                    + coarse * algo_bytes_per_sample(kname, wl["M"], prec, True, packed))
     achieved = bytes_total / (ep_ms / 1000.0) / 1e9
-    tps = ncu_traffic_per_sample(kname)
+    tps = ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
+                                         "mode": args.mode, "precision": args.precision,
+                                         "multilevel": bool(wl.get("multilevel", 1))})
     avg_launch_samples = ep_samples / max(ep_launches, 1)
     line = {
         "metric": "edge-sample gradient updates/s",
