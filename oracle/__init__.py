@@ -136,6 +136,8 @@ class Params:
     rho: float = 0.8           # stop when a coarser level keeps more than rho of the nodes
     match_rounds: int = 8      # handshake rounds of heavy-edge matching
     coarsen: int = 0           # 0 heavy-edge matching, 1 the paper's star grouping (Sec. 3.2.3)
+    level_tables: int = 0      # 0 G^0's tables, samples forwarded to level l (Sec. 3.2.3);
+                               # 1 each level its own distance matrix and tables (the conventional scheme)
     max_levels: int = 32
     init_scale: float = 1e-4   # coarsest positions uniform in [-s, s]^2
     multilevel: bool = True
@@ -435,21 +437,38 @@ def hierarchy(rp, col, p: Params):
     return levels
 
 
+def level_tables(level: Level, p: Params):
+    """The conventional multilevel scheme the paper sets its own against
+    (Sec. 3.2.3, last paragraph): level l's own sparse distance matrix (hop
+    distances in G^l; the coarse edge weights play no part) and sampling
+    tables, so that level l is laid out like an input graph of its own."""
+    gd = korder(level.rp, level.col, p.k)
+    return sampling_tables(*gd, p.k, p.sigma)[0]
+
+
 def run(n, src, dst, p: Params, return_state=False):
-    """The whole layout path, coarse to fine (Sec. 3.2, Fig. 1 pipeline)."""
+    """The whole layout path, coarse to fine (Sec. 3.2, Fig. 1 pipeline).
+    With p.level_tables = 1 every coarse level samples its own tables
+    (level_tables) instead of G^0's through the ancestor map."""
     rp, col = canonical_graph(n, src, dst)
     gd_rp, gd_col, gd_dist = korder(rp, col, p.k)
     tab, sim = sampling_tables(gd_rp, gd_col, gd_dist, p.k, p.sigma)
     levels = hierarchy(rp, col, p)
     L = len(levels) - 1
     Y = init_positions(p, L, levels[L].n)
+    level_tabs = {}
     for lvl in range(L, -1, -1):
         gamma = p.gamma_coarsest if (lvl == L and L > 0) else p.gamma
-        Y = layout_level(tab, Y, lvl, levels[lvl].anc, p, gamma)
+        if p.level_tables and lvl > 0:
+            level_tabs[lvl] = level_tables(levels[lvl], p)
+            Y = layout_level(level_tabs[lvl], Y, lvl, None, p, gamma)
+        else:
+            Y = layout_level(tab, Y, lvl, levels[lvl].anc, p, gamma)
         if lvl > 0:
             Y = interpolate(levels[lvl - 1].parent, Y)
     if return_state:
-        return Y, dict(rp=rp, col=col, gd=(gd_rp, gd_col, gd_dist), tab=tab, sim=sim, levels=levels)
+        return Y, dict(rp=rp, col=col, gd=(gd_rp, gd_col, gd_dist), tab=tab, sim=sim, levels=levels,
+                       level_tabs=level_tabs)
     return Y
 
 

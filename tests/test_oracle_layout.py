@@ -350,6 +350,33 @@ def test_star_hierarchy_bounds(orc):
     assert sum(star) <= 5 * n
 
 
+
+@pytest.mark.parametrize("coarsen", [0, 1])
+def test_level_tables_sample_each_level_graph(orc, coarsen):
+    # The conventional multilevel scheme: level l samples the pairs within k
+    # hops of G^l itself (scipy's shortest paths on the contracted graph),
+    # with NS symmetric, and every node id stays inside level l.
+    n, s, d = gg.barabasi_albert(1500, 2, 6)
+    k = 2
+    p = orc.Params(k=k, M=5, epochs=3, b=1.0, mode=0, stop_nodes=200, seed=4, coarsen=coarsen, level_tables=1)
+    Y, st = orc.run(n, s, d, p, return_state=True)
+    levels = st["levels"]
+    assert len(levels) > 2 and sorted(st["level_tabs"]) == list(range(1, len(levels)))
+    for l, tab in st["level_tabs"].items():
+        lv = levels[l]
+        A = sp.csr_matrix((np.ones(len(lv.col)), lv.col.astype(np.int64), lv.rp.astype(np.int64)), shape=(lv.n, lv.n))
+        D = csg.shortest_path(A, unweighted=True)
+        want = {(int(i), int(j)) for i, j in zip(*np.nonzero((D > 0) & (D <= k)))}
+        got = set(zip(tab.e_src.tolist(), tab.e_dst.tolist()))
+        assert got == want and len(tab.e_src) == len(want)
+        assert tab.n0 == lv.n
+        q = dict(zip(zip(tab.e_src.tolist(), tab.e_dst.tolist()), tab.q.tolist()))
+        assert all(q[(i, j)] == q[(j, i)] for i, j in want)
+    # one level only: both schemes are the same run
+    p1 = orc.Params(k=k, M=5, epochs=3, b=1.0, mode=0, multilevel=False, seed=4)
+    p2 = orc.Params(k=k, M=5, epochs=3, b=1.0, mode=0, multilevel=False, seed=4, level_tables=1)
+    assert np.array_equal(orc.run(n, s, d, p1), orc.run(n, s, d, p2))
+
 # ---------------------------------------------------------------- metrics
 def test_metrics_of_a_path_on_a_line(orc):
     n, s, d = gg.path(40)
