@@ -89,6 +89,10 @@ typedef struct {
     uint32_t max_levels;     /* at most this many levels, 1..64 */
     int32_t multilevel;      /* 0: lay out G^0 only */
     int32_t coarsen;         /* DRG_COARSEN_HEM or DRG_COARSEN_STAR (Sec. 3.2.3) */
+    int32_t level_tables;    /* whole-path runs: 0 every level samples G^0's tables through the
+                                ancestor map (Sec. 3.2.3, the paper's scheme); 1 each coarse level
+                                samples its own distance matrix and tables, built just before the
+                                level runs and freed after it (the conventional scheme) */
 } drg_params;
 
 /* Mode and precision values. */
@@ -213,7 +217,10 @@ drg_status drg_init_positions(drg_ctx* ctx, uint32_t n, uint32_t level, const dr
  * Philox stream counter (s, t, tag(level, gid), call): the positive entry
  * (i, j) from d's edge table and p->M negatives from its node table; the
  * level's nodes are a = anc(i), c = anc(j), c_m = anc(j_m) (identity at
- * level 0 or when h is NULL); negatives with c_m == a or c_m == c are
+ * level 0 or when h is NULL).  d is G^0's matrix or, at a coarse level, one
+ * built on that level's graph (drg_hier_graph), whose entries are the
+ * level's nodes themselves (identity map: the conventional multilevel scheme
+ * the paper sets its forwarding against); negatives with c_m == a or c_m == c are
  * skipped.  The sample moves a by lr (attraction + sum of repulsions), c by
  * -lr attraction and each c_m by -lr repulsion_m, with
  *   attraction = -2b d^{2b-2} (y_a - y_c) / (1 + d^{2b}),
@@ -266,7 +273,9 @@ drg_status drg_interpolate(drg_ctx* ctx, const drg_hier* h, uint32_t coarse_leve
 
 /* The whole path on a graph: distance matrix, hierarchy (when p->multilevel),
  * random coarsest layout, then for each level coarse to fine all epochs and
- * the refinement.  pos: device float[2 n].  Synchronises. */
+ * the refinement.  With p->level_tables each coarse level first gets its own
+ * distance matrix and tables (freed after the level).  pos: device
+ * float[2 n].  Synchronises. */
 drg_status drg_layout(drg_ctx* ctx, const drg_graph* g, const drg_params* p, float* pos);
 
 /* drg_graph_from_edges + drg_layout in one call.  Edges and positions live in
@@ -281,10 +290,11 @@ drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
  * result equals drg_layout of that graph alone with those parameters up to
  * the order of FP32 atomic additions.  Levels run in rounds aligned at every
  * graph's coarsest level; in FP32 Hogwild mode all epochs of a round are one
- * cooperative launch (threads of every active graph, a grid barrier between
- * epochs); otherwise sub-step run c of every active graph is one kernel
- * launch and all epochs of the round are one CUDA graph launch.  pos[g] are
- * device float[2 n_g].  Synchronises. */
+ * cooperative launch (threads of every active graph, warps kept within two
+ * epochs of each other by the same gates as drg_layout_level); otherwise
+ * sub-step run c of every active graph is one kernel launch and all epochs
+ * of the round are one CUDA graph launch.  pos[g] are device float[2 n_g].
+ * p->level_tables must be 0 (DRG_EUNSUPPORTED).  Synchronises. */
 drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
                             const float* b, float* const* pos);
 

@@ -57,6 +57,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("gid", C.c_uint32), ("mode", C.c_int32), ("precision", C.c_int32),
         ("substeps", C.c_uint32), ("stop_nodes", C.c_uint32), ("match_rounds", C.c_uint32),
         ("max_levels", C.c_uint32), ("multilevel", C.c_int32), ("coarsen", C.c_int32),
+        ("level_tables", C.c_int32),
     ]
 
     @classmethod

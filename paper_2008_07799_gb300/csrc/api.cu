@@ -159,6 +159,7 @@ void drg_params_default(drg_params* p) {
     p->max_levels = 32;
     p->multilevel = 1;
     p->coarsen = DRG_COARSEN_HEM;
+    p->level_tables = 0;
 }
 
 const char* drg_status_string(drg_status s) {

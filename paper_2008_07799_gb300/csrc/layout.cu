@@ -759,6 +759,7 @@ void check_params(const drg_params& p) {
     DRG_CHECK(p.rho > 0.f && p.rho <= 1.f, DRG_EINVAL, "rho must be in (0, 1]");
     DRG_CHECK(p.coarsen == DRG_COARSEN_HEM || p.coarsen == DRG_COARSEN_STAR, DRG_EINVAL,
               "coarsen must be DRG_COARSEN_HEM or DRG_COARSEN_STAR");
+    DRG_CHECK(p.level_tables == 0 || p.level_tables == 1, DRG_EINVAL, "level_tables must be 0 or 1");
 }
 
 static int int_b(float b) {
@@ -1027,9 +1028,12 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
     DRG_CHECK(d && pos, DRG_EINVAL, "null distance matrix or positions");
     DRG_CHECK(level == 0 || (h && level < h->g.size()), DRG_EINVAL, "level out of range");
     DRG_CHECK(t_begin <= t_end && t_end <= p.epochs, DRG_EINVAL, "epoch range outside [0, epochs]");
-    DRG_CHECK(!h || h->g[0]->n == d->n, DRG_EINVAL, "hierarchy and distance matrix describe different graphs");
+    // d is G^0's matrix (samples mapped to the level through its ancestor
+    // map) or, at a coarse level, the level graph's own (no mapping)
+    const bool own = level > 0 && h && d->n != h->g[0]->n && d->n == h->g[level]->n;
+    DRG_CHECK(!h || own || h->g[0]->n == d->n, DRG_EINVAL, "hierarchy and distance matrix describe different graphs");
     const uint32_t nl = level == 0 ? d->n : h->g[level]->n;
-    const uint32_t* anc = level == 0 ? nullptr : h->anc[level];
+    const uint32_t* anc = (level == 0 || own) ? nullptr : h->anc[level];
     float2* Y = reinterpret_cast<float2*>(pos);
     const bool sync_mode = p.mode == DRG_MODE_SYNC;
     const int prec = p.precision;
@@ -1200,7 +1204,21 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
         init_positions(ctx, h->g[L]->n, L, p, cur_pos);
         for (int l = (int)L; l >= 0; --l) {
             const float gamma = (l == (int)L && L > 0) ? p.gamma_coarsest : p.gamma;
-            layout_level(ctx, d, h, (uint32_t)l, cur_pos, p, gamma, 0, p.epochs);
+            if (p.level_tables && l > 0) {
+                // the conventional scheme: this level's own matrix and tables
+                drg_dmat* dl = build_dmat(ctx, h->g[l], p.k, p.sigma);
+                try {
+                    layout_level(ctx, dl, h, (uint32_t)l, cur_pos, p, gamma, 0, p.epochs);
+                    sync(ctx);
+                } catch (...) {
+                    cudaStreamSynchronize(ctx->stream);
+                    dmat_free(dl);
+                    throw;
+                }
+                dmat_free(dl);
+            } else {
+                layout_level(ctx, d, h, (uint32_t)l, cur_pos, p, gamma, 0, p.epochs);
+            }
             if (l > 0) {
                 float* fine_pos = pos;
                 if (l - 1 > 0) {
@@ -1253,6 +1271,7 @@ constexpr uint32_t kBatchPrepThreads = 8;
 void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params& p,
                   const float* b_per_graph, float* const* pos) {
     check_params(p);
+    DRG_CHECK(p.level_tables == 0, DRG_EUNSUPPORTED, "per-level tables are for whole runs of one graph");
     DRG_CHECK(count == 0 || (graphs && pos), DRG_EINVAL, "null argument");
     for (uint32_t g = 0; g < count; ++g) {
         DRG_CHECK(graphs[g] && pos[g], DRG_EINVAL, "null graph or position buffer");

@@ -283,6 +283,63 @@ def test_hogwild_one_sample_in_flight_is_sequential(drg, ctx, orc, name, k, b, l
     assert np.max(np.abs(ref - Y0)) > 1e-3
 
 
+@pytest.mark.parametrize("mode,coarsen", [(0, 0), (1, 0), (0, 1)])
+def test_own_level_tables_epoch(drg, ctx, orc, mode, coarsen):
+    # A coarse level sampling a distance matrix built on its own graph (the
+    # conventional multilevel scheme): one synchronous epoch within 1e-5 of
+    # the extent, and with one sample in flight the Hogwild run is the
+    # oracle's sequential loop (bar as in the test above).
+    g = _graphs()["ba2000"]
+    k, level, t = 2, 2, 7
+    orp, ocol = _oracle_csr(orc, g)
+    op = orc.Params(k=k, M=5, epochs=500, b=1.0, mode=mode, substeps=16, stop_nodes=100, seed=5,
+                    coarsen=coarsen)
+    levels = orc.hierarchy(orp, ocol, op)
+    nl = levels[level].n
+    tab = orc.level_tables(levels[level], op)
+    rng = np.random.default_rng(31 + mode)
+    Y0 = (rng.normal(size=(nl, 2)) * np.sqrt(nl) * 0.3).astype(np.float32).astype(np.float64)
+    ref = orc.layout_level(tab, Y0.copy(), level, None, op, 0.1, t, t + 1)
+    sens = 0.0
+    if mode == 1:
+        for _ in range(3):
+            Yp = Y0 * (1 + 6e-8 * rng.standard_normal(Y0.shape))
+            sens = max(sens, np.max(np.abs(orc.layout_level(tab, Yp, level, None, op, 0.1, t, t + 1) - ref)))
+    G = drg.graph_from_edges(ctx, *g)
+    p = drg.Params.default(k=k, M=5, epochs=500, b=1.0, mode=mode, substeps=16 if mode == 0 else nl,
+                           stop_nodes=100, seed=5, coarsen=coarsen)
+    H = drg.build_hierarchy(ctx, G, p)
+    assert H.sizes()[level] == nl
+    D = drg.build_distance_matrix(ctx, H.graph(level), k)
+    got_tab = D.download()
+    assert np.array_equal(got_tab["e_alias"], tab.e_alias) and np.array_equal(got_tab["q"], tab.q)
+    Y = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
+    drg.layout_level(ctx, D, H, level, Y, p, 0.1, t, t + 1)
+    torch.cuda.synchronize()
+    got = Y.cpu().numpy().astype(np.float64).reshape(nl, 2)
+    err = np.max(np.abs(got - ref))
+    assert err <= 10 * sens + 1e-5 * _extent(ref), (err, sens, _extent(ref))
+    assert np.max(np.abs(ref - Y0)) > 1e-3
+
+
+def test_level_tables_whole_run_and_batch_rejects(drg, ctx, orc):
+    # the whole path with per-level tables runs every level (grid32 with a
+    # hierarchy); batches reject the option
+    n, s, d = gg.grid(40, 40)
+    G = drg.graph_from_edges(ctx, n, s, d)
+    p = drg.Params.default(k=2, M=5, epochs=60, b=3.0, mode=1, stop_nodes=200, seed=2, level_tables=1)
+    pos = torch.zeros(2 * n, device="cuda")
+    drg.layout(ctx, G, p, pos)
+    Y = pos.cpu().numpy().astype(np.float64).reshape(-1, 2)
+    assert np.all(np.isfinite(Y)) and _extent(Y) > 1.0
+    rp, col = orc.canonical_graph(n, s, d)
+    ref = orc.run(n, s, d, orc.Params(k=2, M=5, epochs=60, b=3.0, mode=1, stop_nodes=200, seed=2, level_tables=1))
+    np_ref = orc.neighbourhood_preservation(rp, col, ref, 2)     # .42 (sequential oracle)
+    assert orc.neighbourhood_preservation(rp, col, Y, 2) >= 0.8 * np_ref
+    with pytest.raises(drg.DrgError):
+        drg.layout_batch(ctx, [G], p, [pos])
+
+
 @pytest.mark.parametrize("t0", [100, 480])
 def test_sync_epochs_chain(drg, ctx, orc, t0):
     # Five consecutive epochs from the oracle's state after t0 epochs.  The
