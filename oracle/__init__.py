@@ -95,6 +95,14 @@ def lib():
                                 C.c_uint32, U32P]
     L.orc_cluster_ids.argtypes = [C.c_uint32, U32P, U32P]
     L.orc_cluster_ids.restype = C.c_uint32
+    L.orc_exp.argtypes = [C.c_double]
+    L.orc_exp.restype = C.c_double
+    L.orc_row_perplexity.argtypes = [C.c_uint32, U64P, C.c_double]
+    L.orc_row_perplexity.restype = C.c_double
+    L.orc_calibrate_row.argtypes = [C.c_uint32, U64P, C.c_double]
+    L.orc_calibrate_row.restype = C.c_double
+    L.orc_similarity_perplexity.argtypes = [C.c_uint32, U64P, U32P, U8P, C.c_uint32, C.c_float, F64P, F32P, U32P,
+                                            U64P, C.c_void_p]
     L.orc_star_group.argtypes = [C.c_uint32, U64P, U32P, U32P, U32P]
     L.orc_star_priorities.argtypes = [C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, U32P]
     L.orc_star_priorities.restype = None
@@ -127,6 +135,7 @@ class Params:
     b: float = 1.0             # shape of the layout proximity kernel (Eq. 5)
     lr0: float = 1.0           # learning rate at epoch 0, linearly decayed to 0
     sigma: float = 1.0         # Gaussian width of the node similarity (Eq. 9)
+    perplexity: float = 0.0    # > 0: sigma_i per node calibrated to this perplexity (sigma unused)
     clip: float = 5.0          # per-component clip of each pair force
     seed: int = 0
     gid: int = 0               # graph id in the random stream
@@ -237,6 +246,37 @@ def similarity(gd_rp, gd_col, gd_dist, k, sigma=1.0):
     return dict(g=g, Z=Z[:n], q=q[:nnz], r=r[:n], ns=ns[:nnz])
 
 
+def similarity_perplexity(gd_rp, gd_col, gd_dist, k, perplexity):
+    """Eq. 9 with sigma_i calibrated per node to perplexity P (t-SNE rule)."""
+    n = len(gd_rp) - 1
+    nnz = int(gd_rp[-1])
+    beta = np.zeros(max(n, 1), np.float64)
+    Z = np.zeros(max(n, 1), np.float32)
+    q = np.zeros(max(nnz, 1), np.uint32)
+    r = np.zeros(max(n, 1), np.uint64)
+    ns = np.zeros(max(nnz, 1), np.float64)
+    col = gd_col if nnz else np.zeros(1, np.uint32)
+    dist = gd_dist if nnz else np.zeros(1, np.uint8)
+    assert lib().orc_similarity_perplexity(n, gd_rp, col, dist, k, perplexity, beta, Z, q, r,
+                                           ns.ctypes.data) == 0
+    return dict(beta=beta[:n], Z=Z[:n], q=q[:nnz], r=r[:n], ns=ns[:nnz])
+
+
+def exp(x):
+    """The oracle's own FP64 exponential (used by the calibration)."""
+    return lib().orc_exp(float(x))
+
+
+def row_perplexity(counts, beta):
+    c = np.ascontiguousarray(counts, np.uint64)
+    return lib().orc_row_perplexity(len(c), c, float(beta))
+
+
+def calibrate_row(counts, perplexity):
+    c = np.ascontiguousarray(counts, np.uint64)
+    return lib().orc_calibrate_row(len(c), c, float(perplexity))
+
+
 def node_weights_u32(r):
     r = np.ascontiguousarray(r, np.uint64)
     out = np.zeros(max(len(r), 1), np.uint32)
@@ -283,8 +323,11 @@ class Tables:
     shift: int
 
 
-def sampling_tables(gd_rp, gd_col, gd_dist, k, sigma=1.0):
-    sim = similarity(gd_rp, gd_col, gd_dist, k, sigma)
+def sampling_tables(gd_rp, gd_col, gd_dist, k, sigma=1.0, perplexity=0.0):
+    if perplexity > 0:
+        sim = similarity_perplexity(gd_rp, gd_col, gd_dist, k, perplexity)
+    else:
+        sim = similarity(gd_rp, gd_col, gd_dist, k, sigma)
     e_src, e_dst = edge_endpoints(gd_rp, gd_col)
     et = alias_build(sim["q"])
     r32, shift = node_weights_u32(sim["r"])
@@ -443,7 +486,7 @@ def level_tables(level: Level, p: Params):
     distances in G^l; the coarse edge weights play no part) and sampling
     tables, so that level l is laid out like an input graph of its own."""
     gd = korder(level.rp, level.col, p.k)
-    return sampling_tables(*gd, p.k, p.sigma)[0]
+    return sampling_tables(*gd, p.k, p.sigma, p.perplexity)[0]
 
 
 def run(n, src, dst, p: Params, return_state=False):
@@ -452,7 +495,7 @@ def run(n, src, dst, p: Params, return_state=False):
     (level_tables) instead of G^0's through the ancestor map."""
     rp, col = canonical_graph(n, src, dst)
     gd_rp, gd_col, gd_dist = korder(rp, col, p.k)
-    tab, sim = sampling_tables(gd_rp, gd_col, gd_dist, p.k, p.sigma)
+    tab, sim = sampling_tables(gd_rp, gd_col, gd_dist, p.k, p.sigma, p.perplexity)
     levels = hierarchy(rp, col, p)
     L = len(levels) - 1
     Y = init_positions(p, L, levels[L].n)

@@ -254,6 +254,131 @@ int orc_similarity(uint32_t n, const uint64_t* rp, const uint32_t* col, const ui
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Per-node sigma_i of Eq. 9 set by perplexity, the t-SNE rule the paper's
+ * sigma_i comes from: the conditional distribution NS_{.|i} over row i has
+ * perplexity exp(H_i) = P.  Row i holds c_d nodes at hop distance d, so with
+ * beta = 1/(2 sigma_i^2) and weights w_d = e^{-beta (d^2 - 1)} (the common
+ * factor e^{-beta} cancels in NS_{j|i}):
+ *   Z'(beta) = sum_d c_d w_d,   S'(beta) = sum_d c_d (d^2 - 1) w_d,
+ *   exp(H) = Z' exp(beta S'/Z'),
+ * which falls from the row size (beta = 0) to c_1 (beta -> inf).  beta_i is
+ * found by 60 bisection steps on [0, 512]: mid = (lo + hi)/2, lo = mid when
+ * exp(H(mid)) > P, else hi = mid; beta_i = (lo + hi)/2.  Every quantity is
+ * FP64 with separately rounded +, -, *, / (this file is compiled without
+ * contraction) and the exponential orc_exp below, so the result is a fixed
+ * function of (c, P) that the GPU reproduces bit for bit.  Then
+ *   g_i(d) = fl32(orc_exp(-(beta_i (d^2 - 1)))),  Z_i = FP32 sum of
+ *   fl32(c_d) g_i(d) over d = 1..k,  NS_{j|i} ~ fl32(g_i(d) / Z_i),
+ *   q_e = floor((fl32(g_i(d)/Z_i) + fl32(g_j(d)/Z_j)) 2^30).
+ * Pinned by orc_exp against the C library's exp, by the perplexity of the
+ * calibrated rows evaluated with numpy, and by scipy's root finder.          */
+
+/* e^x in FP64: Cody & Waite's reduction x = m ln2 + r, |r| <= ln2/2 (ln 2
+ * split into a 32-significant-bit head, so m ln2_hi is exact, and a tail),
+ * the Taylor polynomial of e^r to degree 13 by Horner's rule (remainder below
+ * 1e-17 relative), times 2^m built from its bits.  0 below -700.            */
+static void orc_exp_coeffs(double c[14])
+{
+    c[0] = 1.0;
+    for (int i = 1; i < 14; ++i) c[i] = c[i - 1] / (double)i;
+}
+
+double orc_exp(double x)
+{
+    const double inv_ln2 = 1.4426950408889634;
+    const double ln2_hi = 0.6931471803691238;
+    const double ln2_lo = 1.9082149292705877e-10;
+    double c[14];
+    if (x < -700.0) return 0.0;
+    orc_exp_coeffs(c);
+    double m = floor(x * inv_ln2 + 0.5);
+    double r = (x - m * ln2_hi) - m * ln2_lo;
+    double p = c[13];
+    for (int i = 12; i >= 0; --i) p = p * r + c[i];
+    uint64_t bits = (uint64_t)((int64_t)m + 1023) << 52;
+    double scale;
+    memcpy(&scale, &bits, sizeof scale);
+    return p * scale;
+}
+
+/* exp(H_i(beta)) of a row with class counts cnt[0..k-1] (d = 1..k). */
+double orc_row_perplexity(uint32_t k, const uint64_t* cnt, double beta)
+{
+    double z = 0.0, s = 0.0;
+    for (uint32_t d = 1; d <= k; ++d) {
+        double dd = (double)(d * d - 1);
+        double w = orc_exp(-(beta * dd));
+        z = z + (double)cnt[d - 1] * w;
+        s = s + ((double)cnt[d - 1] * dd) * w;
+    }
+    return z * orc_exp(beta * (s / z));
+}
+
+/* beta_i of a non-empty row (cnt[0] >= 1). */
+double orc_calibrate_row(uint32_t k, const uint64_t* cnt, double perplexity)
+{
+    double lo = 0.0, hi = 512.0;
+    for (int it = 0; it < 60; ++it) {
+        double mid = (lo + hi) * 0.5;
+        if (orc_row_perplexity(k, cnt, mid) > perplexity) lo = mid;
+        else hi = mid;
+    }
+    return (lo + hi) * 0.5;
+}
+
+/* The similarity of orc_similarity with sigma_i calibrated per node; beta
+ * (n) receives beta_i (0 for an empty row).                                 */
+int orc_similarity_perplexity(uint32_t n, const uint64_t* rp, const uint32_t* col, const uint8_t* dist,
+                              uint32_t k, float perplexity, double* beta, float* Z, uint32_t* q, uint64_t* r,
+                              double* ns)
+{
+    float* g = (float*)malloc(sizeof(float) * (size_t)(n ? n : 1) * k);
+    double* g64 = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1) * k);
+    double* Z64 = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * (k + 1));
+    if (!g || !g64 || !Z64 || !cnt) { free(g); free(g64); free(Z64); free(cnt); return -1; }
+    for (uint32_t i = 0; i < n; ++i) {
+        for (uint32_t d = 0; d <= k; ++d) cnt[d] = 0;
+        for (uint64_t e = rp[i]; e < rp[i + 1]; ++e) cnt[dist[e]] += 1;
+        if (rp[i + 1] == rp[i]) {
+            beta[i] = 0.0;
+            Z[i] = 0.0f;
+            Z64[i] = 0.0;
+            for (uint32_t d = 0; d < k; ++d) { g[(size_t)i * k + d] = 0.0f; g64[(size_t)i * k + d] = 0.0; }
+            continue;
+        }
+        double b = orc_calibrate_row(k, cnt + 1, (double)perplexity);
+        beta[i] = b;
+        double z64 = 0.0;
+        for (uint32_t d = 1; d <= k; ++d) {
+            double w = orc_exp(-(b * (double)(d * d - 1)));
+            g64[(size_t)i * k + d - 1] = w;
+            g[(size_t)i * k + d - 1] = (float)w;
+            z64 += (double)cnt[d] * w;
+        }
+        Z[i] = orc_normaliser(k, cnt + 1, g + (size_t)i * k);
+        Z64[i] = z64;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t acc = 0;
+        for (uint64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            uint32_t j = col[e];
+            uint32_t d = dist[e];
+            float p_ji = g[(size_t)i * k + d - 1] / Z[i];
+            float p_ij = g[(size_t)j * k + d - 1] / Z[j];
+            float s = p_ji + p_ij;
+            q[e] = (uint32_t)(s * 1073741824.0f);
+            acc += q[e];
+            if (ns) ns[e] = (g64[(size_t)i * k + d - 1] / Z64[i] + g64[(size_t)j * k + d - 1] / Z64[j])
+                            / (2.0 * (double)n);
+        }
+        r[i] = acc;
+    }
+    free(g); free(g64); free(Z64); free(cnt);
+    return 0;
+}
+
 /* Node weights for the negative-sample alias table: r_i shifted right by
  * s = max(0, bitlength(max r) - 32) so they fit 32 bits.  Returns s.        */
 uint32_t orc_node_weights_u32(uint32_t n, const uint64_t* r, uint32_t* r32)

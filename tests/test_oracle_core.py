@@ -162,6 +162,83 @@ def test_similarity_k1_is_inverse_degree(orc):
     assert np.allclose(sim["ns"], (1 / deg[rows] + 1 / deg[j]) / (2 * n), rtol=1e-14)
 
 
+
+# ------------------------------------------- perplexity-calibrated sigma_i
+def test_own_exp_against_the_c_library(orc):
+    xs = np.r_[np.linspace(-700.0, 30.0, 40001), [-1e-300, -0.5, 0.5, -np.log(2), 1e-9, -1e-9]]
+    got = np.array([orc.exp(x) for x in xs])
+    ref = np.exp(xs)
+    assert np.max(np.abs(got - ref) / ref) <= 4.5e-16
+    assert orc.exp(0.0) == 1.0 and orc.exp(-700.5) == 0.0
+
+
+def _perplexity_np(counts, beta):
+    # exp of the entropy of the row distribution, evaluated with numpy
+    d = np.arange(1, len(counts) + 1, dtype=np.float64)
+    w = np.repeat(np.exp(-beta * (d * d - 1)), np.asarray(counts, np.int64))
+    p = w / w.sum()
+    p = p[p > 0]
+    return math.exp(-(p * np.log(p)).sum())
+
+
+@pytest.mark.parametrize("counts,P", [([8, 300], 30.0), ([3, 40, 900], 30.0), ([1, 2, 4, 8, 16], 5.0),
+                                      ([25, 10], 30.0), ([5, 5], 9.99), ([40], 7.0), ([2, 4000], 2.5),
+                                      ([50, 100], 30.0), ([3, 4], 30.0)])
+def test_calibrated_row_perplexity(orc, counts, P):
+    beta = orc.calibrate_row(counts, P)
+    N, c1 = sum(counts), counts[0]
+    if P >= N:                                    # not reachable: uniform row
+        assert beta < 1e-12
+    elif P <= c1 and len(counts) > 1:             # all weight on the nearest class
+        assert beta > 511
+    elif len(counts) > 1:
+        assert math.isclose(_perplexity_np(counts, beta), P, rel_tol=1e-9)
+        # the root of the closed-form entropy, found by scipy
+        from scipy.optimize import brentq
+        root = brentq(lambda b: math.log(_perplexity_np(counts, b)) - math.log(P), 0.0, 512.0, xtol=1e-14)
+        assert math.isclose(beta, root, rel_tol=1e-9, abs_tol=1e-12)
+    assert math.isclose(orc.row_perplexity(counts, beta), _perplexity_np(counts, beta), rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("k,P", [(2, 30.0), (3, 12.0), (1, 5.0)])
+def test_similarity_perplexity_rows(orc, k, P):
+    n, s, d = gg.barabasi_albert(400, 2, 9)
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, k)
+    sim = orc.similarity_perplexity(*gd, k, P)
+    rows = np.repeat(np.arange(n), np.diff(gd[0]).astype(np.int64))
+    dist = gd[2].astype(np.int64)
+    beta = sim["beta"]
+    # NS_{j|i} with the calibrated sigma_i sums to one and has perplexity P
+    # (or the row's limit) in every row
+    w = np.exp(-beta[rows] * (dist * dist - 1))
+    Zrow = np.zeros(n)
+    np.add.at(Zrow, rows, w)
+    cond = w / Zrow[rows]
+    H = np.zeros(n)
+    np.add.at(H, rows, -cond * np.log(np.where(cond > 0, cond, 1.0)))
+    size = np.diff(gd[0]).astype(np.int64)
+    c1 = np.bincount(rows[dist == 1], minlength=n)
+    mid = (size > P) & (c1 < P)
+    assert np.allclose(np.exp(H[mid]), P, rtol=1e-8)
+    assert np.allclose(np.exp(H[size <= P]), size[size <= P], rtol=1e-8)
+    # FP32 normaliser and quantised weights from the per-node Gaussians
+    g32 = np.exp(-beta[rows] * (dist * dist - 1)).astype(np.float32)
+    assert np.allclose(sim["Z"][rows], Zrow[rows], rtol=1e-6)
+    ns = sim["ns"]
+    key = rows * n + gd[1].astype(np.int64)
+    tkey = gd[1].astype(np.int64) * n + rows
+    order = np.argsort(key)
+    assert np.allclose(ns, ns[order][np.searchsorted(key[order], tkey)], rtol=1e-14)
+    assert math.isclose(ns.sum(), 1.0, rel_tol=1e-12)
+    exact = ns * 2 * n * 2.0 ** 30
+    q = sim["q"].astype(np.float64)
+    assert np.all(q <= exact * (1 + 4e-7) + 1e-9) and np.all(q >= exact * (1 - 4e-7) - 1.0)
+    assert np.array_equal(sim["r"], np.bincount(rows, weights=sim["q"], minlength=n).astype(np.uint64))
+    if k == 1:   # one class: the calibration cannot matter, NS_{j|i} = 1/deg
+        deg = np.diff(rp).astype(np.float64)
+        assert np.allclose(ns, (1 / deg[rows] + 1 / deg[col.astype(np.int64)]) / (2 * n), rtol=1e-14)
+
 def test_node_weight_shift(orc):
     r = np.array([0, 5, 2 ** 40 + 7, 2 ** 33], np.uint64)
     r32, s = orc.node_weights_u32(r)
