@@ -228,6 +228,7 @@ def make_params(drg, wl, args, gid):
         p.substeps = args.substeps
     p.coarsen = {"hem": 0, "star": 1}[args.coarsen]
     p.level_tables = 1 if args.level_tables else 0
+    p.perplexity = args.perplexity
     return p
 
 
@@ -313,6 +314,8 @@ def main():
     ap.add_argument("--once", action="store_true", help="run exactly one step and exit (for ncu captures)")
     ap.add_argument("--coarsen", default="hem", choices=["hem", "star"],
                     help="coarsening rule: heavy-edge matching or the paper's star grouping (Sec. 3.2.3)")
+    ap.add_argument("--perplexity", type=float, default=0.0,
+                    help="> 0: sigma_i of Eq. 9 per node calibrated to this perplexity")
     ap.add_argument("--level-tables", action="store_true",
                     help="each coarse level samples its own distance matrix and tables (the conventional "
                          "multilevel scheme) instead of G^0's through the ancestor map")
@@ -349,6 +352,8 @@ def main():
         wl["desc"] = wl["desc"].replace("multilevel HEM", "multilevel star grouping")
     if args.level_tables:
         wl["desc"] += "; each coarse level samples its own distance matrix and tables"
+    if args.perplexity > 0:
+        wl["desc"] += f"; sigma_i per node at perplexity {args.perplexity:g}"
     stream = torch.cuda.current_stream()
     ctx = drg.Context(local, stream.cuda_stream)
     p = make_params(drg, wl, args, gid=rank)
@@ -433,7 +438,7 @@ def main():
     bytes_total = (s0 * algo_bytes_per_sample(kname, wl["M"], prec, False, packed)
                    + coarse * algo_bytes_per_sample(kname, wl["M"], prec, True, packed))
     achieved = bytes_total / (ep_ms / 1000.0) / 1e9
-    tps = None if args.level_tables else ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
+    tps = None if (args.level_tables or args.perplexity > 0) else ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
                                          "mode": args.mode, "precision": args.precision,
                                          "multilevel": bool(wl.get("multilevel", 1))})
     avg_launch_samples = ep_samples / max(ep_launches, 1)
@@ -451,7 +456,8 @@ def main():
         "dtype": "f32" if prec == 0 else ("f32+f16" if prec == 1 else "f32+bf16"),
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "mode": args.mode, "precision": args.precision,
-                   "coarsen": args.coarsen, "level_tables": bool(args.level_tables), "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
+                   "coarsen": args.coarsen, "level_tables": bool(args.level_tables),
+                   "perplexity": args.perplexity, "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
                    "samples_per_step": samples_per_step, "layout_time_ms": ms,
                    "l2": "1 GiB buffer written between timed steps (flush)",
                    "parallelism": f"replicas x{world}"},

@@ -93,6 +93,8 @@ typedef struct {
                                 ancestor map (Sec. 3.2.3, the paper's scheme); 1 each coarse level
                                 samples its own distance matrix and tables, built just before the
                                 level runs and freed after it (the conventional scheme) */
+    float perplexity;        /* whole-path runs: > 0 sets sigma_i of Eq. 9 per node by this
+                                perplexity (drg_build_distance_matrix_ex); 0 uses sigma */
 } drg_params;
 
 /* Mode and precision values. */
@@ -171,6 +173,32 @@ drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint
  * buckets.  e_end <= nnz.  Synchronises. */
 drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_begin, uint64_t e_end, uint32_t* col,
                                    uint8_t* dist, uint32_t* q, uint32_t* e_thresh, uint32_t* e_alias);
+/* drg_build_distance_matrix with Eq. 9's sigma_i set per node by perplexity
+ * (perplexity > 0; sigma is then unused; 0 is the global-sigma build).  Row i
+ * holds c_d nodes at hop distance d; beta_i = 1/(2 sigma_i^2) makes the
+ * perplexity exp(H_i) = Z' exp(beta S'/Z') of NS_{.|i} equal `perplexity`,
+ * with w_d = e^{-beta (d^2 - 1)}, Z' = sum_d c_d w_d and
+ * S' = sum_d c_d (d^2 - 1) w_d (the factor e^{-beta} cancels in NS_{j|i});
+ * it falls from the row size at beta = 0 to c_1, so rows smaller than
+ * `perplexity` come out uniform and rows with c_1 >= perplexity keep only
+ * their first-order neighbours.  beta_i: 60 bisection steps on [0, 512]
+ * (mid = (lo + hi)/2; lo = mid when exp(H(mid)) > perplexity, else hi = mid;
+ * beta_i = (lo + hi)/2), every step in FP64 with separately rounded
+ * operations and the exponential e^x = p(r) 2^m, x = m ln2 + r (Cody-Waite
+ * reduction with ln 2 = 0.6931471803691238 + 1.9082149292705877e-10,
+ * m = floor(x * 1.4426950408889634 + 0.5), p the degree-13 Taylor polynomial
+ * by Horner's rule with coefficients 1/n! computed by repeated division;
+ * e^x = 0 below -700).  Then g_i(d) = fl32(e^{-beta_i (d^2 - 1)}),
+ * Z_i = sum over d of count_i(d) * g_i(d) (FP32, in order) and
+ *   q[e] = floor((fl(g_i(d)/Z_i) + fl(g_j(d)/Z_j)) * 2^30);
+ * everything else as drg_build_distance_matrix.  DRG_EINVAL for a negative
+ * or non-finite perplexity or one of 4.2e9 or more.  Synchronises. */
+drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity,
+                                        drg_dmat** out);
+/* Host copy of beta_i = 1/(2 sigma_i^2) of every node (n doubles; 0 for an
+ * empty row) of a perplexity-calibrated matrix; DRG_EINVAL for a matrix
+ * built with a global sigma.  Synchronises. */
+drg_status drg_dmat_calibration(drg_ctx* ctx, const drg_dmat* d, double* beta);
 drg_status drg_dmat_destroy(drg_dmat* d);
 
 /* ---------------------------------------------------------------- hierarchy */

@@ -37,6 +37,7 @@ EXPORTS = [
     "drg_init_positions", "drg_layout_level", "drg_interpolate", "drg_layout", "drg_layout_edges",
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
     "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
+    "drg_build_distance_matrix_ex", "drg_dmat_calibration",
 ]
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
@@ -57,7 +58,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("gid", C.c_uint32), ("mode", C.c_int32), ("precision", C.c_int32),
         ("substeps", C.c_uint32), ("stop_nodes", C.c_uint32), ("match_rounds", C.c_uint32),
         ("max_levels", C.c_uint32), ("multilevel", C.c_int32), ("coarsen", C.c_int32),
-        ("level_tables", C.c_int32),
+        ("level_tables", C.c_int32), ("perplexity", C.c_float),
     ]
 
     @classmethod
@@ -108,6 +109,8 @@ def lib():
         "drg_dmat_info": (st, [VP, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
         "drg_dmat_download": (st, [VP] * 12),
         "drg_dmat_destroy": (st, [VP]),
+        "drg_build_distance_matrix_ex": (st, [VP, VP, C.c_uint32, C.c_float, C.c_float, C.POINTER(VP)]),
+        "drg_dmat_calibration": (st, [VP, VP, VP]),
         "drg_dmat_download_range": (st, [VP, VP, C.c_uint64, C.c_uint64, VP, VP, VP, VP, VP]),
         "drg_coarsen": (st, [VP, VP, C.c_uint32, PP, C.POINTER(VP), VP]),
         "drg_build_hierarchy": (st, [VP, VP, PP, C.POINTER(VP)]),
@@ -252,6 +255,13 @@ class Graph(_Handle):
 class DistanceMatrix(_Handle):
     _destroy = "drg_dmat_destroy"
 
+    def calibration(self):
+        """beta_i = 1/(2 sigma_i^2) of every node (perplexity-calibrated matrices)."""
+        n = self.info()[0]
+        out = np.zeros(max(n, 1), np.float64)
+        self.ctx.check(lib().drg_dmat_calibration(self.ctx.h, self.h, _ptr(out)))
+        return out[:n]
+
     def info(self):
         n = C.c_uint32()
         nnz = C.c_uint64()
@@ -344,9 +354,16 @@ def graph_from_edges(ctx: Context, n, src, dst) -> Graph:
     return Graph(ctx, h)
 
 
-def build_distance_matrix(ctx: Context, g: Graph, k: int, sigma: float = 1.0) -> DistanceMatrix:
+def build_distance_matrix(ctx: Context, g: Graph, k: int, sigma: float = 1.0,
+                          perplexity: float = 0.0) -> DistanceMatrix:
+    """perplexity > 0: sigma_i per node calibrated to that perplexity (any
+    other non-zero value is refused by the library)."""
     h = VP()
-    ctx.check(lib().drg_build_distance_matrix(ctx.h, g.h, int(k), float(sigma), C.byref(h)))
+    if perplexity != 0.0:
+        ctx.check(lib().drg_build_distance_matrix_ex(ctx.h, g.h, int(k), float(sigma), float(perplexity),
+                                                     C.byref(h)))
+    else:
+        ctx.check(lib().drg_build_distance_matrix(ctx.h, g.h, int(k), float(sigma), C.byref(h)))
     d = DistanceMatrix(ctx, h)
     d.graph = g
     return d

@@ -160,6 +160,7 @@ void drg_params_default(drg_params* p) {
     p->multilevel = 1;
     p->coarsen = DRG_COARSEN_HEM;
     p->level_tables = 0;
+    p->perplexity = 0.f;
 }
 
 const char* drg_status_string(drg_status s) {
@@ -312,6 +313,24 @@ drg_status drg_build_distance_matrix(drg_ctx* ctx, const drg_graph* g, uint32_t 
     *out = nullptr;
     API_TRY
     *out = drg::build_dmat(ctx, g, k, sigma);
+    API_CATCH(ctx)
+}
+
+drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity,
+                                        drg_dmat** out) {
+    if (!ctx || !g || !out) return DRG_EINVAL;
+    *out = nullptr;
+    API_TRY
+    *out = drg::build_dmat(ctx, g, k, sigma, perplexity);
+    API_CATCH(ctx)
+}
+
+drg_status drg_dmat_calibration(drg_ctx* ctx, const drg_dmat* d, double* beta) {
+    if (!ctx || !d || !beta) return DRG_EINVAL;
+    API_TRY
+    DRG_CHECK(d->beta, DRG_EINVAL, "the matrix was built with a global sigma");
+    DRG_CUDA(cudaMemcpyAsync(beta, d->beta, sizeof(double) * d->n, cudaMemcpyDeviceToHost, ctx->stream));
+    drg::sync(ctx);
     API_CATCH(ctx)
 }
 

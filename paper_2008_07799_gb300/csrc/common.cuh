@@ -100,6 +100,7 @@ struct drg_dmat {
     uint32_t n = 0, k = 0;
     uint64_t nnz = 0;
     float sigma = 1.f;
+    float perplexity = 0.f;      // > 0: sigma_i calibrated per node (beta below)
     uint32_t shift = 0;
     uint64_t* rp = nullptr;      // [n + 1]
     uint32_t* col = nullptr;     // [nnz]
@@ -111,6 +112,7 @@ struct drg_dmat {
     uint32_t erec_bytes = 32;
     uint32_t* e_alias = nullptr; // [nnz] alias entry of each bucket
     uint2* vtab = nullptr;       // [n] {thresh, alias}
+    double* beta = nullptr;      // [n] 1/(2 sigma_i^2) when calibrated
 };
 
 struct drg_hier {
@@ -280,7 +282,7 @@ void build_csr_from_keys(drg_ctx* ctx, uint32_t n, uint64_t* keys, uint32_t* val
 drg_graph* graph_from_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                             bool on_device);
 void graph_free(drg_graph* g);
-drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma);
+drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity = 0.f);
 void dmat_free(drg_dmat* d);
 drg_graph* coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params& p, uint32_t* parent);
 drg_hier* build_hierarchy(drg_ctx* ctx, const drg_graph* g0, const drg_params& p);

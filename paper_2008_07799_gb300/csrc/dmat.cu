@@ -725,8 +725,11 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t q, uint32_t lo, uint32_t 
 // correctly rounded with no fused multiply-add.  One warp per row; each lane
 // reads aligned 16-byte pieces of the row's distances and counts the bytes
 // of each class with byte-wise compares.
+// With COUNTS the row's class counts go to cnt[i k + d - 1] instead (the
+// perplexity calibration needs them, not Z).
+template <bool COUNTS>
 __global__ void k_row_Z(const uint64_t* __restrict__ rp, const uint8_t* __restrict__ dist, uint32_t n, uint32_t k,
-                        Gauss gs, float* __restrict__ Z) {
+                        Gauss gs, float* __restrict__ Z, uint32_t* __restrict__ cnt) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -755,10 +758,88 @@ __global__ void k_row_Z(const uint64_t* __restrict__ rp, const uint8_t* __restri
                 uint32_t t = c[d];
 #pragma unroll
                 for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
-                z = __fadd_rn(z, __fmul_rn(__uint2float_rn(t), gs.g[d]));
+                if (COUNTS) {
+                    if (lane == 0) cnt[i * k + d] = t;
+                } else {
+                    z = __fadd_rn(z, __fmul_rn(__uint2float_rn(t), gs.g[d]));
+                }
             }
         }
-        if (lane == 0) Z[i] = z;
+        if (!COUNTS && lane == 0) Z[i] = z;
+    }
+}
+
+// ------------------------------------------------------------------ perplexity calibration
+// Eq. 9's sigma_i per node by the perplexity rule: row i holds c_d nodes at
+// hop distance d; with beta = 1/(2 sigma_i^2) and w_d = e^{-beta (d^2 - 1)},
+// exp(H_i) = Z' exp(beta S'/Z') (Z' = sum c_d w_d, S' = sum c_d (d^2 - 1) w_d)
+// falls from the row size to c_1 as beta grows; 60 bisection steps on
+// [0, 512] give beta_i.  All FP64 with separately rounded operations and the
+// exponential below, so beta_i is a fixed function of the counts; then
+// g_i(d) = fl32(e^{-beta_i (d^2 - 1)}), Z_i as for a global sigma, and the
+// per-node table W_i(d) = fl32(g_i(d) / Z_i) that the quantisation reads.
+struct ExpPoly {
+    double c[14];  // 1/n!, n = 0..13
+};
+
+// e^x: Cody & Waite's reduction x = m ln2 + r (ln 2 as a 32-significant-bit
+// head and a tail, so m * head is exact), degree-13 Taylor polynomial of e^r
+// by Horner's rule, times 2^m from its bits; 0 below -700.
+__device__ __forceinline__ double cal_exp(double x, const ExpPoly& P) {
+    if (x < -700.0) return 0.0;
+    const double m = floor(__dadd_rn(__dmul_rn(x, 1.4426950408889634), 0.5));
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(m, 0.6931471803691238)), __dmul_rn(m, 1.9082149292705877e-10));
+    double p = P.c[13];
+#pragma unroll
+    for (int i = 12; i >= 0; --i) p = __dadd_rn(__dmul_rn(p, r), P.c[i]);
+    const double scale = __longlong_as_double((long long)((int)m + 1023) << 52);
+    return __dmul_rn(p, scale);
+}
+
+__device__ __forceinline__ double cal_perplexity(const uint32_t* c, uint32_t k, double beta, const ExpPoly& P) {
+    double z = 0.0, s = 0.0;
+    for (uint32_t d = 1; d <= k; ++d) {
+        const double dd = (double)(d * d - 1);
+        const double w = cal_exp(-__dmul_rn(beta, dd), P);
+        const double cd = (double)c[d - 1];
+        z = __dadd_rn(z, __dmul_rn(cd, w));
+        s = __dadd_rn(s, __dmul_rn(__dmul_rn(cd, dd), w));
+    }
+    return __dmul_rn(z, cal_exp(__dmul_rn(beta, __ddiv_rn(s, z)), P));
+}
+
+// One thread per node: beta_i, Z_i and W_i(1..k) (all zero for an empty row).
+__global__ void k_calibrate(const uint32_t* __restrict__ cnt, uint32_t n, uint32_t k, double perplexity, ExpPoly P,
+                            double* __restrict__ beta, float* __restrict__ Z, float* __restrict__ W) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t c[15];
+        uint64_t size = 0;
+        for (uint32_t d = 0; d < k; ++d) {
+            c[d] = cnt[v * k + d];
+            size += c[d];
+        }
+        if (size == 0) {
+            beta[v] = 0.0;
+            Z[v] = 0.f;
+            for (uint32_t d = 0; d < k; ++d) W[v * k + d] = 0.f;
+            continue;
+        }
+        double lo = 0.0, hi = 512.0;
+        for (int it = 0; it < 60; ++it) {
+            const double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+            if (cal_perplexity(c, k, mid, P) > perplexity) lo = mid;
+            else hi = mid;
+        }
+        const double b = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+        beta[v] = b;
+        float g[15];
+        float z = 0.f;
+        for (uint32_t d = 1; d <= k; ++d) {
+            g[d - 1] = __double2float_rn(cal_exp(-__dmul_rn(b, (double)(d * d - 1)), P));
+            z = __fadd_rn(z, __fmul_rn(__uint2float_rn(c[d - 1]), g[d - 1]));
+        }
+        Z[v] = z;
+        for (uint32_t d = 0; d < k; ++d) W[v * k + d] = __fdiv_rn(g[d], z);
     }
 }
 
@@ -773,9 +854,13 @@ __device__ __forceinline__ uint32_t quantise1(float gd, float zi, float zj) {
 // so a thread adds any run of its own entries that ends inside its four, and
 // the warp sums the open runs by row (segmented suffix sums over the lanes)
 // and adds each row's total with one atomic.  r must start at zero.
+// With PERNODE the two conditional similarities come from the calibrated
+// per-node table W (fl32(g_i(d) / Z_i), row-major n x k) instead.
+template <bool PERNODE>
 __global__ void k_quantise_r(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
                              const uint8_t* __restrict__ dist, const float* __restrict__ Z, Gauss gs, uint64_t nnz,
-                             uint32_t* __restrict__ q, unsigned long long* __restrict__ r) {
+                             uint32_t* __restrict__ q, unsigned long long* __restrict__ r,
+                             const float* __restrict__ W, uint32_t k) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t nv = (nnz + 3) / 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -805,7 +890,14 @@ __global__ void k_quantise_r(const uint32_t* __restrict__ esrc, const uint32_t* 
                 }
             }
 #pragma unroll
-            for (int t = 0; t < 4; ++t) qq[t] = quantise1(gs.g[dd[t] - 1], Z[ii[t]], Z[jj[t]]);
+            for (int t = 0; t < 4; ++t) {
+                if (PERNODE) {
+                    const float s = __fadd_rn(W[(uint64_t)ii[t] * k + dd[t] - 1], W[(uint64_t)jj[t] * k + dd[t] - 1]);
+                    qq[t] = __float2uint_rz(__fmul_rn(s, 1073741824.0f));
+                } else {
+                    qq[t] = quantise1(gs.g[dd[t] - 1], Z[ii[t]], Z[jj[t]]);
+                }
+            }
             if (cnt == 4) {
                 *reinterpret_cast<uint4*>(q + e) = make_uint4(qq[0], qq[1], qq[2], qq[3]);
             } else {
@@ -1273,21 +1365,23 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& ou
 void dmat_free(drg_dmat* d) {
     if (!d) return;
     drg_ctx* c = d->ctx;
-    void* ps[] = {d->rp, d->col, d->dist, d->q, d->r, d->Z, d->etab, d->e_alias, d->vtab};
+    void* ps[] = {d->rp, d->col, d->dist, d->q, d->r, d->Z, d->etab, d->e_alias, d->vtab, d->beta};
     for (void* p : ps)
         if (p) dfree(c, p);
     delete d;
 }
 
-drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) {
+drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity) {
     DRG_CHECK(g, DRG_EINVAL, "null graph");
     DRG_CHECK(k >= 1 && k <= 15, DRG_EINVAL, "k must be in [1, 15]");
     DRG_CHECK(sigma > 0.f, DRG_EINVAL, "sigma must be positive");
+    DRG_CHECK(perplexity >= 0.f && perplexity < 4.2e9f, DRG_EINVAL, "perplexity must be in [0, 4.2e9)");
     drg_dmat* d = new drg_dmat();
     d->ctx = ctx;
     d->n = g->n;
     d->k = k;
     d->sigma = sigma;
+    d->perplexity = perplexity;
     try {
         DRG_CHECK(g->nnz > 0, DRG_EEMPTY, "graph has no edges");
         ProfSpan span(ctx, DRG_PROF_DMAT, 0);
@@ -1303,12 +1397,30 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma) 
         d->q = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * nnz));
         d->r = static_cast<uint64_t*>(dalloc(ctx, sizeof(uint64_t) * n));
         const uint32_t gw = grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16);
-        DRG_LAUNCH(ctx, k_row_Z, gw, 256, 0, d->rp, d->dist, n, k, gs, d->Z);
+        DBuf<float> W;
+        if (perplexity > 0.f) {
+            ExpPoly P;
+            P.c[0] = 1.0;
+            for (int x = 1; x < 14; ++x) P.c[x] = P.c[x - 1] / (double)x;
+            DBuf<uint32_t> cnt(ctx, (size_t)n * k);
+            W = DBuf<float>(ctx, (size_t)n * k);
+            d->beta = static_cast<double*>(dalloc(ctx, sizeof(double) * n));
+            DRG_LAUNCH(ctx, k_row_Z<true>, gw, 256, 0, d->rp, d->dist, n, k, gs, d->Z, cnt.p);
+            DRG_LAUNCH(ctx, k_calibrate, grid_for(n, 128, (uint32_t)ctx->num_sms * 16), 128, 0, cnt.p, n, k,
+                       (double)perplexity, P, d->beta, d->Z, W.p);
+        } else {
+            DRG_LAUNCH(ctx, k_row_Z<false>, gw, 256, 0, d->rp, d->dist, n, k, gs, d->Z, (uint32_t*)nullptr);
+        }
         DBuf<uint32_t> esrc(ctx, nnz);
         DRG_LAUNCH(ctx, k_expand_rows, gw, 256, 0, d->rp, n, esrc.p);
         DRG_CUDA(cudaMemsetAsync(d->r, 0, sizeof(uint64_t) * n, ctx->stream));
-        DRG_LAUNCH(ctx, k_quantise_r, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist, d->Z, gs, nnz,
-                   d->q, reinterpret_cast<unsigned long long*>(d->r));
+        if (perplexity > 0.f)
+            DRG_LAUNCH(ctx, k_quantise_r<true>, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist,
+                       d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r), (const float*)W.p, k);
+        else
+            DRG_LAUNCH(ctx, k_quantise_r<false>, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist,
+                       d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r), (const float*)nullptr, k);
+        W.reset();
         DBuf<unsigned long long> rmax(ctx, 1);
         DRG_CUDA(cudaMemsetAsync(rmax.p, 0, 8, ctx->stream));
         DRG_LAUNCH(ctx, k_rmax, grid_for(n, 256, (uint32_t)ctx->num_sms * 8), 256, 0, d->r, n, rmax.p);

@@ -760,6 +760,7 @@ void check_params(const drg_params& p) {
     DRG_CHECK(p.coarsen == DRG_COARSEN_HEM || p.coarsen == DRG_COARSEN_STAR, DRG_EINVAL,
               "coarsen must be DRG_COARSEN_HEM or DRG_COARSEN_STAR");
     DRG_CHECK(p.level_tables == 0 || p.level_tables == 1, DRG_EINVAL, "level_tables must be 0 or 1");
+    DRG_CHECK(p.perplexity >= 0.f && p.perplexity < 4.2e9f, DRG_EINVAL, "perplexity must be in [0, 4.2e9)");
 }
 
 static int int_b(float b) {
@@ -1168,7 +1169,7 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
     std::unique_ptr<WorkerCtx> hw;  // owns h when built concurrently; freed after h
     try {
         if (ctx->prof) {
-            d = build_dmat(ctx, g, p.k, p.sigma);
+            d = build_dmat(ctx, g, p.k, p.sigma, p.perplexity);
             h = build_hierarchy(ctx, g, p);
         } else {
             // the hierarchy does not need the distance matrix: a worker thread
@@ -1185,7 +1186,7 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
                 }
             });
             try {
-                d = build_dmat(ctx, g, p.k, p.sigma);
+                d = build_dmat(ctx, g, p.k, p.sigma, p.perplexity);
             } catch (...) {
                 th.join();
                 throw;
@@ -1206,7 +1207,7 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
             const float gamma = (l == (int)L && L > 0) ? p.gamma_coarsest : p.gamma;
             if (p.level_tables && l > 0) {
                 // the conventional scheme: this level's own matrix and tables
-                drg_dmat* dl = build_dmat(ctx, h->g[l], p.k, p.sigma);
+                drg_dmat* dl = build_dmat(ctx, h->g[l], p.k, p.sigma, p.perplexity);
                 try {
                     layout_level(ctx, dl, h, (uint32_t)l, cur_pos, p, gamma, 0, p.epochs);
                     sync(ctx);
@@ -1310,7 +1311,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
             for (uint32_t g = 0; g < count; ++g) {
                 drg_params q = p;
                 q.gid = g;
-                gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma);
+                gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma, p.perplexity);
                 gs[g].h = build_hierarchy(ctx, graphs[g], q);
             }
         } else {
@@ -1329,7 +1330,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                             if (g >= count || failed.load()) break;
                             drg_params q = p;
                             q.gid = g;
-                            gs[g].d = build_dmat(wc, graphs[g], p.k, p.sigma);
+                            gs[g].d = build_dmat(wc, graphs[g], p.k, p.sigma, p.perplexity);
                             gs[g].h = build_hierarchy(wc, graphs[g], q);
                         }
                         sync(wc);

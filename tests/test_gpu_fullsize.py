@@ -212,3 +212,24 @@ def test_dcsbm1m_star_hierarchy_and_quality(env, orc):
         Y = pos.cpu().numpy().astype(np.float64).reshape(-1, 2)
         nps[rule] = orc.neighbourhood_preservation(rp, col, Y, 2, nodes)
     assert nps[1] >= 0.65 * nps[0] and nps[1] > 0.02, nps
+
+
+def test_dcsbm1m_perplexity_calibration(env, orc):
+    """sigma_i calibrated per node on the 3.4e9-entry k=2 matrix of the bench
+    graph: beta_i of sampled rows (the hubs among them) bit for bit against
+    the oracle's calibration of the same class counts."""
+    drg, ctx = env
+    g = gg.workload("dcsbm1m")
+    n = g[0]
+    rp, col = orc.canonical_graph(*g)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, 2, perplexity=30.0)
+    beta = D.calibration()
+    deg = np.diff(rp).astype(np.int64)
+    rows = np.r_[np.random.default_rng(5).choice(np.nonzero(deg > 0)[0], 40, replace=False),
+                 np.argsort(deg)[-4:]].astype(np.uint32)
+    counts = orc.class_counts(rp, col, 2, rows)
+    for x, i in enumerate(rows):
+        want = orc.calibrate_row(counts[x], 30.0)
+        assert beta[i].view(np.uint64) == np.float64(want).view(np.uint64), (int(i), beta[i], want)
+    assert np.all(beta[deg == 0] == 0.0)

@@ -101,6 +101,51 @@ def test_distance_matrix_and_tables(drg, ctx, orc, name, k):
     assert np.array_equal(got["v_thresh"], vth) and np.array_equal(got["v_alias"], val)
 
 
+@pytest.mark.parametrize("name,k,P", [("grid32", 3, 30.0), ("ba2000", 2, 30.0), ("ba2000", 3, 50.0),
+                                      ("tree3000", 3, 5.0), ("er_ragged", 2, 12.0), ("path7", 3, 2.5),
+                                      ("er_ragged", 1, 4.0)])
+def test_perplexity_tables(drg, ctx, orc, name, k, P):
+    # sigma_i calibrated per node: beta_i (FP64), Z, q, the node weights and
+    # both alias tables bit for bit
+    g = _graphs()[name]
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, k, perplexity=P)
+    got = D.download()
+    orp, ocol = _oracle_csr(orc, g)
+    gd = orc.korder(orp, ocol, k)
+    assert np.array_equal(got["col"], gd[1]) and np.array_equal(got["dist"], gd[2])
+    sim = orc.similarity_perplexity(*gd, k, P)
+    assert np.array_equal(D.calibration().view(np.uint64), sim["beta"].view(np.uint64))
+    assert np.array_equal(got["Z"].view(np.uint32), sim["Z"].view(np.uint32))
+    assert np.array_equal(got["q"], sim["q"]) and np.array_equal(got["r"], sim["r"])
+    r32, shift = orc.node_weights_u32(sim["r"])
+    assert got["shift"] == shift
+    th, al, _ = orc.alias_build(sim["q"])
+    assert np.array_equal(got["e_thresh"], th) and np.array_equal(got["e_alias"], al)
+    vth, val, _ = orc.alias_build(r32)
+    assert np.array_equal(got["v_thresh"], vth) and np.array_equal(got["v_alias"], val)
+    # a global-sigma matrix has no calibration; bad perplexities are refused
+    with pytest.raises(drg.DrgError):
+        drg.build_distance_matrix(ctx, G, k).calibration()
+    for bad in (-1.0, float("nan"), 5e9):
+        with pytest.raises(drg.DrgError):
+            drg.build_distance_matrix(ctx, G, k, perplexity=bad)
+
+
+def test_perplexity_whole_run(drg, ctx, orc):
+    # the whole path with calibrated similarities matches the oracle's
+    # quality (grid 40x40, k=2, perplexity 10, multilevel)
+    n, s, d = gg.grid(40, 40)
+    G = drg.graph_from_edges(ctx, n, s, d)
+    p = drg.Params.default(k=2, M=5, epochs=60, b=3.0, mode=1, stop_nodes=200, seed=2, perplexity=10.0)
+    pos = torch.zeros(2 * n, device="cuda")
+    drg.layout(ctx, G, p, pos)
+    Y = pos.cpu().numpy().astype(np.float64).reshape(-1, 2)
+    rp, col = orc.canonical_graph(n, s, d)
+    ref = orc.run(n, s, d, orc.Params(k=2, M=5, epochs=60, b=3.0, mode=1, stop_nodes=200, seed=2, perplexity=10.0))
+    assert orc.neighbourhood_preservation(rp, col, Y, 2) >= 0.8 * orc.neighbourhood_preservation(rp, col, ref, 2)
+
+
 def _device_tables(orc, g, k, sigma=1.0):
     orp, ocol = _oracle_csr(orc, g)
     gd = orc.korder(orp, ocol, k)
