@@ -103,6 +103,9 @@ def lib():
     L.orc_calibrate_row.restype = C.c_double
     L.orc_similarity_perplexity.argtypes = [C.c_uint32, U64P, U32P, U8P, C.c_uint32, C.c_float, F64P, F32P, U32P,
                                             U64P, C.c_void_p]
+    L.orc_crossings.argtypes = [C.c_uint32, U64P, U32P, F64P, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
+    L.orc_min_angle.argtypes = [C.c_uint32, U64P, U32P, F64P]
+    L.orc_min_angle.restype = C.c_double
     L.orc_star_group.argtypes = [C.c_uint32, U64P, U32P, U32P, U32P]
     L.orc_star_priorities.argtypes = [C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, U32P]
     L.orc_star_priorities.restype = None
@@ -524,6 +527,24 @@ def neighbourhood_preservation(rp, col, Y, k_eval=2, nodes=None):
                                              np.ascontiguousarray(Y, np.float64).reshape(-1), k_eval,
                                              n if sel is None else len(sel), _ptr(sel), C.byref(cnt))
     return v
+
+
+def crossings(rp, col, Y):
+    """Sec. 4.1 Eq. 17: (number of edge crossings, crosslessness), crossings
+    decided exactly on positions snapped per axis to a 30-bit grid."""
+    n = len(rp) - 1
+    c = C.c_uint64()
+    cl = C.c_double()
+    assert lib().orc_crossings(n, np.ascontiguousarray(rp, np.uint64), col if len(col) else np.zeros(1, np.uint32),
+                               np.ascontiguousarray(Y, np.float64).reshape(-1), C.byref(c), C.byref(cl)) == 0
+    return int(c.value), float(cl.value)
+
+
+def min_angle(rp, col, Y):
+    """Sec. 4.1 Eq. 19, over nodes with at least one edge."""
+    n = len(rp) - 1
+    return lib().orc_min_angle(n, np.ascontiguousarray(rp, np.uint64), col if len(col) else np.zeros(1, np.uint32),
+                               np.ascontiguousarray(Y, np.float64).reshape(-1))
 
 
 def stress(rp, col, Y, sources=None):

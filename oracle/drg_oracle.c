@@ -917,3 +917,120 @@ double orc_stress(uint32_t n, const uint64_t* rp, const uint32_t* col, const dou
     double scale = nsel ? (double)n / (double)nsel : 0.0;
     return s * scale / ((double)n * (double)n);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1 Eq. 17, crosslessness: 1 - sqrt(c / c_max) (1 when c_max = 0),
+ * c the number of unordered pairs of edges that cross, c_max =
+ * |E|(|E|-1)/2 - (1/2) sum_v deg(v)(deg(v)-1).  Edges are the graph's
+ * undirected edges drawn as straight segments.  To decide crossings exactly,
+ * positions are first snapped per axis to the grid 0..2^30-1 over the
+ * layout's bounding box, q = floor((x - min) / (max - min) * (2^30 - 1) + 0.5)
+ * in FP64 (q = 0 when max = min); an affine map changes no crossing, so only
+ * near-degenerate pairs can be decided differently from the unsnapped
+ * drawing.  Two edges without a common endpoint cross when each separates
+ * the other's endpoints strictly: orient(a,b,c) and orient(a,b,d) have
+ * opposite signs and so have orient(c,d,a) and orient(c,d,b), with
+ * orient(a,b,c) = (bx-ax)(cy-ay) - (by-ay)(cx-ax) exact in 64-bit integers
+ * (touching and collinear pairs do not count).  Brute force over all pairs.
+ * Pinned by hand-drawn cases, closed forms on grids and stars, and exact
+ * rational segment intersection (sympy) on random drawings.                 */
+static void orc_snap(uint32_t n, const double* Y, int axis, int64_t* q)
+{
+    double lo = 0.0, hi = 0.0;
+    for (uint32_t v = 0; v < n; ++v) {
+        double x = Y[2 * v + axis];
+        if (v == 0 || x < lo) lo = x;
+        if (v == 0 || x > hi) hi = x;
+    }
+    double span = hi - lo;
+    for (uint32_t v = 0; v < n; ++v)
+        q[v] = span > 0.0 ? (int64_t)floor((Y[2 * v + axis] - lo) / span * 1073741823.0 + 0.5) : 0;
+}
+
+static int orc_sign(int64_t x) { return (x > 0) - (x < 0); }
+
+static int64_t orc_orient(const int64_t* qx, const int64_t* qy, uint32_t a, uint32_t b, uint32_t c)
+{
+    return (qx[b] - qx[a]) * (qy[c] - qy[a]) - (qy[b] - qy[a]) * (qx[c] - qx[a]);
+}
+
+int orc_crossings(uint32_t n, const uint64_t* rp, const uint32_t* col, const double* Y,
+                  uint64_t* crossings, double* crosslessness)
+{
+    int64_t* qx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    int64_t* qy = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    uint64_t m = rp[n] / 2;
+    uint32_t* eu = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
+    uint32_t* ev = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
+    if (!qx || !qy || !eu || !ev) { free(qx); free(qy); free(eu); free(ev); return -1; }
+    orc_snap(n, Y, 0, qx);
+    orc_snap(n, Y, 1, qy);
+    uint64_t ne = 0;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = rp[u]; e < rp[u + 1]; ++e)
+            if (col[e] > u) { eu[ne] = u; ev[ne] = col[e]; ++ne; }
+    uint64_t c = 0;
+    for (uint64_t x = 0; x < ne; ++x)
+        for (uint64_t y = x + 1; y < ne; ++y) {
+            uint32_t a = eu[x], b = ev[x], p = eu[y], r = ev[y];
+            if (a == p || a == r || b == p || b == r) continue;
+            int s1 = orc_sign(orc_orient(qx, qy, a, b, p)), s2 = orc_sign(orc_orient(qx, qy, a, b, r));
+            int s3 = orc_sign(orc_orient(qx, qy, p, r, a)), s4 = orc_sign(orc_orient(qx, qy, p, r, b));
+            if (s1 * s2 < 0 && s3 * s4 < 0) ++c;
+        }
+    /* c_max = |E|(|E|-1)/2 - sum_v deg(v)(deg(v)-1)/2, exact */
+    unsigned __int128 cmax = (unsigned __int128)ne * (ne ? ne - 1 : 0) / 2;
+    unsigned __int128 adj = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+        uint64_t d = rp[v + 1] - rp[v];
+        adj += (unsigned __int128)d * (d ? d - 1 : 0) / 2;
+    }
+    cmax -= adj;
+    *crossings = c;
+    *crosslessness = cmax > 0 ? 1.0 - sqrt((double)c / (double)cmax) : 1.0;
+    free(qx); free(qy); free(eu); free(ev);
+    return 0;
+}
+
+/* Sec. 4.1 Eq. 19, minimum angle: 1 - mean over nodes of
+ * |theta(v) - theta_min(v)| / theta(v), theta(v) = 2 pi / deg(v), theta_min(v)
+ * the smallest angle between two edges at v that are consecutive around it
+ * (directions atan2(y_u - y_v, x_u - x_v), sorted; the wrap-around gap
+ * included).  The mean runs over nodes with an edge (isolated nodes are never
+ * drawn); a node of degree 1 has no angle and deviates by 0.  Pinned by
+ * closed forms on grids, regular stars and a path.                           */
+static int orc_cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+double orc_min_angle(uint32_t n, const uint64_t* rp, const uint32_t* col, const double* Y)
+{
+    uint64_t dmax = 0;
+    for (uint32_t v = 0; v < n; ++v)
+        if (rp[v + 1] - rp[v] > dmax) dmax = rp[v + 1] - rp[v];
+    double* ang = (double*)malloc(sizeof(double) * (size_t)(dmax ? dmax : 1));
+    if (!ang) return -1.0;
+    const double two_pi = 6.283185307179586;
+    double dev = 0.0;
+    uint64_t counted = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+        uint64_t d = rp[v + 1] - rp[v];
+        if (d == 0) continue;
+        ++counted;
+        if (d == 1) continue;
+        for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+            uint32_t u = col[e];
+            ang[e - rp[v]] = atan2(Y[2 * u + 1] - Y[2 * v + 1], Y[2 * u] - Y[2 * v]);
+        }
+        qsort(ang, d, sizeof(double), orc_cmp_double);
+        double mn = two_pi - (ang[d - 1] - ang[0]);
+        for (uint64_t x = 1; x < d; ++x)
+            if (ang[x] - ang[x - 1] < mn) mn = ang[x] - ang[x - 1];
+        double theta = two_pi / (double)d;
+        dev += fabs(theta - mn) / theta;
+    }
+    free(ang);
+    return counted ? 1.0 - dev / (double)counted : 1.0;
+}

@@ -377,6 +377,89 @@ def test_level_tables_sample_each_level_graph(orc, coarsen):
     p2 = orc.Params(k=k, M=5, epochs=3, b=1.0, mode=0, multilevel=False, seed=4, level_tables=1)
     assert np.array_equal(orc.run(n, s, d, p1), orc.run(n, s, d, p2))
 
+
+# ------------------------------------ crosslessness and minimum angle (Sec. 4.1)
+def test_crossings_hand_drawn(orc):
+    # K4 on a square: only the two diagonals cross; c_max = 15 - 4*3 = 3
+    rp, col = _graph(4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)])
+    Y = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], float)
+    c, cl = orc.crossings(rp, col, Y)
+    assert c == 1 and math.isclose(cl, 1 - math.sqrt(1 / 3), rel_tol=1e-15)
+    # the same K4 drawn with one node inside the triangle of the others: planar
+    Y2 = np.array([[0, 0], [4, 0], [2, 3], [2, 1]], float)
+    assert orc.crossings(rp, col, Y2) == (0, 1.0)
+    # touching (a T) and collinear overlapping segments do not count
+    rp, col = _graph(6, [(0, 1), (2, 3), (4, 5)])
+    Y = np.array([[0, 0], [4, 0], [2, 0], [2, 3], [1, 0], [3, 0]], float)
+    assert orc.crossings(rp, col, Y)[0] == 0
+
+
+@pytest.mark.parametrize("r,c", [(5, 4), (8, 8), (3, 11)])
+def test_grid_drawings_closed_forms(orc, r, c):
+    n, s, d = gg.grid(r, c)
+    rp, col = orc.canonical_graph(n, s, d)
+    Y = np.array([[v % c, v // c] for v in range(n)], float)
+    assert orc.crossings(rp, col, Y) == (0, 1.0)
+    # interior nodes: four right angles (deviation 0); border nodes of degree
+    # 3: 90 against 120 degrees (1/4); corners: 90 against 180 (1/2)
+    dev = 4 * 0.5 + (2 * (r - 2) + 2 * (c - 2)) * 0.25
+    assert math.isclose(orc.min_angle(rp, col, Y), 1 - dev / (r * c), rel_tol=1e-13)
+
+
+def test_star_and_path_angles(orc):
+    d = 7
+    rp, col = _graph(d + 1, [(0, v) for v in range(1, d + 1)])
+    t = 2 * np.pi * np.arange(d) / d
+    Y = np.r_[[[0.0, 0.0]], np.c_[np.cos(t), np.sin(t)]]
+    assert orc.crossings(rp, col, Y) == (0, 1.0)          # c_max = 0 for a star
+    assert math.isclose(orc.min_angle(rp, col, Y), 1.0, abs_tol=1e-13)
+    # three leaves at 0, 10 and 180 degrees: theta 120, minimum 10
+    rp, col = _graph(4, [(0, 1), (0, 2), (0, 3)])
+    a = np.radians([0.0, 10.0, 180.0])
+    Y = np.r_[[[0.0, 0.0]], np.c_[np.cos(a), np.sin(a)]]
+    assert math.isclose(orc.min_angle(rp, col, Y), 1 - (110 / 120) / 4, rel_tol=1e-12)
+    # a path: straight (every inner angle 180) and zigzag with right angles
+    rp, col = _graph(6, [(v, v + 1) for v in range(5)])
+    assert math.isclose(orc.min_angle(rp, col, np.c_[np.arange(6.0), np.zeros(6)]), 1.0, abs_tol=1e-13)
+    zig = np.array([[0, 0], [1, 0], [1, 1], [2, 1], [2, 2], [3, 2]], float)
+    assert math.isclose(orc.min_angle(rp, col, zig), 1 - 4 * 0.5 / 6, rel_tol=1e-13)
+    # isolated nodes are not counted
+    rp, col = _graph(9, [(v, v + 1) for v in range(5)])
+    Y9 = np.r_[zig, [[5.0, 5.0], [6.0, 6.0], [7.0, 7.0]]]
+    assert math.isclose(orc.min_angle(rp, col, Y9), 1 - 4 * 0.5 / 6, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_crossings_match_exact_rational_geometry(orc, seed):
+    # random drawings: the snapped integer test against sympy's exact
+    # intersection of the unsnapped segments (proper crossings only), and
+    # invariance under an affine map of the drawing
+    sympy = pytest.importorskip("sympy")
+    from sympy import Point, Rational, Segment
+    rng = np.random.default_rng(seed)
+    n = 14
+    edges = {tuple(sorted(e)) for e in rng.integers(0, n, size=(40, 2)).tolist() if e[0] != e[1]}
+    edges = sorted(edges)[:24]
+    rp, col = _graph(n, edges)
+    Y = rng.normal(size=(n, 2))
+    pts = [Point(Rational(x), Rational(y)) for x, y in Y]
+    want = 0
+    for x in range(len(edges)):
+        for y in range(x + 1, len(edges)):
+            (a, b), (p, q) = edges[x], edges[y]
+            if len({a, b, p, q}) < 4:
+                continue
+            inter = Segment(pts[a], pts[b]).intersection(Segment(pts[p], pts[q]))
+            if inter and isinstance(inter[0], Point) and inter[0] not in (pts[a], pts[b], pts[p], pts[q]):
+                want += 1
+    c, cl = orc.crossings(rp, col, Y)
+    assert c == want and want > 0
+    m = len(edges)
+    deg = np.diff(rp).astype(np.int64)
+    cmax = m * (m - 1) // 2 - int((deg * (deg - 1) // 2).sum())
+    assert math.isclose(cl, 1 - math.sqrt(want / cmax), rel_tol=1e-15)
+    assert orc.crossings(rp, col, Y * [7.0, 0.1] + [3.0, -2.0])[0] == c
+
 # ---------------------------------------------------------------- metrics
 def test_metrics_of_a_path_on_a_line(orc):
     n, s, d = gg.path(40)
