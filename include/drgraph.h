@@ -326,6 +326,30 @@ drg_status drg_layout_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
 drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, const drg_params* p,
                             const float* b, float* const* pos);
 
+/* ---------------------------------------------------------------- quality metrics */
+/* Sec. 4.1 Eq. 17, crosslessness of a drawing of g: *crosslessness =
+ * 1 - sqrt(c / c_max) (1 when c_max = 0), *crossings = c, the number of
+ * unordered pairs of edges (straight segments) that cross, c_max =
+ * |E|(|E|-1)/2 - (1/2) sum_v deg(v)(deg(v)-1).  Crossings are decided
+ * exactly: positions snap per axis to the grid 0..2^30-1 over the drawing's
+ * bounding box, q = floor((x - min) / (max - min) * (2^30 - 1) + 0.5) in FP64
+ * (0 when max = min; an affine map changes no crossing), and two edges
+ * without a common endpoint cross when each strictly separates the other's
+ * endpoints by 64-bit integer orientation tests (touching and collinear
+ * pairs do not count).  All pairs are tested (|E|^2 / 2 tests, about 2 s for
+ * 4 million edges).  pos: device float[2 n].  DRG_EINVAL for a non-finite
+ * coordinate.  Synchronises. */
+drg_status drg_crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* crossings,
+                         double* crosslessness);
+/* Sec. 4.1 Eq. 19, minimum angle: *min_angle = 1 - mean over nodes of
+ * |theta(v) - theta_min(v)| / theta(v), theta(v) = 2 pi / deg(v), theta_min(v)
+ * the smallest angle between two edges consecutive around v (directions
+ * atan2 in FP64; the wrap-around gap included).  The mean runs over nodes
+ * with at least one edge; a node of degree 1 deviates by 0.  Directions
+ * closer than 2 pi / 2^32 may be ordered either way (their gap then counts as
+ * 0).  pos: device float[2 n].  Synchronises. */
+drg_status drg_min_angle(drg_ctx* ctx, const drg_graph* g, const float* pos, double* min_angle);
+
 /* Self-check of the epoch gates of the Hogwild level runs (no counterpart in
  * the paper).  `blocks` one-warp thread blocks (1 .. number of SMs), launched
  * so that all are resident at once, run `rounds` (1 .. 100000) empty epochs;

@@ -7,7 +7,7 @@ C ABI in ``include/drgraph.h``:
 
     graph_from_edges, build_distance_matrix, coarsen, build_hierarchy,
     init_positions, layout_level, interpolate, layout, layout_edges,
-    layout_batch, sample_draws
+    layout_batch, sample_draws, crossings, min_angle
 
 There is no CPU fallback: without the built library (``build()``) every call
 raises.
@@ -37,7 +37,7 @@ EXPORTS = [
     "drg_init_positions", "drg_layout_level", "drg_interpolate", "drg_layout", "drg_layout_edges",
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
     "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
-    "drg_build_distance_matrix_ex", "drg_dmat_calibration",
+    "drg_build_distance_matrix_ex", "drg_dmat_calibration", "drg_crossings", "drg_min_angle",
 ]
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
@@ -111,6 +111,8 @@ def lib():
         "drg_dmat_destroy": (st, [VP]),
         "drg_build_distance_matrix_ex": (st, [VP, VP, C.c_uint32, C.c_float, C.c_float, C.POINTER(VP)]),
         "drg_dmat_calibration": (st, [VP, VP, VP]),
+        "drg_crossings": (st, [VP, VP, VP, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+        "drg_min_angle": (st, [VP, VP, VP, C.POINTER(C.c_double)]),
         "drg_dmat_download_range": (st, [VP, VP, C.c_uint64, C.c_uint64, VP, VP, VP, VP, VP]),
         "drg_coarsen": (st, [VP, VP, C.c_uint32, PP, C.POINTER(VP), VP]),
         "drg_build_hierarchy": (st, [VP, VP, PP, C.POINTER(VP)]),
@@ -367,6 +369,21 @@ def build_distance_matrix(ctx: Context, g: Graph, k: int, sigma: float = 1.0,
     d = DistanceMatrix(ctx, h)
     d.graph = g
     return d
+
+
+def crossings(ctx: Context, g: Graph, pos):
+    """Sec. 4.1 Eq. 17 of a drawing (device positions): (crossings, crosslessness)."""
+    c = C.c_uint64()
+    cl = C.c_double()
+    ctx.check(lib().drg_crossings(ctx.h, g.h, _ptr(pos), C.byref(c), C.byref(cl)))
+    return int(c.value), float(cl.value)
+
+
+def min_angle(ctx: Context, g: Graph, pos) -> float:
+    """Sec. 4.1 Eq. 19 of a drawing (device positions)."""
+    out = C.c_double()
+    ctx.check(lib().drg_min_angle(ctx.h, g.h, _ptr(pos), C.byref(out)))
+    return float(out.value)
 
 
 def coarsen(ctx: Context, g: Graph, level: int, p: Params, parent) -> Graph:

@@ -325,6 +325,21 @@ drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32
     API_CATCH(ctx)
 }
 
+drg_status drg_crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* crossings,
+                         double* crosslessness) {
+    if (!ctx || !g || !pos || !crossings || !crosslessness) return DRG_EINVAL;
+    API_TRY
+    drg::crossings(ctx, g, pos, crossings, crosslessness);
+    API_CATCH(ctx)
+}
+
+drg_status drg_min_angle(drg_ctx* ctx, const drg_graph* g, const float* pos, double* min_angle) {
+    if (!ctx || !g || !pos || !min_angle) return DRG_EINVAL;
+    API_TRY
+    *min_angle = drg::min_angle(ctx, g, pos);
+    API_CATCH(ctx)
+}
+
 drg_status drg_dmat_calibration(drg_ctx* ctx, const drg_dmat* d, double* beta) {
     if (!ctx || !d || !beta) return DRG_EINVAL;
     API_TRY

@@ -283,6 +283,8 @@ drg_graph* graph_from_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t
                             bool on_device);
 void graph_free(drg_graph* g);
 drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity = 0.f);
+void crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* c, double* crosslessness);
+double min_angle(drg_ctx* ctx, const drg_graph* g, const float* pos);
 void dmat_free(drg_dmat* d);
 drg_graph* coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params& p, uint32_t* parent);
 drg_hier* build_hierarchy(drg_ctx* ctx, const drg_graph* g0, const drg_params& p);

@@ -146,6 +146,35 @@ def test_perplexity_whole_run(drg, ctx, orc):
     assert orc.neighbourhood_preservation(rp, col, Y, 2) >= 0.8 * orc.neighbourhood_preservation(rp, col, ref, 2)
 
 
+@pytest.mark.parametrize("name", ["grid32", "ba2000", "er_ragged", "path7"])
+def test_crossings_and_min_angle(drg, ctx, orc, name):
+    # Sec. 4.1 metrics of random drawings and of a GPU layout: crossing counts
+    # and crosslessness bit for bit, minimum angle within 1e-9 (FP64 atan2 of
+    # two libraries); a drawing with every node at one point and a
+    # non-finite coordinate
+    g = _graphs()[name]
+    n = g[0]
+    G = drg.graph_from_edges(ctx, *g)
+    orp, ocol = _oracle_csr(orc, g)
+    rng = np.random.default_rng(3)
+    drawn = torch.zeros(2 * n, device="cuda")
+    drg.layout(ctx, G, drg.Params.default(k=2, M=5, epochs=40, b=1.0, mode=1, multilevel=0, seed=1), drawn)
+    drawings = [rng.normal(size=(n, 2)).astype(np.float32), drawn.cpu().numpy().reshape(n, 2),
+                np.full((n, 2), 0.25, np.float32)]
+    for Y in drawings:
+        pos = torch.from_numpy(np.ascontiguousarray(Y).reshape(-1)).cuda()
+        c, cl = drg.crossings(ctx, G, pos)
+        oc, ocl = orc.crossings(orp, ocol, Y.astype(np.float64))
+        assert c == oc and cl == ocl, (c, oc, cl, ocl)
+        ma = drg.min_angle(ctx, G, pos)
+        assert abs(ma - orc.min_angle(orp, ocol, Y.astype(np.float64))) <= 1e-9
+    assert drg.crossings(ctx, G, torch.from_numpy(drawings[0].reshape(-1)).cuda())[0] > 0 or name == "path7"
+    bad = drawings[0].copy()
+    bad[n // 2, 1] = np.nan
+    with pytest.raises(drg.DrgError):
+        drg.crossings(ctx, G, torch.from_numpy(bad.reshape(-1)).cuda())
+
+
 def _device_tables(orc, g, k, sigma=1.0):
     orp, ocol = _oracle_csr(orc, g)
     gd = orc.korder(orp, ocol, k)
