@@ -70,3 +70,16 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "updates/s"
+
+
+def test_traffic_record_only_for_its_configuration():
+    # the committed DRAM-traffic figure of the level kernel feeds the bench's
+    # roofline only for the configuration and kernel source it was taken on
+    sys.path.insert(0, ROOT)
+    import bench
+    cfg = {"workload": "dcsbm1m", "k": 2, "coarsen": "hem", "mode": "hogwild", "precision": "fp32",
+           "multilevel": True}
+    assert bench.ncu_traffic_per_sample("k_hogwild", cfg) is not None
+    for key, other in (("coarsen", "star"), ("workload", "ba100k"), ("k", 3), ("mode", "sync"), ("multilevel", False)):
+        assert bench.ncu_traffic_per_sample("k_hogwild", dict(cfg, **{key: other})) is None
+    assert bench.ncu_traffic_per_sample("k_no_such_kernel", cfg) is None
