@@ -9,9 +9,13 @@ The arithmetic lives in ``drg_oracle.c`` (plain C, FP64 layout math, exact
 integer graph and index work, its own Philox4x32-10); this module only
 marshals numpy arrays and runs the multilevel loop of Sec. 3.2.3 step by step:
 canonical graph -> sparse distance matrix (Sec. 3.2.1) -> similarity and
-quantised sampling weights -> alias tables (Sec. 3.2.2) -> hierarchy by
-heavy-edge matching (Sec. 3.2.3) -> coarsest random layout -> for each level,
-coarse to fine: epochs of negative-sampling SGD (Eqs. 11-12), then refinement.
+quantised sampling weights (one sigma, or sigma_i per node by perplexity) ->
+alias tables (Sec. 3.2.2) -> hierarchy by heavy-edge matching or the paper's
+star grouping (Sec. 3.2.3) -> coarsest random layout -> for each level, coarse
+to fine: epochs of negative-sampling SGD (Eqs. 11-12) on G^0's tables through
+the ancestor map or on the level's own tables, then refinement.  The quality
+metrics of Sec. 4.1 (NP, stress, crosslessness, minimum angle) evaluate the
+result.
 
 Parity status: every stage is pinned by ``tests/test_oracle_*.py`` against
 closed forms, brute force, library routines or invariants.  Whole-run layout

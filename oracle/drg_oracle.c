@@ -653,8 +653,9 @@ void orc_interpolate(uint32_t n_fine, const uint32_t* parent, const double* Yc, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 3.2.3 "Coarsening", with heavy-edge matching in place of the paper's
- * star grouping.  Deterministic handshake rounds: in round r every unmatched
+/* Sec. 3.2.3 "Coarsening" by heavy-edge matching (the default rule; the
+ * paper's own star grouping is orc_star_group below).  Deterministic
+ * handshake rounds: in round r every unmatched
  * node proposes to its unmatched neighbour with the largest key (edge weight,
  * then Philox hash of (min id, max id, round) under purpose 2, then the
  * smaller neighbour id); two nodes that propose to each other are matched.

@@ -1,6 +1,7 @@
-"""The grid barrier between the epochs of a Hogwild level run: it completes
-when every block arrives, and when one cannot (a barrier that expects more
-blocks than run) every wait ends after its limit with DRG_ETIMEOUT and the
+"""The epoch gates of a Hogwild level run (a warp waits for the others'
+completion counters before it runs ahead): a wait completes when every
+expected arrival comes, and when one cannot (a gate that expects more
+arrivals than run) every wait ends after its limit with DRG_ETIMEOUT and the
 context stays usable."""
 import numpy as np
 import pytest
