@@ -10,6 +10,7 @@
  *   drg_build_distance_matrix  Sec. 3.2.1 sparse k-order distance matrix (Eq. 8),
  *                                          similarity (Eqs. 4, 9) and the
  *                                          sampling tables of Sec. 3.2.2
+ *                                          (_ex: sigma_i per node by perplexity)
  *   drg_coarsen / drg_build_hierarchy
  *                              Sec. 3.2.3 coarsening (the paper's star grouping
  *                                          or heavy-edge matching)
@@ -17,10 +18,14 @@
  *                                          (Eqs. 11-12) at one level, samples
  *                                          drawn on G^0, gradients forwarded to
  *                                          the level through the ancestor map
+ *                                          (or on the level's own tables)
  *   drg_interpolate            Sec. 3.2.3 refinement: a fine node starts at its
  *                                          coarse node's position
  *   drg_layout / drg_layout_edges      the whole pipeline
  *   drg_layout_batch           many independent graphs in one launch per step
+ *   drg_crossings / drg_min_angle
+ *                              Sec. 4.1   crosslessness and minimum angle of a
+ *                                          drawing
  *
  * Conventions
  *   - Every call returns a drg_status; nothing aborts.  On error the context's
