@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -75,3 +76,17 @@ def test_status_strings_and_null_arguments(drg):
     assert L.drg_graph_destroy(None) == 1
     assert L.drg_layout(None, None, None, None) == 1
     assert L.drg_kernel_launches(None) == 0
+
+
+def test_missing_library_fails_loudly():
+    # no CPU fallback: without the built library the first call raises
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2008_07799_gb300 as m\n"
+            "m._lib = None\n"
+            "m.LIB_PATH = '/nonexistent/libdrgraph.so'\n"
+            "try:\n"
+            "    m.Context(0)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n") % ROOT
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "raised:" in out.stdout and "missing" in out.stdout, (out.stdout, out.stderr)
