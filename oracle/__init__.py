@@ -196,6 +196,71 @@ def korder(rp, col, k):
     return gd_rp, gd_col[:nnz], gd_dist[:nnz]
 
 
+def korder_capped(rp, col, k, cap):
+    """Sec. 3.2.1 with a per-row neighbour cap (a reading for graphs whose
+    k-order rows are too large): row i keeps K_i, its `cap` nearest entries by
+    (hop distance, node id); the sampling pattern is the union of the kept
+    entries and their transposes, rows sorted by column.  Returns the union
+    CSR (rp, col, dist) and per entry (i, j) the flags own (j in K_i) and
+    back (i in K_j).  Index work only; small graphs (the full rows are built
+    first)."""
+    n = len(rp) - 1
+    g_rp, g_col, g_dist = korder(rp, col, k)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g_rp).astype(np.int64))
+    c64 = g_col.astype(np.int64)
+    # rank of every entry within its row by (distance, column)
+    order = np.lexsort((c64, g_dist.astype(np.int64), rows))
+    start = g_rp[:-1].astype(np.int64)
+    rank = np.empty(len(order), np.int64)
+    rank[order] = np.arange(len(order)) - start[rows[order]]
+    kept = rank < cap
+    fwd = rows[kept] * n + c64[kept]
+    bwd = c64[kept] * n + rows[kept]
+    keys = np.union1d(fwd, bwd)
+    u_rows, u_col = keys // n, keys % n
+    own = np.isin(keys, fwd)
+    back = np.isin(keys, bwd)
+    dist_of = dict(zip((rows * n + c64).tolist(), g_dist.tolist()))
+    u_dist = np.array([dist_of[int(x)] for x in keys], np.uint8)
+    u_rp = np.zeros(n + 1, np.uint64)
+    np.cumsum(np.bincount(u_rows, minlength=n), out=u_rp[1:])
+    return u_rp, u_col.astype(np.uint32), u_dist, own, back
+
+
+def similarity_capped(u_rp, u_col, u_dist, own, back, k, sigma=1.0):
+    """Eq. 9 over each row's kept set K_i and Eq. 4 over the union pattern:
+    NS_{j|i} = g(d)/Z_i for j in K_i (else 0), Z_i = FP32 sum over d = 1..k of
+    fl32(count of K_i at distance d) * g(d); q_e = floor((a + b) 2^30) in FP32
+    with a = fl32(g/Z_i) when j in K_i else 0 and b = fl32(g/Z_j) when i in
+    K_j else 0; r_i = row sums of q; ns the FP64 NS_ij."""
+    n = len(u_rp) - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(u_rp).astype(np.int64))
+    d = u_dist.astype(np.int64)
+    s32 = np.float64(np.float32(sigma))
+    g64 = np.exp(-np.arange(1, k + 1, dtype=np.float64) ** 2 / (2.0 * s32 * s32))
+    g32 = g64.astype(np.float32)
+    Z = np.zeros(n, np.float32)
+    Z64 = np.zeros(n, np.float64)
+    for i in range(n):
+        dd = d[int(u_rp[i]):int(u_rp[i + 1])][own[int(u_rp[i]):int(u_rp[i + 1])]]
+        z = np.float32(0.0)
+        for c in range(1, k + 1):
+            cnt = np.float32(np.count_nonzero(dd == c))
+            z = np.float32(z + np.float32(cnt * g32[c - 1]))
+            Z64[i] += float(np.count_nonzero(dd == c)) * g64[c - 1]
+        Z[i] = z
+    j = u_col.astype(np.int64)
+    gd = g32[d - 1]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = np.where(own, gd / Z[rows], np.float32(0.0)).astype(np.float32)
+        b = np.where(back, gd / Z[j], np.float32(0.0)).astype(np.float32)
+    q = ((a + b).astype(np.float32) * np.float32(2.0 ** 30)).astype(np.float32).astype(np.uint32)
+    r = np.bincount(rows, weights=q, minlength=n).astype(np.uint64)
+    ns = (np.where(own, g64[d - 1] / np.where(Z64[rows] > 0, Z64[rows], 1.0), 0.0)
+          + np.where(back, g64[d - 1] / np.where(Z64[j] > 0, Z64[j], 1.0), 0.0)) / (2.0 * n)
+    return dict(Z=Z, q=q, r=r, ns=ns, g=g32)
+
+
 class RowBFS:
     """Single rows of GD (spot checks of graphs too large for the full matrix)."""
 

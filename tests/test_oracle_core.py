@@ -239,6 +239,66 @@ def test_similarity_perplexity_rows(orc, k, P):
         deg = np.diff(rp).astype(np.float64)
         assert np.allclose(ns, (1 / deg[rows] + 1 / deg[col.astype(np.int64)]) / (2 * n), rtol=1e-14)
 
+
+# ------------------------------------------------- per-row neighbour cap
+@pytest.mark.parametrize("k", [2, 3])
+def test_capped_matrix_without_binding_cap_is_the_matrix(orc, k):
+    n, s, d = gg.barabasi_albert(300, 2, 7)
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, k)
+    sim = orc.similarity(*gd, k, 1.0)
+    u = orc.korder_capped(rp, col, k, 10 ** 6)
+    assert all(np.array_equal(a, b) for a, b in zip(u[:3], gd)) and u[3].all() and u[4].all()
+    sc = orc.similarity_capped(*u, k, 1.0)
+    assert np.array_equal(sc["Z"].view(np.uint32), sim["Z"].view(np.uint32))
+    assert np.array_equal(sc["q"], sim["q"]) and np.array_equal(sc["r"], sim["r"])
+
+
+def test_capped_star_by_hand(orc):
+    # K_{1,5}, k = 2, cap 2: the hub keeps leaves 1, 2; every leaf keeps the
+    # hub and the smallest other leaf (1, or 2 for leaf 1)
+    rp, col = orc.canonical_graph(6, np.zeros(5, np.int64), np.arange(1, 6))
+    u_rp, u_col, u_dist, own, back = orc.korder_capped(rp, col, 2, 2)
+    rows = {i: u_col[int(u_rp[i]):int(u_rp[i + 1])].tolist() for i in range(6)}
+    assert rows == {0: [1, 2, 3, 4, 5], 1: [0, 2, 3, 4, 5], 2: [0, 1], 3: [0, 1], 4: [0, 1], 5: [0, 1]}
+    flags = {i: list(zip(own[int(u_rp[i]):int(u_rp[i + 1])].tolist(), back[int(u_rp[i]):int(u_rp[i + 1])].tolist()))
+             for i in range(6)}
+    assert flags[0] == [(True, True), (True, True), (False, True), (False, True), (False, True)]
+    assert flags[1] == [(True, True), (True, True), (False, True), (False, True), (False, True)]
+    assert flags[3] == [(True, False), (True, False)]
+    sc = orc.similarity_capped(u_rp, u_col, u_dist, own, back, 2, 1.0)
+    g1, g2 = np.float32(np.exp(-0.5)), np.float32(np.exp(-2.0))
+    assert sc["Z"][0] == np.float32(np.float32(2) * g1) and sc["Z"][3] == np.float32(g1 + g2)
+    # (0, 3): only the leaf's side keeps the pair
+    e03 = int(u_rp[0]) + 2
+    assert sc["q"][e03] == np.uint32(np.float32(np.float32(g1 / sc["Z"][3]) * np.float32(2.0 ** 30)))
+
+
+@pytest.mark.parametrize("seed,k,cap", [(0, 2, 5), (1, 3, 12), (2, 2, 1)])
+def test_capped_sets_against_all_pairs_shortest_paths(orc, seed, k, cap):
+    n, s, d = gg.erdos_renyi(120, 200, seed)
+    rp, col = orc.canonical_graph(n, s, d)
+    A = sp.csr_matrix((np.ones(len(col)), col.astype(np.int64), rp.astype(np.int64)), shape=(n, n))
+    D = csg.shortest_path(A, unweighted=True)
+    kept = set()
+    for i in range(n):
+        cand = [(D[i, j], j) for j in range(n) if j != i and D[i, j] <= k]
+        kept |= {(i, j) for _, j in sorted(cand)[:cap]}
+    want = kept | {(j, i) for i, j in kept}
+    u_rp, u_col, u_dist, own, back = orc.korder_capped(rp, col, k, cap)
+    rows = np.repeat(np.arange(n), np.diff(u_rp).astype(np.int64))
+    got = list(zip(rows.tolist(), u_col.tolist()))
+    assert set(got) == want and len(got) == len(want)
+    assert [p in kept for p in got] == own.tolist()
+    assert [(j, i) in kept for i, j in got] == back.tolist()
+    assert np.array_equal(u_dist, D[rows, u_col.astype(np.int64)].astype(np.uint8))
+    sc = orc.similarity_capped(u_rp, u_col, u_dist, own, back, k, 1.0)
+    key = rows * n + u_col.astype(np.int64)
+    tkey = u_col.astype(np.int64) * n + rows
+    order = np.argsort(key)
+    assert np.array_equal(sc["q"], sc["q"][order][np.searchsorted(key[order], tkey)])   # symmetric
+    assert math.isclose(sc["ns"].sum(), 1.0 - np.mean(np.diff(rp) == 0), rel_tol=1e-12)
+
 def test_node_weight_shift(orc):
     r = np.array([0, 5, 2 ** 40 + 7, 2 ** 33], np.uint64)
     r32, s = orc.node_weights_u32(r)
