@@ -267,6 +267,40 @@ def oracle_sample(wl, budget_s):
     return samples / wall, samples, f"{sample}; {epochs} level-0 epochs ({samples} samples) of the FP64 oracle, sequential mode"
 
 
+def oracle_parallel_sample(wl, budget_s):
+    """The paper's multi-threaded optimisation (Sec. 4.3) on the same bounded
+    sample as oracle_sample: the oracle's sequential loop with each epoch's
+    samples shared over every host core without locks.  Returns None when the
+    toolchain has no OpenMP."""
+    import graphgen as gg
+    import oracle as orc
+    if orc.build_omp() is None:
+        return None
+    threads = os.cpu_count() or 1
+    if wl["graph"] == "dcsbm1m":
+        n, s, d = gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2)
+    elif wl["graph"] == "batch256":
+        n, s, d = gg.barabasi_albert(20_000, 2, 3)
+    elif wl["graph"] == "ba100k":
+        n, s, d = gg.barabasi_albert(100_000, 3, 1)
+    else:
+        n, s, d = gg.grid(32, 32)
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, wl["k"])
+    tab, _ = orc.sampling_tables(*gd, wl["k"])
+    p = orc.Params(k=wl["k"], M=wl["M"], epochs=10 ** 6, b=wl["b"], mode=1, seed=0)
+    Y = orc.init_positions(p, 0, n) * 1e4
+    w0 = time.perf_counter()
+    epochs = 0
+    while time.perf_counter() - w0 < budget_s:
+        orc.layout_level_omp(tab, Y, 0, None, p, 0.1, threads, epochs, epochs + 1)
+        epochs += 1
+    wall = time.perf_counter() - w0
+    samples = epochs * n
+    return samples / wall, threads, (f"the cpu_baseline sample; {epochs} level-0 epochs ({samples} samples) of the "
+                                     f"FP64 oracle's loop on {threads} lock-free OpenMP threads")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -309,6 +343,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for cpu_baseline; also caps each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-parallel", action="store_true",
+                    help="also time the oracle's loop on every host core without locks (the paper's "
+                         "multi-threaded mode), on the same bounded sample")
     ap.add_argument("--k", type=int, default=None, help="override the distance-matrix order (profiling cases)")
     ap.add_argument("--single-level", action="store_true", help="lay out G^0 only (profiling cases)")
     ap.add_argument("--once", action="store_true", help="run exactly one step and exit (for ncu captures)")
@@ -477,6 +514,12 @@ def main():
     if not args.no_cpu_baseline:
         v, ns, sample = oracle_sample(wl, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+    if args.cpu_parallel:
+        par = oracle_parallel_sample(wl, args.cpu_budget)
+        if par is not None:
+            line["cpu_parallel_baseline"] = {"value": par[0], "unit": "updates/s", "cores": par[1],
+                                             "kind": "oracle, lock-free OpenMP threads (Sec. 4.3)",
+                                             "sample": par[2]}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

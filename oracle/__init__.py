@@ -55,6 +55,45 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_SRC_OMP = os.path.join(_HERE, "drg_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "_drg_oracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False):
+    """Compile the optional multi-threaded baseline (gcc -fopenmp); returns
+    its path, or None when the toolchain has no OpenMP."""
+    newest = max(os.path.getmtime(_SRC_OMP), os.path.getmtime(_SRC))
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < newest:
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        r = subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                            "-fno-fast-math", "-Wall", "-o", tmp, _SRC_OMP, "-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def lib_omp():
+    """The multi-threaded baseline library (raises when it cannot be built)."""
+    global _lib_omp
+    if _lib_omp is not None:
+        return _lib_omp
+    path = build_omp()
+    if path is None:
+        raise RuntimeError("the OpenMP baseline needs gcc with OpenMP")
+    L = C.CDLL(path)
+    L.orc_layout_level_omp.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32,
+                                       C.c_uint64, U32P, U32P, U32P, U32P,
+                                       C.c_uint32, U32P, U32P,
+                                       C.c_uint32, C.c_void_p, F64P,
+                                       C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_int]
+    L.orc_omp_max_threads.restype = C.c_int
+    _lib_omp = L
+    return L
+
+
 def lib():
     global _lib
     if _lib is not None:
@@ -441,6 +480,21 @@ def layout_level(tab: Tables, Y, level, anc, p: Params, gamma, t_begin=0, t_end=
                                 tab.e_thresh, tab.e_alias, tab.n0, tab.v_thresh, tab.v_alias,
                                 Y.shape[0], _ptr(anc_arr), Y.reshape(-1),
                                 p.epochs, t_begin, t_end, p.M, gamma, p.b, p.lr0, p.clip, p.mode, p.substeps)
+    assert rc == 0
+    return Y
+
+
+def layout_level_omp(tab: Tables, Y, level, anc, p: Params, gamma, threads, t_begin=0, t_end=None):
+    """Sec. 4.3's multi-threaded optimisation: the sequential loop with each
+    epoch's samples shared over `threads` lock-free threads (a CPU
+    performance baseline; one thread is the sequential loop exactly)."""
+    Y = np.ascontiguousarray(Y, np.float64)
+    t_end = p.epochs if t_end is None else t_end
+    anc_arr = None if anc is None else np.ascontiguousarray(anc, np.uint32)
+    rc = lib_omp().orc_layout_level_omp(p.seed, p.gid, level, len(tab.e_thresh), tab.e_src, tab.e_dst,
+                                        tab.e_thresh, tab.e_alias, tab.n0, tab.v_thresh, tab.v_alias,
+                                        Y.shape[0], _ptr(anc_arr), Y.reshape(-1),
+                                        p.epochs, t_begin, t_end, p.M, gamma, p.b, p.lr0, p.clip, int(threads))
     assert rc == 0
     return Y
 

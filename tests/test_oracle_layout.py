@@ -517,3 +517,39 @@ def test_grid17_quality_near_paper(orc):
         # loose sanity range: the paper's RNG, sigma and learning rate are unknown
         assert np_ > paper[k][0] - 0.12, (k, np_, paper[k])
         assert st < paper[k][1] * 1.6, (k, st, paper[k])
+
+
+# ------------------------------------------ multi-threaded baseline (Sec. 4.3)
+def test_openmp_loop_with_one_thread_is_the_sequential_loop(orc):
+    if orc.build_omp() is None:
+        pytest.skip("no OpenMP in this toolchain")
+    for g, k, level in ((gg.grid(20, 20), 2, 0), (gg.barabasi_albert(1500, 2, 6), 2, 2)):
+        n, s, d = g
+        rp, col = orc.canonical_graph(n, s, d)
+        gd = orc.korder(rp, col, k)
+        tab, _ = orc.sampling_tables(*gd, k)
+        p = orc.Params(k=k, M=5, epochs=30, b=1.0, mode=1, stop_nodes=200, seed=3)
+        levels = orc.hierarchy(rp, col, p)
+        lv = levels[min(level, len(levels) - 1)]
+        Y0 = np.random.default_rng(1).normal(size=(lv.n, 2)) * 3
+        seq = orc.layout_level(tab, Y0.copy(), level, lv.anc, p, 0.1)
+        one = orc.layout_level_omp(tab, Y0.copy(), level, lv.anc, p, 0.1, 1)
+        assert np.array_equal(seq, one)
+
+
+def test_openmp_loop_keeps_quality(orc):
+    # lock-free threads on a 32x32 grid: mean NP over three seeds within 15 %
+    # of the sequential loop's (both vary by about +-.05 across seeds)
+    if orc.build_omp() is None:
+        pytest.skip("no OpenMP in this toolchain")
+    n, s, d = gg.grid(32, 32)
+    rp, col = orc.canonical_graph(n, s, d)
+    gd = orc.korder(rp, col, 2)
+    tab, _ = orc.sampling_tables(*gd, 2)
+    nps = {1: [], 4: []}
+    for seed in (0, 1, 2):
+        p = orc.Params(k=2, M=5, epochs=200, b=3.0, mode=1, seed=seed)
+        Y0 = orc.init_positions(p, 0, n) * 1e4
+        nps[1].append(orc.neighbourhood_preservation(rp, col, orc.layout_level(tab, Y0.copy(), 0, None, p, 0.1), 2))
+        nps[4].append(orc.neighbourhood_preservation(rp, col, orc.layout_level_omp(tab, Y0.copy(), 0, None, p, 0.1, 4), 2))
+    assert np.mean(nps[4]) >= 0.85 * np.mean(nps[1]), nps
