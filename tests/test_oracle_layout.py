@@ -1,7 +1,9 @@
 """Pins of the oracle's layout arithmetic, hierarchy and metrics (CPU only).
 
 The gradient is pinned by finite differences of the sampled objective
-(Eq. 11) and by its equilibrium distance; the epoch loop by exact symmetry
+(Eq. 11) with respect to the source, the positive target and every negative,
+and by its equilibrium distance; one whole epoch's update by finite
+differences of the sum of its drawn terms; the epoch loop by exact symmetry
 and reduction identities and by a brute-force expectation; the hierarchy by
 scipy's sparse products and matching invariants; the metrics by closed-form
 layouts and a brute-force kNN; whole runs by a loose range around the paper's
@@ -48,6 +50,16 @@ def test_pair_forces_are_objective_gradient(orc, b):
             numj[c] = (orc.sample_objective(yi, yj + e, yneg, gamma, b)
                        - orc.sample_objective(yi, yj - e, yneg, gamma, b)) / (2 * h)
         assert np.allclose(-np.array(orc.pair_force(*(yi - yj), False, gamma, b, 1e300)), numj, rtol=1e-6, atol=1e-8)
+        # and with respect to each negative it is minus that negative's repulsion
+        for m in range(M):
+            numm = np.zeros(2)
+            for c in range(2):
+                e = np.zeros((M, 2))
+                e[m, c] = h
+                numm[c] = (orc.sample_objective(yi, yj, yneg + e, gamma, b)
+                           - orc.sample_objective(yi, yj, yneg - e, gamma, b)) / (2 * h)
+            rep = np.array(orc.pair_force(*(yi - yneg[m]), True, gamma, b, 1e300))
+            assert np.allclose(-rep, numm, rtol=1e-6, atol=1e-8)
 
 
 @pytest.mark.parametrize("b,M,gamma", [(1.0, 5, 0.1), (3.0, 5, 0.1), (2.0, 3, 0.2)])
@@ -159,6 +171,48 @@ def test_epoch_gradient_matches_brute_force_expectation(orc):
             EG[c] -= Pe[e] * M * Pv[c] * fr
     EG *= n
     assert np.all(np.abs(mean - EG) <= 5 * sd + 1e-9), (mean, EG, sd)
+
+
+@pytest.mark.parametrize("b,level_map", [(1.0, False), (3.0, False), (2.0, True)])
+def test_epoch_update_is_gradient_of_drawn_terms(orc, b, level_map):
+    # One synchronous epoch in a single run (every sample reads the start
+    # positions) with lr = 1 and no clip moves the layout by exactly the
+    # gradient, over every position, of the sum of the epoch's sampled terms
+    # of Eq. 11 (negatives that hit the source or target skipped, R8).  Every
+    # role is pinned by finite differences: the source (attraction plus
+    # repulsions), the positive target and each negative -- a wrong sign or a
+    # dropped update on any of them fails here.  With level_map the drawn
+    # G^0 nodes are mapped to a coarse level first (Sec. 3.2.3 forwarding).
+    n, rp, col, gd, tab, sim = _setup(orc, gg.erdos_renyi(11, 20, 5), 2)
+    gamma, M, t = 0.3, 4, 3
+    if level_map:
+        anc = np.array([0, 0, 1, 2, 2, 3, 4, 5, 5, 6, 7], np.uint32)[:n]
+        nl = int(anc.max()) + 1
+    else:
+        anc, nl = None, n
+    Y0 = np.random.default_rng(int(b * 7)).normal(size=(nl, 2)) * 1.3
+    p = orc.Params(M=M, epochs=10, b=b, lr0=1.0, mode=0, substeps=1, clip=1e300)
+    lr = 1.0 - t / p.epochs
+    G = (orc.layout_level(tab, Y0.copy(), 1, anc, p, gamma, t_begin=t, t_end=t + 1) - Y0) / lr
+    terms = []
+    for s in range(nl):  # an epoch at level l draws n_l samples (R5)
+        i, j, neg = orc.sample_draws(tab, p.seed, p.gid, 1, t, s, M)
+        a, c = (i, j) if anc is None else (int(anc[i]), int(anc[j]))
+        cm = [int(x) if anc is None else int(anc[x]) for x in neg]
+        terms.append((a, c, [x for x in cm if x != a and x != c]))
+
+    def objective(Y):
+        return sum(orc.sample_objective(Y[a], Y[c], Y[cm].reshape(-1, 2), gamma, b) for a, c, cm in terms)
+
+    h = 1e-6
+    num = np.zeros_like(Y0)
+    for v in range(nl):
+        for x in range(2):
+            e = np.zeros_like(Y0)
+            e[v, x] = h
+            num[v, x] = (objective(Y0 + e) - objective(Y0 - e)) / (2 * h)
+    assert np.any(np.abs(num) > 1e-3)
+    assert np.allclose(G, num, rtol=1e-5, atol=1e-6), np.max(np.abs(G - num))
 
 
 def test_coarse_level_maps_through_ancestors(orc):
