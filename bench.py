@@ -45,6 +45,10 @@ WORKLOADS = {
                      desc="256 graphs (grids b=3, random binary trees and Barabasi-Albert m=2 b=2), node counts "
                           "log-uniform in [1k, 50k], seed 3; multilevel, k=2, M=5, 300 epochs, one batched launch "
                           "per sub-step across graphs"),
+    "rmat22": dict(graph="rmat22", k=1, M=5, epochs=300, b=1.0, stop_nodes=1000,
+                   desc="R-MAT scale 22 (4,194,304 nodes), edge factor 8, a,b,c,d = .57,.19,.19,.05, duplicates and "
+                        "self-loops removed, seed 4; multilevel HEM to <1000 nodes, k=1 (k=2 exceeds 2^32 entries), "
+                        "M=5, 300 epochs per level, b=1"),
 }
 
 
@@ -85,32 +89,98 @@ class Job:
     def step(self):
         self._run(self.dev, self.pos)
 
-    def e2e(self):
+    def pin_host(self):
+        """Pinned host copies of the edges and positions (made once, outside any timed region)."""
         np, torch = self.np, self.torch
         if self.host is None:
             self.host = ([(g[0], torch.from_numpy(g[1].view(np.int32)).pin_memory(),
                            torch.from_numpy(g[2].view(np.int32)).pin_memory()) for g in self.graphs],
                          [torch.zeros(2 * g[0], dtype=torch.float32).pin_memory() for g in self.graphs])
+
+    def e2e(self):
+        self.pin_host()
         self._run(*self.host)
         return self.host[1]
 
-ALGO_BYTES_NOTE = ("per sample: edge record (16 B packed below 2^24 nodes, else 20 B read of the 32-B record) + "
-                   "M negative records (node table 8 B on level 0; the Hogwild kernel's level node table 16 B on "
-                   "coarse levels, the sub-step kernel's node table 8 B + ancestor 4 B) + (2+M) position gathers "
-                   "(8 B; 4 B for negatives with half copies) + (2+M) 8-B atomic adds; + 2 ancestor reads of 4 B "
-                   "for the endpoints on coarse levels")
+# Per-sample accesses of the level kernels, by kind (the probe that bounds
+# each): table records and position gathers of 4 or 8 bytes cost one L2
+# request like an 8-byte load; 16-byte records like a 16-byte load; every
+# touched node one 8-byte vector atomic add; the edge record is the one
+# access that misses L2 (its table is far larger than L2).
+def sample_accesses(kernel, M, precision, coarse):
+    """(load8, load16, red8, hbm16, l2_bytes) per sample."""
+    hog = kernel in ("k_hogwild", "k_hogwild_batch")
+    load8 = 2 + M  # position gathers (negatives from the half copy when precision > 0: 4 bytes, one request)
+    load16 = 0
+    l2_bytes = 2 * 8 + M * (4 if precision else 8)
+    if coarse and hog:
+        load16 += M        # level node records {thresh, anc(own), anc(alias)}
+        l2_bytes += 16 * M
+        load8 += 2         # ancestors of the two endpoints
+        l2_bytes += 8
+    else:
+        load8 += M         # node records {thresh, alias}
+        l2_bytes += 8 * M
+        if coarse:
+            load8 += 2 + M  # ancestors of every drawn node
+            l2_bytes += 4 * (2 + M)
+    red8 = 2 + M
+    l2_bytes += 8 * red8
+    return load8, load16, red8, 1, l2_bytes
 
 
-def algo_bytes_per_sample(kernel, M, precision, coarse, packed=True):
-    edge = 16 if packed else 20
-    neg_rec = 16 if (coarse and kernel in ("k_hogwild", "k_hogwild_batch")) else 8
-    if coarse and kernel not in ("k_hogwild", "k_hogwild_batch"):
-        neg_rec += 4  # ancestor of each negative
-    neg_pos = 4 if precision else 8
-    b = edge + M * neg_rec + 2 * 8 + M * neg_pos + (2 + M) * 8
-    if coarse:
-        b += 2 * 4
-    return b
+PROBE_L2_BYTES = 32 << 20     # inside L2 (about a quarter of it), like the level kernels' working set
+PROBE_HBM_BYTES = 8 << 30     # far larger than L2, like the edge table
+
+
+def measure_probes(drg, ctx):
+    """Random-access ceilings of this GPU (accesses/s), each the best of three
+    launches after a warm-up: L2-resident 8-byte loads, 16-byte loads and
+    8-byte atomic adds; 16-byte loads over a buffer far larger than L2 (plain
+    and evict-first); and the streaming copy (GB/s, read + written)."""
+    out = {}
+    for name, kind, size, count in (("l2_load8", drg.PROBE_LOAD8, PROBE_L2_BYTES, 400_000_000),
+                                    ("l2_load16", drg.PROBE_LOAD16, PROBE_L2_BYTES, 400_000_000),
+                                    ("l2_red8", drg.PROBE_RED8, PROBE_L2_BYTES, 400_000_000),
+                                    ("hbm_load16", drg.PROBE_LOAD16, PROBE_HBM_BYTES, 40_000_000),
+                                    ("hbm_load16_evict_first", drg.PROBE_LOAD16_EVICT_FIRST, PROBE_HBM_BYTES,
+                                     40_000_000),
+                                    ("copy", drg.PROBE_COPY, PROBE_HBM_BYTES, 1)):
+        best = 0.0
+        for rep in range(4):
+            ms, done = drg.probe_memory(ctx, kind, size, count)
+            if rep:
+                rate = (done * 32 / ms / 1e6) if kind == drg.PROBE_COPY else (done / (ms / 1e3))
+                best = max(best, rate)
+        out[name] = best
+    out["unit"] = "accesses/s (copy: GB/s read + written)"
+    out["buffers"] = {"l2": PROBE_L2_BYTES, "hbm": PROBE_HBM_BYTES}
+    return out
+
+
+def roofline_l2_hbm(kernel, M, precision, level_samples, kernel_ms, probes, hbm_copy_peak):
+    """Both ceilings of a level-kernel run.  level_samples: [(samples, coarse)].
+    L2: the time the run's L2 accesses take at the probes' rates, against the
+    kernel's time; HBM: the edge records, one random 16-byte read per sample,
+    against the random-read probe and against the copy peak."""
+    t_l2 = 0.0
+    l2_bytes = 0.0
+    samples = 0
+    for cnt, coarse in level_samples:
+        l8, l16, r8, _, b = sample_accesses(kernel, M, precision, coarse)
+        t_l2 += cnt * (l8 / probes["l2_load8"] + l16 / probes["l2_load16"] + r8 / probes["l2_red8"])
+        l2_bytes += cnt * b
+        samples += cnt
+    sec = kernel_ms / 1e3
+    l2 = {"achieved": l2_bytes / sec / 1e9, "peak": l2_bytes / t_l2 / 1e9, "unit": "GB/s",
+          "frac": t_l2 / sec, "algorithmic_bytes_per_sample": l2_bytes / max(samples, 1),
+          "peak_kind": "measured: random-access probes (drg_probe_memory) of this run, weighted by the "
+                       "kernel's per-sample mix of 8-byte loads, 16-byte loads and 8-byte atomic adds"}
+    hbm_ach = samples * 16 / sec / 1e9
+    hbm = {"achieved": hbm_ach, "unit": "GB/s", "bytes_per_sample": 16,
+           "peak_random16": probes["hbm_load16"] * 16 / 1e9, "frac_random16": samples / probes["hbm_load16"] / sec,
+           "peak_copy": hbm_copy_peak, "frac_copy": hbm_ach / hbm_copy_peak}
+    return l2, hbm
 
 
 def max_over_ranks(x, dist, device):
@@ -233,28 +303,66 @@ def make_params(drg, wl, args, gid):
 
 
 # ------------------------------------------------------------------ CPU oracle legs
-def oracle_sample(wl, budget_s):
-    """The oracle's layout loop on a bounded sample of the workload: the same
-    generator and parameters at a node count the oracle handles, level-0
-    epochs in sequential mode, until about budget_s seconds of CPU time."""
+def cpu_sample_graph(wl):
+    """The bounded sample of a workload that the oracle times: the same
+    generator family and parameters at a node count the oracle handles."""
     import graphgen as gg
+    g = wl["graph"]
+    if g == "dcsbm1m":
+        return gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2), "DC-SBM 20,000 nodes (the 1M workload's generator parameters)"
+    if g == "batch256":
+        return gg.barabasi_albert(20_000, 2, 3), "one Barabasi-Albert 20,000-node m=2 member of the batch family"
+    if g == "ba100k":
+        return gg.barabasi_albert(20_000, 3, 1), "Barabasi-Albert 20,000 nodes m=3 (the workload's generator)"
+    if g == "rmat22":
+        return gg.rmat(14, 8, 0.57, 0.19, 0.19, 4), "R-MAT scale 14 (the workload's generator parameters)"
+    return gg.grid(32, 32), "32x32 grid (the workload graph)"
+
+
+def _oracle_params(wl, epochs, mode):
     import oracle as orc
-    if wl["graph"] == "dcsbm1m":
-        n, s, d = gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2)
-        sample = "DC-SBM 20,000 nodes (same generator parameters as the 1M workload), k=2"
-    elif wl["graph"] == "batch256":
-        n, s, d = gg.barabasi_albert(20_000, 2, 3)
-        sample = "one Barabasi-Albert 20,000-node m=2 member of the batch family, k=2"
-    elif wl["graph"] == "ba100k":
-        n, s, d = gg.barabasi_albert(100_000, 3, 1)
-        sample = "Barabasi-Albert 100,000 nodes m=3 (the workload graph), k=3"
-    else:
-        n, s, d = gg.grid(32, 32)
-        sample = "32x32 grid (the workload graph), k=3"
+    return orc.Params(k=wl["k"], M=wl["M"], epochs=epochs, b=wl["b"], mode=mode, seed=0, stop_nodes=wl["stop_nodes"],
+                      multilevel=bool(wl.get("multilevel", 1)))
+
+
+def oracle_whole_path(wl, budget_s):
+    """The oracle's whole path (canonical graph, distance matrix, tables,
+    hierarchy, every level's epochs in sequential mode, refinement) on the
+    workload's bounded sample, single-threaded, with the workload's epochs
+    per level scaled down when a calibration run says the full count would
+    exceed budget_s.  Returns (updates/s, samples, description)."""
+    import oracle as orc
+    (n, s, d), desc = cpu_sample_graph(wl)
+    E = wl["epochs"]
+    cal = []
+    for e in (2, 12):  # the fixed part (tables, hierarchy) and the cost per epoch
+        t0 = time.perf_counter()
+        _, st = orc.run(n, s, d, _oracle_params(wl, e, 1), return_state=True)
+        cal.append(time.perf_counter() - t0)
+    sizes = [lv.n for lv in st["levels"]]
+    per_epoch = max((cal[1] - cal[0]) / 10.0, 1e-6)
+    fixed = max(cal[0] - 2 * per_epoch, 0.0)
+    if fixed + per_epoch * E > budget_s:
+        E = max(10, int((budget_s - fixed) / per_epoch))
+    p = _oracle_params(wl, E, 1)
+    t0 = time.perf_counter()
+    orc.run(n, s, d, p, return_state=False)
+    wall = time.perf_counter() - t0
+    samples = sum(sizes) * E
+    return samples / wall, samples, (f"{desc}, k={wl['k']}, M={wl['M']}, b={wl['b']:g}; the FP64 oracle's whole path "
+                                     f"(tables, hierarchy of {len(sizes)} levels, {E} epochs per level in "
+                                     f"sequential mode, refinement) on one core: {samples} samples in {wall:.1f} s")
+
+
+def oracle_sample(wl, budget_s):
+    """The oracle's layout loop on the workload's bounded sample: level-0
+    epochs in sequential mode, until about budget_s seconds of CPU time."""
+    import oracle as orc
+    (n, s, d), desc = cpu_sample_graph(wl)
     rp, col = orc.canonical_graph(n, s, d)
     gd = orc.korder(rp, col, wl["k"])
     tab, _ = orc.sampling_tables(*gd, wl["k"])
-    p = orc.Params(k=wl["k"], M=wl["M"], epochs=10 ** 6, b=wl["b"], mode=1, seed=0)
+    p = _oracle_params(wl, 10 ** 6, 1)
     Y = orc.init_positions(p, 0, n) * 1e4
     t0 = time.process_time()
     w0 = time.perf_counter()
@@ -264,41 +372,38 @@ def oracle_sample(wl, budget_s):
         epochs += 1
     wall = time.perf_counter() - w0
     samples = epochs * n
-    return samples / wall, samples, f"{sample}; {epochs} level-0 epochs ({samples} samples) of the FP64 oracle, sequential mode"
+    return samples / wall, samples, (f"{desc}, k={wl['k']}; {epochs} level-0 epochs ({samples} samples) of the FP64 "
+                                     f"oracle, sequential mode, one core")
 
 
-def oracle_parallel_sample(wl, budget_s):
-    """The paper's multi-threaded optimisation (Sec. 4.3) on the same bounded
-    sample as oracle_sample: the oracle's sequential loop with each epoch's
-    samples shared over every host core without locks.  Returns None when the
-    toolchain has no OpenMP."""
-    import graphgen as gg
+def oracle_parallel_sample(wl, budget_s, reps=5):
+    """The paper's multi-threaded optimisation (Sec. 4.3) on the workload's
+    bounded sample: the oracle's sequential loop with each epoch's samples
+    shared over every host core without locks; the median of `reps` timed
+    runs of budget_s / reps seconds each.  Returns None when the toolchain
+    has no OpenMP."""
     import oracle as orc
     if orc.build_omp() is None:
         return None
     threads = os.cpu_count() or 1
-    if wl["graph"] == "dcsbm1m":
-        n, s, d = gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2)
-    elif wl["graph"] == "batch256":
-        n, s, d = gg.barabasi_albert(20_000, 2, 3)
-    elif wl["graph"] == "ba100k":
-        n, s, d = gg.barabasi_albert(100_000, 3, 1)
-    else:
-        n, s, d = gg.grid(32, 32)
+    (n, s, d), desc = cpu_sample_graph(wl)
     rp, col = orc.canonical_graph(n, s, d)
     gd = orc.korder(rp, col, wl["k"])
     tab, _ = orc.sampling_tables(*gd, wl["k"])
-    p = orc.Params(k=wl["k"], M=wl["M"], epochs=10 ** 6, b=wl["b"], mode=1, seed=0)
+    p = _oracle_params(wl, 10 ** 6, 1)
     Y = orc.init_positions(p, 0, n) * 1e4
-    w0 = time.perf_counter()
+    rates = []
     epochs = 0
-    while time.perf_counter() - w0 < budget_s:
-        orc.layout_level_omp(tab, Y, 0, None, p, 0.1, threads, epochs, epochs + 1)
-        epochs += 1
-    wall = time.perf_counter() - w0
-    samples = epochs * n
-    return samples / wall, threads, (f"the cpu_baseline sample; {epochs} level-0 epochs ({samples} samples) of the "
-                                     f"FP64 oracle's loop on {threads} lock-free OpenMP threads")
+    for _ in range(reps):
+        w0 = time.perf_counter()
+        e0 = epochs
+        while time.perf_counter() - w0 < budget_s / reps:
+            orc.layout_level_omp(tab, Y, 0, None, p, 0.1, threads, epochs, epochs + 1)
+            epochs += 1
+        rates.append((epochs - e0) * n / (time.perf_counter() - w0))
+    return statistics.median(rates), threads, (f"{desc}, k={wl['k']}; level-0 epochs of the FP64 oracle's loop on "
+                                               f"{threads} lock-free OpenMP threads (all host cores), median of "
+                                               f"{reps} runs of {budget_s / reps:.1f} s")
 
 
 def run_reference(args):
@@ -306,16 +411,16 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    per_step = max(0.5, min(args.cpu_budget, 60.0 / max(args.steps + args.warmup, 1)))
+    # each step: the oracle's whole path on the workload's bounded sample,
+    # sized so that warm-up and timed steps take about two minutes in all
+    per_step = max(2.0, min(args.cpu_budget, 120.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
-        oracle_sample(wl, per_step / 4)
-    vals = []
+        oracle_sample(wl, 0.5)
     t0 = time.perf_counter()
     sample = ""
     total_samples = 0
     for _ in range(args.steps):
-        v, ns, sample = oracle_sample(wl, per_step)
-        vals.append(v)
+        v, ns, sample = oracle_whole_path(wl, per_step)
         total_samples += ns
     wall = time.perf_counter() - t0
     value = total_samples / wall
@@ -343,9 +448,6 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for cpu_baseline; also caps each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-parallel", action="store_true",
-                    help="also time the oracle's loop on every host core without locks (the paper's "
-                         "multi-threaded mode), on the same bounded sample")
     ap.add_argument("--k", type=int, default=None, help="override the distance-matrix order (profiling cases)")
     ap.add_argument("--single-level", action="store_true", help="lay out G^0 only (profiling cases)")
     ap.add_argument("--once", action="store_true", help="run exactly one step and exit (for ncu captures)")
@@ -394,6 +496,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = drg.Context(local, stream.cuda_stream)
     p = make_params(drg, wl, args, gid=rank)
+    probes = measure_probes(drg, ctx)
     job = Job(drg, ctx, wl, p, np, torch)
     n, m = job.n, job.m
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 1 GiB > L2
@@ -449,10 +552,14 @@ def main():
     samples_per_step = ep_samples
     value = whole_job_rate(samples_per_step, world, ms / 1000.0)
 
-    # end to end through the public API from pinned host buffers
+    # end to end through the public API from pinned host buffers: the buffers
+    # are pinned and the host path warmed up once before the timed calls
+    job.pin_host()
+    job.e2e()
+    torch.cuda.synchronize()
     e2e_times = []
     hpos = None
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -466,19 +573,31 @@ def main():
     if rank != 0:
         return
     hbm, peak_kind = peaks()
+    if peak_kind == "fallback" and probes.get("copy"):
+        hbm, peak_kind = probes["copy"], "measured by this run's streaming-copy probe (drg_probe_memory)"
     n0 = n
     s0 = n0 * wl["epochs"]
     coarse = max(ep_samples - s0, 0)
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
     kname = epoch_kernel(wl["graph"], args.mode, args.precision)
-    packed = n < (1 << 24)
-    bytes_total = (s0 * algo_bytes_per_sample(kname, wl["M"], prec, False, packed)
-                   + coarse * algo_bytes_per_sample(kname, wl["M"], prec, True, packed))
-    achieved = bytes_total / (ep_ms / 1000.0) / 1e9
     tps = None if (args.level_tables or args.perplexity > 0) else ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
                                          "mode": args.mode, "precision": args.precision,
                                          "multilevel": bool(wl.get("multilevel", 1))})
     avg_launch_samples = ep_samples / max(ep_launches, 1)
+    l2, hbm_roof = roofline_l2_hbm(kname, wl["M"], prec, [(s0, False), (coarse, True)], ep_ms, probes, hbm)
+    if l2["frac"] >= hbm_roof["frac_random16"]:
+        top = {"bound": "l2", "achieved": l2["achieved"], "peak": l2["peak"], "frac": l2["frac"],
+               "peak_kind": l2["peak_kind"]}
+    else:
+        top = {"bound": "hbm", "achieved": hbm_roof["achieved"], "peak": hbm_roof["peak_random16"],
+               "frac": hbm_roof["frac_random16"],
+               "peak_kind": "measured: random 16-byte-read probe over 8 GiB (drg_probe_memory)"}
+    roofline = {"kernel": kname, **top, "unit": "GB/s",
+                "traffic": None if tps is None else tps * avg_launch_samples,
+                "traffic_note": "DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture "
+                                "of this configuration and kernel source)",
+                "l2": l2, "hbm": {**hbm_roof, "peak_copy_kind": peak_kind}, "probes": probes,
+                "avg_launch_ms": ep_ms / max(ep_launches, 1), "launches": ep_launches}
     line = {
         "metric": "edge-sample gradient updates/s",
         "value": value,
@@ -502,19 +621,15 @@ def main():
         "phases_note": "CUDA-event timers of one profiled step, in which builds that the timed steps run "
                        "concurrently (hierarchy beside the distance matrix; a batch's graphs) run one after another",
         "gpu_launches": launches,
-        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": None if tps is None else tps * avg_launch_samples,
-                     "algorithmic_bytes_note": ALGO_BYTES_NOTE,
-                     "avg_launch_ms": ep_ms / max(ep_launches, 1), "launches": ep_launches},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 2 * m * 4,
                 "d2h_bytes_per_step": 2 * n * 4, "seconds_per_step": e2e_s},
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        v, ns, sample = oracle_sample(wl, args.cpu_budget)
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
-    if args.cpu_parallel:
+        v, ns, sample = oracle_whole_path(wl, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample,
+                                "nproc": os.cpu_count()}
         par = oracle_parallel_sample(wl, args.cpu_budget)
         if par is not None:
             line["cpu_parallel_baseline"] = {"value": par[0], "unit": "updates/s", "cores": par[1],

@@ -290,12 +290,16 @@ drg_status drg_layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, 
  * larger levels return DRG_EUNSUPPORTED.  It runs synchronous FP32 mode only
  * (other modes or precisions: DRG_EUNSUPPORTED) with the same kernels, random
  * streams and results as drg_layout_level, launched one by one instead of as
- * a graph.  It calls no allocating routine: the first call on a device looks
- * up the array's device address (the only set-up; make that first call
- * before any stream capture), and every call clears the gradient part, which
- * keeps the previous call's contents.  All calls share the one array per
- * device, so calls that overlap on the GPU (other streams, other contexts on
- * the same device) race and corrupt each other: serialise them. */
+ * a graph.  d may be G^0's matrix or, at a coarse level, one built on that
+ * level's graph, as for drg_layout_level.  It calls no allocating routine:
+ * the first call on a device looks up the array's device address (the only
+ * set-up; make that first call before any stream capture) and keeps it with
+ * the id of the CUDA context it was read in, so a later call in another
+ * context (for instance after the primary context was reset) repeats that
+ * look-up; every call clears the gradient part, which keeps the previous
+ * call's contents.  All calls share the one array per device, so calls that
+ * overlap on the GPU (other streams, other contexts on the same device) race
+ * and corrupt each other: serialise them. */
 drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t level, float* pos,
                                     const drg_params* p, float gamma, uint32_t t_begin, uint32_t t_end);
 
@@ -385,6 +389,39 @@ drg_status drg_profile_reset(drg_ctx* ctx);
 /* Total milliseconds, number of timed launches and units of one family.
  * Synchronises. */
 drg_status drg_profile_read(drg_ctx* ctx, int which, double* ms, uint64_t* launches, uint64_t* units);
+
+/* ---------------------------------------------------------------- memory probes */
+/* Measured ceilings for the roofline of the level kernels (no counterpart in
+ * the paper, whose implementation runs on CPUs).  A sample of Sec. 3.2.2 is a
+ * handful of random accesses: one 16-byte edge record from a table far larger
+ * than L2, node records and position gathers that stay in L2, and vector
+ * atomic adds; a streaming copy does not bound such accesses.  Each probe
+ * allocates a zeroed buffer of buffer_bytes (1 MiB .. 64 GiB; DRG_ENOMEM when
+ * it does not fit the free device memory), launches blocks_per_sm (1 .. 8)
+ * blocks of 256 threads on every SM, each thread keeping 8 independent
+ * accesses in flight, and times the launch with CUDA events on the context
+ * stream:
+ *   DRG_PROBE_LOAD8    random 8-byte loads through L2 (ld.global.cg.v2.f32),
+ *                      the position gathers
+ *   DRG_PROBE_LOAD16   random 16-byte loads (ld.global.nc.v4.u32), the table
+ *                      records
+ *   DRG_PROBE_RED8     random 8-byte vector atomic adds (red of a float2),
+ *                      the position updates
+ *   DRG_PROBE_LOAD16_EVICT_FIRST  as LOAD16 with an L2 evict-first policy
+ *   DRG_PROBE_COPY     streaming copy of the buffer's first half to its second
+ *                      half (16-byte vectors; `accesses` is ignored)
+ * Random places are uniform over the buffer (a 32-bit linear congruential
+ * stream per thread, scaled to the element count).  `accesses` (1 .. 1e11) is
+ * rounded up to whole iterations; *done receives the accesses made (COPY: the
+ * 16-byte vectors copied, each read once and written once) and *ms the kernel
+ * time.  Synchronises. */
+#define DRG_PROBE_LOAD8 0
+#define DRG_PROBE_LOAD16 1
+#define DRG_PROBE_RED8 2
+#define DRG_PROBE_LOAD16_EVICT_FIRST 3
+#define DRG_PROBE_COPY 4
+drg_status drg_probe_memory(drg_ctx* ctx, int kind, uint64_t buffer_bytes, uint64_t accesses, uint32_t blocks_per_sm,
+                            double* ms, uint64_t* done);
 
 /* ---------------------------------------------------------------- inspection */
 /* The draws of samples [s_begin, s_end) of epoch t at `level`: out_i, out_j

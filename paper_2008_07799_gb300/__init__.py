@@ -38,7 +38,10 @@ EXPORTS = [
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
     "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
     "drg_build_distance_matrix_ex", "drg_dmat_calibration", "drg_crossings", "drg_min_angle",
+    "drg_probe_memory",
 ]
+
+PROBE_LOAD8, PROBE_LOAD16, PROBE_RED8, PROBE_LOAD16_EVICT_FIRST, PROBE_COPY = range(5)
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
 
@@ -129,6 +132,8 @@ def lib():
         "drg_layout_edges": (st, [VP, C.c_uint32, C.c_uint64, VP, VP, C.c_int, PP, VP, C.c_int]),
         "drg_layout_batch": (st, [VP, C.c_uint32, VP, PP, VP, VP]),
         "drg_sample_draws": (st, [VP, VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, PP, VP, VP, VP]),
+        "drg_probe_memory": (st, [VP, C.c_int, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_uint64)]),
         "drg_profile_enable": (st, [VP, C.c_int]),
         "drg_profile_reset": (st, [VP]),
         "drg_profile_read": (st, [VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
@@ -446,3 +451,12 @@ def layout_batch(ctx: Context, graphs, p: Params, positions, b=None):
 def sample_draws(ctx: Context, d: DistanceMatrix, level, t, s_begin, s_end, p: Params, out_i, out_j, out_neg):
     ctx.check(lib().drg_sample_draws(ctx.h, d.h, int(level), int(t), int(s_begin), int(s_end), C.byref(p),
                                      _ptr(out_i), _ptr(out_j), _ptr(out_neg)))
+
+
+def probe_memory(ctx: Context, kind, buffer_bytes, accesses, blocks_per_sm=6):
+    """One memory probe (PROBE_*): (milliseconds, accesses made)."""
+    ms = C.c_double()
+    done = C.c_uint64()
+    ctx.check(lib().drg_probe_memory(ctx.h, int(kind), int(buffer_bytes), int(accesses), int(blocks_per_sm),
+                                     C.byref(ms), C.byref(done)))
+    return ms.value, done.value

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdrgraph.so")
-SOURCES = ["api.cu", "prims.cu", "graph.cu", "dmat.cu", "layout.cu", "metrics.cu"]
+SOURCES = ["api.cu", "prims.cu", "graph.cu", "dmat.cu", "layout.cu", "metrics.cu", "probe.cu"]
 HEADERS = ["common.cuh", "prims.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -486,6 +486,14 @@ drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_h
     API_CATCH(ctx)
 }
 
+drg_status drg_probe_memory(drg_ctx* ctx, int kind, uint64_t buffer_bytes, uint64_t accesses, uint32_t blocks_per_sm,
+                            double* ms, uint64_t* done) {
+    if (!ctx || !ms || !done) return DRG_EINVAL;
+    API_TRY
+    drg::probe_memory(ctx, kind, buffer_bytes, accesses, blocks_per_sm, ms, done);
+    API_CATCH(ctx)
+}
+
 drg_status drg_check_epoch_barrier(drg_ctx* ctx, uint32_t blocks, uint32_t arrivals, uint32_t rounds,
                                    uint32_t timeout_ms) {
     if (!ctx) return DRG_EINVAL;

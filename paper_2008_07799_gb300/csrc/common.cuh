@@ -302,5 +302,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                   const float* b_per_graph, float* const* pos);
 void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, uint32_t s_begin, uint32_t s_end,
                   const drg_params& p, uint32_t* oi, uint32_t* oj, uint32_t* oneg);
+void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uint32_t blocks_per_sm, double* ms,
+                  uint64_t* done);
 
 }  // namespace drg

@@ -19,6 +19,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <cuda.h>
 #include <exception>
 #include <memory>
 #include <mutex>
@@ -1514,7 +1515,9 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
 // device array that every GPU loading this library holds until the process
 // exits.  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
-// (that device current) and keeps it.
+// (that device current) and keeps it together with the id of the CUDA context
+// it was read in; a call in another context (the primary context reset and
+// created again, which reloads the module) looks it up again.
 constexpr uint32_t kNoAllocMaxNodes = 1u << 20;
 constexpr uint32_t kNoAllocStateSlots = 32;  // 256 bytes reserved for the EpochState
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocStateSlots + kNoAllocMaxNodes];
@@ -1522,21 +1525,55 @@ static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocStateSlots + k
 static_assert(sizeof(EpochState) <= kNoAllocStateSlots * sizeof(float2), "epoch state does not fit its slot");
 
 
+// Unique id of the calling thread's current CUDA context (driver entry points
+// reached through the runtime, so the library needs no link to libcuda); 0
+// when the driver cannot say.
+static unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        (void)cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
 static float2* noalloc_scratch(drg_ctx* ctx) {
     static std::mutex mu;
     static void* addr[256] = {};
+    static unsigned long long ctx_id[256] = {};
     DRG_CHECK(ctx->device >= 0 && ctx->device < 256, DRG_EUNSUPPORTED, "device index beyond 255");
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[ctx->device]) {
-        int prev = 0;
-        DRG_CUDA(cudaGetDevice(&prev));
-        DRG_CUDA(cudaSetDevice(ctx->device));
+    int prev = 0;
+    DRG_CUDA(cudaGetDevice(&prev));
+    DRG_CUDA(cudaSetDevice(ctx->device));
+    const unsigned long long id = current_context_id();
+    // 0: the context cannot be identified, so the address is looked up on every call
+    if (!addr[ctx->device] || id == 0 || id != ctx_id[ctx->device]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        cudaSetDevice(prev);
-        if (e != cudaSuccess) fail(DRG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+            cudaSetDevice(prev);
+            fail(DRG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        }
         addr[ctx->device] = p;
+        ctx_id[ctx->device] = id;
     }
+    DRG_CUDA(cudaSetDevice(prev));
     return static_cast<float2*>(addr[ctx->device]);
 }
 
@@ -1546,7 +1583,10 @@ void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, ui
     DRG_CHECK(d && pos, DRG_EINVAL, "null distance matrix or positions");
     DRG_CHECK(level == 0 || (h && level < h->g.size()), DRG_EINVAL, "level out of range");
     DRG_CHECK(t_begin <= t_end && t_end <= p.epochs, DRG_EINVAL, "epoch range outside [0, epochs]");
-    DRG_CHECK(!h || h->g[0]->n == d->n, DRG_EINVAL, "hierarchy and distance matrix describe different graphs");
+    // as in layout_level: d is G^0's matrix (samples mapped to the level) or,
+    // at a coarse level, the level graph's own (no mapping)
+    const bool own = level > 0 && h && d->n != h->g[0]->n && d->n == h->g[level]->n;
+    DRG_CHECK(!h || own || h->g[0]->n == d->n, DRG_EINVAL, "hierarchy and distance matrix describe different graphs");
     DRG_CHECK(p.mode == DRG_MODE_SYNC && p.precision == DRG_PREC_FP32, DRG_EUNSUPPORTED,
               "the allocation-free run supports synchronous FP32 mode only");
     const uint32_t nl = level == 0 ? d->n : h->g[level]->n;
@@ -1558,7 +1598,7 @@ void layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, ui
     float2* Y = reinterpret_cast<float2*>(pos);
     // the array keeps the previous call's contents: the gradient must start at zero
     DRG_CUDA(cudaMemsetAsync(G, 0, sizeof(float2) * (size_t)nl, ctx->stream));
-    EpochArgs a = epoch_args(d, level == 0 ? nullptr : h->anc[level], Y, p, gamma, level);
+    EpochArgs a = epoch_args(d, (level == 0 || own) ? nullptr : h->anc[level], Y, p, gamma, level);
     a.G = G;
     a.st = st;
     const EpochKernel ek = pick_epoch(p.M, true, DRG_PREC_FP32);

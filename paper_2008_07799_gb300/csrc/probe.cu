@@ -1,0 +1,173 @@
+// Memory probes: the measured ceilings that the level kernels' roofline is
+// stated against (no counterpart in the paper, which has no GPU path).
+//
+// A sample of the layout optimisation (Sec. 3.2.2) is a handful of random
+// accesses: one 16-byte edge record from a table far larger than L2, M
+// 8- or 16-byte node records and 2 + M 8-byte position gathers that stay in
+// L2, and 2 + M 8-byte vector atomic adds.  The streaming copy that gives the
+// HBM figure says nothing about such accesses, so each probe here times one
+// access kind alone, at random places spread uniformly over a buffer of a
+// chosen size (inside L2, or far larger than L2 for the HBM-resident table),
+// with enough independent accesses in flight on every SM to saturate the
+// memory system rather than the issuing threads.
+#include "prims.cuh"
+
+namespace drg {
+
+namespace {
+
+constexpr uint32_t kProbeThreads = 256;
+constexpr uint32_t kProbeUnroll = 8;  // independent accesses per thread per iteration
+
+__device__ __forceinline__ uint32_t probe_hash(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// next index in [0, nelem): a 32-bit linear congruential step, scaled by the
+// high half of the product (the generator's strong bits)
+__device__ __forceinline__ uint64_t probe_next(uint32_t& x, uint64_t nelem) {
+    x = x * 1664525u + 1013904223u;
+    return (uint64_t)(((unsigned __int128)x * nelem) >> 32);
+}
+
+__device__ __forceinline__ float2 ld_cg_f2(const float2* p) {
+    float2 v;
+    asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_nc_u4(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_nc_u4_evict_first(const uint4* p, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+// Random accesses of one kind: iters x kProbeUnroll per thread.
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads) k_probe(void* __restrict__ buf, uint64_t nelem, uint32_t iters,
+                                                         uint32_t seed, uint32_t* __restrict__ sink) {
+    uint32_t x = probe_hash((blockIdx.x * kProbeThreads + threadIdx.x) ^ seed);
+    uint32_t acc = 0;
+    uint64_t pol = 0;
+    if constexpr (KIND == DRG_PROBE_LOAD16_EVICT_FIRST)
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    for (uint32_t it = 0; it < iters; ++it) {
+        if constexpr (KIND == DRG_PROBE_LOAD8) {
+            float2 v[kProbeUnroll];
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u) v[u] = ld_cg_f2(static_cast<const float2*>(buf) + probe_next(x, nelem));
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u) acc += __float_as_uint(v[u].x) ^ __float_as_uint(v[u].y);
+        } else if constexpr (KIND == DRG_PROBE_LOAD16 || KIND == DRG_PROBE_LOAD16_EVICT_FIRST) {
+            uint4 v[kProbeUnroll];
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u) {
+                const uint4* p = static_cast<const uint4*>(buf) + probe_next(x, nelem);
+                if constexpr (KIND == DRG_PROBE_LOAD16) v[u] = ld_nc_u4(p);
+                else v[u] = ld_nc_u4_evict_first(p, pol);
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u) acc += v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        } else {  // DRG_PROBE_RED8
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u)
+                atomicAdd(static_cast<float2*>(buf) + probe_next(x, nelem), make_float2(1.f, -1.f));
+        }
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;  // keeps the loads; the buffer is zero, so never taken
+}
+
+// Streaming copy of nvec 16-byte vectors from the first half of the buffer
+// to the second (coalesced, grid-stride).
+__global__ void __launch_bounds__(kProbeThreads) k_probe_copy(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                              uint64_t nvec) {
+    const uint64_t stride = (uint64_t)gridDim.x * kProbeThreads;
+    for (uint64_t v = blockIdx.x * (uint64_t)kProbeThreads + threadIdx.x; v < nvec; v += stride) dst[v] = src[v];
+}
+
+}  // namespace
+
+void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uint32_t blocks_per_sm, double* ms,
+                  uint64_t* done) {
+    DRG_CHECK(kind >= DRG_PROBE_LOAD8 && kind <= DRG_PROBE_COPY, DRG_EINVAL, "unknown probe kind");
+    DRG_CHECK(bytes >= (1ull << 20) && bytes <= (64ull << 30), DRG_EINVAL, "probe buffer must be 1 MiB .. 64 GiB");
+    DRG_CHECK(accesses >= 1 && accesses <= 100000000000ull, DRG_EINVAL, "probe accesses must be 1 .. 1e11");
+    DRG_CHECK(blocks_per_sm >= 1 && blocks_per_sm <= 8, DRG_EINVAL, "blocks per SM must be 1 .. 8");
+    DRG_CHECK(ms && done, DRG_EINVAL, "null output");
+    size_t free_b = 0, total_b = 0;
+    DRG_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    DRG_CHECK(bytes + (256ull << 20) < free_b, DRG_ENOMEM, "probe buffer larger than the free device memory");
+    DBuf<uint8_t> buf(ctx, bytes);
+    DBuf<uint32_t> sink(ctx, 1);
+    DRG_CUDA(cudaMemsetAsync(buf.p, 0, bytes, ctx->stream));
+    const uint32_t grid = (uint32_t)ctx->num_sms * blocks_per_sm;
+    const uint64_t threads = (uint64_t)grid * kProbeThreads;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DRG_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        fail(DRG_ECUDA, "cudaEventCreate failed");
+    }
+    try {
+        if (kind == DRG_PROBE_COPY) {
+            const uint64_t nvec = bytes / 32;  // half the buffer read, half written
+            DRG_CUDA(cudaEventRecord(e0, ctx->stream));
+            DRG_LAUNCH(ctx, k_probe_copy, grid, kProbeThreads, 0, reinterpret_cast<const uint4*>(buf.p),
+                       reinterpret_cast<uint4*>(buf.p) + nvec, nvec);
+            DRG_CUDA(cudaEventRecord(e1, ctx->stream));
+            *done = nvec;
+        } else {
+            const uint64_t per_thread = (accesses + threads - 1) / threads;
+            const uint32_t iters = (uint32_t)((per_thread + kProbeUnroll - 1) / kProbeUnroll);
+            const uint64_t elem = (kind == DRG_PROBE_LOAD8 || kind == DRG_PROBE_RED8) ? 8 : 16;
+            const uint64_t nelem = bytes / elem;
+            const uint32_t seed = (uint32_t)(accesses * 0x9E3779B97F4A7C15ull >> 32);
+            DRG_CUDA(cudaEventRecord(e0, ctx->stream));
+            switch (kind) {
+                case DRG_PROBE_LOAD8:
+                    DRG_LAUNCH(ctx, k_probe<DRG_PROBE_LOAD8>, grid, kProbeThreads, 0, (void*)buf.p, nelem, iters, seed,
+                               sink.p);
+                    break;
+                case DRG_PROBE_LOAD16:
+                    DRG_LAUNCH(ctx, k_probe<DRG_PROBE_LOAD16>, grid, kProbeThreads, 0, (void*)buf.p, nelem, iters,
+                               seed, sink.p);
+                    break;
+                case DRG_PROBE_RED8:
+                    DRG_LAUNCH(ctx, k_probe<DRG_PROBE_RED8>, grid, kProbeThreads, 0, (void*)buf.p, nelem, iters, seed,
+                               sink.p);
+                    break;
+                default:
+                    DRG_LAUNCH(ctx, k_probe<DRG_PROBE_LOAD16_EVICT_FIRST>, grid, kProbeThreads, 0, (void*)buf.p, nelem,
+                               iters, seed, sink.p);
+                    break;
+            }
+            DRG_CUDA(cudaEventRecord(e1, ctx->stream));
+            *done = threads * iters * kProbeUnroll;
+        }
+        DRG_CUDA(cudaEventSynchronize(e1));
+        float t = 0.f;
+        DRG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        *ms = t;
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+}  // namespace drg

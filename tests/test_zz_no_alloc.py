@@ -62,6 +62,28 @@ def test_two_calls_in_a_row_match_layout_level(env):
             assert torch.max(torch.abs(cur - before)).item() > 1e-3  # the epoch moved the layout
 
 
+def test_coarse_level_with_its_own_tables(env):
+    # a coarse level's own distance matrix (no ancestor map), as drg_layout_level takes it
+    drg, ctx = env
+    g = gg.barabasi_albert(3000, 3, 6)
+    G = drg.graph_from_edges(ctx, *g)
+    p = drg.Params.default(k=2, M=5, epochs=100, b=1.0, mode=0, stop_nodes=300, seed=4)
+    H = drg.build_hierarchy(ctx, G, p)
+    D1 = drg.build_distance_matrix(ctx, H.graph(1), 2)
+    n = H.sizes()[1]
+    cur = torch.from_numpy((np.random.default_rng(7).normal(size=(n, 2)) * 8).astype(np.float32).reshape(-1)).cuda()
+    for t in (10, 11):
+        ref = cur.clone()
+        drg.layout_level(ctx, D1, H, 1, ref, p, 0.1, t, t + 1)
+        st = _noalloc(drg, ctx, D1, H, 1, cur, p, 0.1, t, t + 1)
+        assert st == 0, drg.lib().drg_last_error(ctx.h)
+        torch.cuda.synchronize()
+        got = cur.cpu().numpy().astype(np.float64).reshape(n, 2)
+        want = ref.cpu().numpy().astype(np.float64).reshape(n, 2)
+        ext = float(np.max(np.ptp(want, axis=0)))
+        assert np.max(np.abs(got - want)) <= 1e-5 * ext, t
+
+
 def test_limits_are_refused(env):
     drg, ctx = env
     g = gg.grid(8, 8)
