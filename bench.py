@@ -45,6 +45,10 @@ WORKLOADS = {
                      desc="256 graphs (grids b=3, random binary trees and Barabasi-Albert m=2 b=2), node counts "
                           "log-uniform in [1k, 50k], seed 3; multilevel, k=2, M=5, 300 epochs, one batched launch "
                           "per sub-step across graphs"),
+    # a smaller graph of the 1M workload's generator (profiling captures)
+    "dcsbm100k": dict(graph="dcsbm100k", k=2, M=5, epochs=500, b=1.0, stop_nodes=1000,
+                      desc="DC-SBM 100,000 nodes with the 1M workload's generator parameters, seed 2; multilevel "
+                           "HEM to <1000 nodes, k=2, M=5, 500 epochs per level, b=1"),
     "rmat22": dict(graph="rmat22", k=1, M=5, epochs=300, b=1.0, stop_nodes=1000,
                    desc="R-MAT scale 22 (4,194,304 nodes), edge factor 8, a,b,c,d = .57,.19,.19,.05, duplicates and "
                         "self-loops removed, seed 4; multilevel HEM to <1000 nodes, k=1 (k=2 exceeds 2^32 entries), "
@@ -126,6 +130,11 @@ def sample_accesses(kernel, M, precision, coarse):
             l2_bytes += 4 * (2 + M)
     red8 = 2 + M
     l2_bytes += 8 * red8
+    if precision and hog:
+        # the copy of every node rewritten once per epoch (n_l samples): one
+        # coalesced 8-byte read and 4-byte write per sample, 12/32 of a sector
+        load8 += 12 / 32
+        l2_bytes += 12
     return load8, load16, red8, 1, l2_bytes
 
 
@@ -220,18 +229,18 @@ def kernel_hash():
 
 def epoch_kernel(graph, mode, precision):
     """The kernel that runs a level's samples: one persistent launch per level
-    for FP32 Hogwild on one graph, sub-step launches otherwise."""
-    one_launch = mode == "hogwild" and precision == "fp32"
+    in Hogwild mode, sub-step launches in synchronous mode."""
+    one_launch = mode == "hogwild"
     if graph == "batch256":
         return "k_hogwild_batch" if one_launch else "k_epoch_batch"
     return "k_hogwild" if one_launch else "k_epoch"
 
 
-def ncu_traffic_per_sample(kernel, cfg):
+def ncu_traffic_per_sample(kernel, cfg, root=ROOT):
     """DRAM bytes per sample of the level kernel from the committed ncu
     summary, or None when the kernel source has changed since that capture or
     the run's configuration is not the captured one."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    path = os.path.join(root, "profiles", f"{kernel}_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -308,7 +317,7 @@ def cpu_sample_graph(wl):
     generator family and parameters at a node count the oracle handles."""
     import graphgen as gg
     g = wl["graph"]
-    if g == "dcsbm1m":
+    if g in ("dcsbm1m", "dcsbm100k"):
         return gg.dc_sbm(20_000, 64, 2.5, 8.0, 20.0, 2), "DC-SBM 20,000 nodes (the 1M workload's generator parameters)"
     if g == "batch256":
         return gg.barabasi_albert(20_000, 2, 3), "one Barabasi-Albert 20,000-node m=2 member of the batch family"
@@ -496,7 +505,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = drg.Context(local, stream.cuda_stream)
     p = make_params(drg, wl, args, gid=rank)
-    probes = measure_probes(drg, ctx)
+    probes = None if args.once else measure_probes(drg, ctx)
     job = Job(drg, ctx, wl, p, np, torch)
     n, m = job.n, job.m
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 1 GiB > L2

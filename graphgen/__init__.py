@@ -209,6 +209,8 @@ def workload(name: str):
         return barabasi_albert(100_000, 3, 1)
     if name == "dcsbm1m":
         return dc_sbm(1_000_000, 64, 2.5, 8.0, 20.0, 2)
+    if name == "dcsbm100k":
+        return dc_sbm(100_000, 64, 2.5, 8.0, 20.0, 2)
     if name == "rmat22":
         return rmat(22, 8, 0.57, 0.19, 0.19, 4)
     raise KeyError(name)

@@ -169,13 +169,17 @@ drg_status drg_build_distance_matrix(drg_ctx* ctx, const drg_graph* g, uint32_t 
 drg_status drg_dmat_info(const drg_dmat* d, uint32_t* n, uint64_t* nnz, uint32_t* node_shift);
 /* Copy to host buffers (any may be NULL): rp[n+1], col[nnz], dist[nnz],
  * q[nnz], r[n], Z[n]; edge table e_thresh[nnz], e_alias[nnz] (entry ids);
- * node table v_thresh[n], v_alias[n].  Synchronises. */
+ * node table v_thresh[n], v_alias[n].  The sampling path keeps no alias entry
+ * ids (a record holds the alias's endpoints): e_alias is rebuilt for this
+ * call by searching row i1 of the alias's endpoints (i1, j1) for j1, in a
+ * temporary device buffer of 4 nnz bytes.  Synchronises. */
 drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint32_t* col, uint8_t* dist,
                              uint32_t* q, uint64_t* r, float* Z, uint32_t* e_thresh, uint32_t* e_alias,
                              uint32_t* v_thresh, uint32_t* v_alias);
 /* Host copies of the entries [e_begin, e_end) only (any pointer may be NULL):
  * col, dist, q, and the edge table's thresh and alias entry of those
- * buckets.  e_end <= nnz.  Synchronises. */
+ * buckets (rebuilt as for drg_dmat_download, 4 (e_end - e_begin) bytes of
+ * temporary device memory).  e_end <= nnz.  Synchronises. */
 drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_begin, uint64_t e_end, uint32_t* col,
                                    uint8_t* dist, uint32_t* q, uint32_t* e_thresh, uint32_t* e_alias);
 /* drg_build_distance_matrix with Eq. 9's sigma_i set per node by perplexity

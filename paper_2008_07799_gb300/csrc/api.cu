@@ -368,7 +368,7 @@ drg_status drg_dmat_download(drg_ctx* ctx, const drg_dmat* d, uint64_t* rp, uint
     if (q) drg::d2h(ctx, q, d->q, d->nnz);
     if (r) drg::d2h(ctx, r, d->r, d->n);
     if (Z) drg::d2h(ctx, Z, d->Z, d->n);
-    if (e_alias) drg::d2h(ctx, e_alias, d->e_alias, d->nnz);
+    if (e_alias) drg::edge_alias_ids(ctx, d, 0, d->nnz, e_alias);
     if (e_thresh) {
         DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), d->etab, d->erec_bytes, sizeof(uint32_t), d->nnz,
                                    cudaMemcpyDeviceToHost, ctx->stream));
@@ -391,7 +391,7 @@ drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_b
     if (col) drg::d2h(ctx, col, d->col + e_begin, m);
     if (dist) drg::d2h(ctx, dist, d->dist + e_begin, m);
     if (q) drg::d2h(ctx, q, d->q + e_begin, m);
-    if (e_alias) drg::d2h(ctx, e_alias, d->e_alias + e_begin, m);
+    if (e_alias) drg::edge_alias_ids(ctx, d, e_begin, e_end, e_alias);
     if (e_thresh && m)
         DRG_CUDA(cudaMemcpy2DAsync(e_thresh, sizeof(uint32_t), static_cast<const char*>(d->etab) + e_begin * d->erec_bytes,
                                    d->erec_bytes, sizeof(uint32_t), m,

@@ -110,7 +110,6 @@ struct drg_dmat {
     float* Z = nullptr;          // [n]
     void* etab = nullptr;        // [nnz] edge records: packed 16-byte (erec_bytes 16) or EdgeRec (32)
     uint32_t erec_bytes = 32;
-    uint32_t* e_alias = nullptr; // [nnz] alias entry of each bucket
     uint2* vtab = nullptr;       // [n] {thresh, alias}
     double* beta = nullptr;      // [n] 1/(2 sigma_i^2) when calibrated
 };
@@ -286,6 +285,7 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
 void crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* c, double* crosslessness);
 double min_angle(drg_ctx* ctx, const drg_graph* g, const float* pos);
 void dmat_free(drg_dmat* d);
+void edge_alias_ids(drg_ctx* ctx, const drg_dmat* d, uint64_t e0, uint64_t e1, uint32_t* host_out);
 drg_graph* coarsen(drg_ctx* ctx, const drg_graph* fine, uint32_t level, const drg_params& p, uint32_t* parent);
 drg_hier* build_hierarchy(drg_ctx* ctx, const drg_graph* g0, const drg_params& p);
 void hier_free(drg_hier* h);

@@ -1242,14 +1242,13 @@ __global__ void __launch_bounds__(MERGE_THREADS) k_merge_alias(MergeArgs m) {
 
 // Where the table goes: the node table as {thresh, alias} pairs, or the edge
 // table as packed 16-byte or wide 32-byte records with the endpoints of the
-// bucket's own entry and of its alias (and the alias of every bucket).
+// bucket's own entry and of its alias.
 enum AliasOutKind { kOutNodes = 0, kOutEdges16 = 1, kOutEdges32 = 2 };
 
 struct AliasOut {
     int kind;
     uint2* nodes;            // kOutNodes: [N]
     void* edges;             // kOutEdges*: [N] records
-    uint32_t* e_alias;       // kOutEdges*: [N] alias of each bucket
     const uint32_t* esrc;    // kOutEdges*: row of each entry
     const uint32_t* col;     // kOutEdges*: column of each entry
 };
@@ -1290,7 +1289,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_alias_items(const uint32_t* _
                 o.nodes[i] = make_uint2(th, al);
             } else {
                 const uint32_t i0 = o.esrc[i], j0 = o.col[i], i1 = o.esrc[al], j1 = o.col[al];
-                o.e_alias[i] = al;
                 if constexpr (KIND == kOutEdges16) {
                     static_cast<uint4*>(o.edges)[i] = pack_edge16(th, i0, j0, i1, j1);
                 } else {
@@ -1362,10 +1360,45 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& ou
     return true;
 }
 
+// Alias entry of buckets [e0, e1) of the edge table, recovered from the
+// records (inspection only; the sampling path never needs it): the alias's
+// endpoints (i1, j1) name the entry of row i1 whose column is j1, found by a
+// binary search of that sorted row.
+__global__ void k_edge_alias_ids(const void* __restrict__ etab, int packed, const uint64_t* __restrict__ rp,
+                                 const uint32_t* __restrict__ col, uint64_t e0, uint64_t e1, uint32_t* __restrict__ out) {
+    for (uint64_t b = e0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < e1; b += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t i1, j1;
+        if (packed) {
+            const uint4 e = static_cast<const uint4*>(etab)[b];
+            i1 = (e.z >> 16) | ((e.w & 0xFFu) << 16);
+            j1 = e.w >> 8;
+        } else {
+            const EdgeRec& r = static_cast<const EdgeRec*>(etab)[b];
+            i1 = r.i1;
+            j1 = r.j1;
+        }
+        uint64_t lo = rp[i1], hi = rp[i1 + 1];
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (col[mid] < j1) lo = mid + 1; else hi = mid;
+        }
+        out[b - e0] = (uint32_t)lo;
+    }
+}
+
+void edge_alias_ids(drg_ctx* ctx, const drg_dmat* d, uint64_t e0, uint64_t e1, uint32_t* host_out) {
+    if (e1 <= e0) return;
+    DBuf<uint32_t> tmp(ctx, e1 - e0);
+    DRG_LAUNCH(ctx, k_edge_alias_ids, grid_for(e1 - e0, 256, (uint32_t)ctx->num_sms * 16), 256, 0, d->etab,
+               d->erec_bytes == 16 ? 1 : 0, d->rp, d->col, e0, e1, tmp.p);
+    d2h(ctx, host_out, tmp.p, e1 - e0);
+    sync(ctx);
+}
+
 void dmat_free(drg_dmat* d) {
     if (!d) return;
     drg_ctx* c = d->ctx;
-    void* ps[] = {d->rp, d->col, d->dist, d->q, d->r, d->Z, d->etab, d->e_alias, d->vtab, d->beta};
+    void* ps[] = {d->rp, d->col, d->dist, d->q, d->r, d->Z, d->etab, d->vtab, d->beta};
     for (void* p : ps)
         if (p) dfree(c, p);
     delete d;
@@ -1433,8 +1466,7 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
             const bool packed = n <= kPackedIdLimit;
             d->erec_bytes = packed ? 16u : (uint32_t)sizeof(EdgeRec);
             d->etab = dalloc(ctx, (size_t)d->erec_bytes * nnz);
-            d->e_alias = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * nnz));
-            AliasOut out{packed ? kOutEdges16 : kOutEdges32, nullptr, d->etab, d->e_alias, esrc.p, d->col};
+            AliasOut out{packed ? kOutEdges16 : kOutEdges32, nullptr, d->etab, esrc.p, d->col};
             DRG_CHECK(build_alias(ctx, d->q, nnz, out), DRG_EEMPTY, "all edge weights are zero");
         }
         // node table (negative samples)
@@ -1442,7 +1474,7 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
             DBuf<uint32_t> r32(ctx, n);
             DRG_LAUNCH(ctx, k_shift_u32, grid_for(n, 256, 65536), 256, 0, d->r, n, d->shift, r32.p);
             d->vtab = static_cast<uint2*>(dalloc(ctx, sizeof(uint2) * n));
-            AliasOut out{kOutNodes, d->vtab, nullptr, nullptr, nullptr, nullptr};
+            AliasOut out{kOutNodes, d->vtab, nullptr, nullptr, nullptr};
             DRG_CHECK(build_alias(ctx, r32.p, n, out), DRG_EEMPTY, "all node weights are zero");
         }
         sync(ctx);

@@ -19,6 +19,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <cuda.h>
 #include <exception>
 #include <memory>
@@ -297,7 +298,8 @@ struct HogwildArgs {
     uint32_t t_begin;     // first epoch
     uint32_t epochs;      // epochs of this launch
     uint32_t T;           // threads of the run
-    uint32_t nl;          // samples per epoch
+    uint32_t nl;          // samples per epoch (and nodes of the level)
+    uint32_t refresh;     // half-precision copies: threads g < refresh rewrite nodes g, g + refresh, ...
 };
 
 // Epoch gates of one launch: done[e] counts the warps that finished epoch e
@@ -411,6 +413,41 @@ __global__ void k_level_nodes(const uint2* __restrict__ vtab, const uint32_t* __
     }
 }
 
+// A negative's position for the force: the FP32 master or the half-precision
+// copy, read through L2 only (both change during the launch).
+template <int PREC>
+__device__ __forceinline__ float2 hw_gather_neg(const EpochArgs& a, uint32_t v) {
+    if constexpr (PREC == DRG_PREC_FP32) {
+        return __ldcg(&a.Y[v]);
+    } else {
+        const unsigned int u = __ldcg(reinterpret_cast<const unsigned int*>(a.Yh) + v);
+        if constexpr (PREC == DRG_PREC_FP16) {
+            __half2 h;
+            memcpy(&h, &u, sizeof(h));
+            return __half22float2(h);
+        } else {
+            __nv_bfloat162 h;
+            memcpy(&h, &u, sizeof(h));
+            return __bfloat1622float2(h);
+        }
+    }
+}
+
+// End of an epoch with half-precision copies: thread g rewrites the copies of
+// nodes g, g + stride, ... from the FP32 masters (coalesced), so a copy lags
+// its master by at most the epochs that warps drift apart.
+template <int PREC>
+__device__ __forceinline__ void hw_refresh(const HogwildArgs& h, uint32_t g) {
+    if constexpr (PREC != DRG_PREC_FP32) {
+        if (g >= h.refresh) return;
+        for (uint32_t v = g; v < h.nl; v += h.refresh) {
+            const float2 y = __ldcg(&h.a.Y[v]);
+            if constexpr (PREC == DRG_PREC_FP16) reinterpret_cast<__half2*>(const_cast<void*>(h.a.Yh))[v] = __float22half2_rn(y);
+            else reinterpret_cast<__nv_bfloat162*>(const_cast<void*>(h.a.Yh))[v] = __float22bfloat162_rn(y);
+        }
+    }
+}
+
 __device__ __forceinline__ void hw_push(float2* Y, uint32_t v, float lr, float fx, float fy) {
     atomicAdd(&Y[v], make_float2(lr * fx, lr * fy));
 }
@@ -438,14 +475,14 @@ struct HwPipe {
     uint32_t t1, s1, g;     // next sample to request; the thread's first sample
 };
 
-template <int MT, bool ANC, int P>
+template <int MT, bool ANC, int PREC, int P>
 __device__ __forceinline__ void hw_step(const HogwildArgs& h, HwPipe<MT, ANC>& p, uint64_t k, uint64_t cnt) {
     const EpochArgs& a = h.a;
     const Resolved<MT> I = p.V[P];
     const float2 ya = __ldcg(&a.Y[I.ia]), yc = __ldcg(&a.Y[I.ic]);
     float2 ym[MT];
 #pragma unroll
-    for (int m = 0; m < MT; ++m) ym[m] = __ldcg(&a.Y[I.jm[m]]);
+    for (int m = 0; m < MT; ++m) ym[m] = hw_gather_neg<PREC>(a, I.jm[m]);
     const float lr = __ldg(&h.lr_tab[p.tV[P]]);
     if (k + 2 < cnt) {
         hw_resolve<MT, ANC>(a, p.Q[P], p.V[P]);
@@ -484,7 +521,7 @@ __device__ __forceinline__ uint32_t hw_share(const HogwildArgs& h, uint32_t g) {
 
 // One thread's share of a run: in each epoch the samples g, g + T, ... < n_l;
 // every thread of the grid takes part in every epoch barrier.
-template <int MT, bool ANC>
+template <int MT, bool ANC, int PREC>
 __device__ __forceinline__ bool hogwild_thread(const HogwildArgs& h, const GridSync& gs, uint32_t g,
                                                uint32_t t_begin, uint32_t epochs) {
     const uint32_t share = hw_share(h, g);
@@ -511,19 +548,20 @@ __device__ __forceinline__ bool hogwild_thread(const HogwildArgs& h, const GridS
         // samples [k, end) of this epoch, two at a time (slot parity = sample
         // parity; the pair body lets one sample's compute fill the other's waits)
         const uint64_t end = k + share;
-        if (k < end && (k & 1)) hw_step<MT, ANC, 1>(h, p, k++, cnt);
+        if (k < end && (k & 1)) hw_step<MT, ANC, PREC, 1>(h, p, k++, cnt);
         for (; k + 1 < end; k += 2) {
-            hw_step<MT, ANC, 0>(h, p, k, cnt);
-            hw_step<MT, ANC, 1>(h, p, k + 1, cnt);
+            hw_step<MT, ANC, PREC, 0>(h, p, k, cnt);
+            hw_step<MT, ANC, PREC, 1>(h, p, k + 1, cnt);
         }
-        if (k < end) hw_step<MT, ANC, 0>(h, p, k++, cnt);
+        if (k < end) hw_step<MT, ANC, PREC, 0>(h, p, k++, cnt);
+        hw_refresh<PREC>(h, g);
         if (gs.done) epoch_done(gs, e);
     }
     return true;
 }
 
 // Runtime number of negatives: the same samples, one after another.
-template <bool ANC>
+template <bool ANC, int PREC>
 __device__ __forceinline__ bool hogwild_thread_rt(const HogwildArgs& h, const GridSync& gs, uint32_t g,
                                                   uint32_t t_begin, uint32_t epochs) {
     const EpochArgs& a = h.a;
@@ -544,7 +582,7 @@ __device__ __forceinline__ bool hogwild_thread_rt(const HogwildArgs& h, const Gr
                 uint32_t cm = draw_negative(a, W, m);
                 if (ANC) cm = __ldg(&a.anc[cm]);
                 if (cm == ia || cm == ic) continue;
-                const float2 fr = repel(a, ya, __ldcg(&a.Y[cm]));
+                const float2 fr = repel(a, ya, hw_gather_neg<PREC>(a, cm));
                 Fx += fr.x;
                 Fy += fr.y;
                 hw_push(a.Y, cm, lr, -fr.x, -fr.y);
@@ -552,23 +590,26 @@ __device__ __forceinline__ bool hogwild_thread_rt(const HogwildArgs& h, const Gr
             hw_push(a.Y, ia, lr, Fx, Fy);
             hw_push(a.Y, ic, lr, -fa.x, -fa.y);
         }
+        hw_refresh<PREC>(h, g);
         if (gs.done) epoch_done(gs, e);
     }
     return true;
 }
 
-template <int MT, bool ANC>
+template <int MT, bool ANC, int PREC>
 __device__ __forceinline__ void hogwild_dispatch(const HogwildArgs& h, const GridSync& gs, uint32_t g,
                                                  uint32_t t_begin, uint32_t epochs) {
-    if constexpr (MT > 0) hogwild_thread<MT, ANC>(h, gs, g, t_begin, epochs);
-    else hogwild_thread_rt<ANC>(h, gs, g, t_begin, epochs);
+    if constexpr (MT > 0) hogwild_thread<MT, ANC, PREC>(h, gs, g, t_begin, epochs);
+    else hogwild_thread_rt<ANC, PREC>(h, gs, g, t_begin, epochs);
 }
 
-// MT > 0: compile-time number of negatives; MT == 0: runtime M.  Every
-// thread of the grid (also those past T) runs, for the epoch barriers.
-template <int MT, bool ANC>
+// MT > 0: compile-time number of negatives; MT == 0: runtime M.  PREC: the
+// negatives' positions from the FP32 masters or from a half-precision copy
+// (refreshed at the end of every epoch).  Every thread of the grid (also
+// those past T) runs, for the epoch barriers.
+template <int MT, bool ANC, int PREC>
 __global__ void __launch_bounds__(128, 4) k_hogwild(HogwildArgs h, GridSync gs) {
-    hogwild_dispatch<MT, ANC>(h, gs, blockIdx.x * blockDim.x + threadIdx.x, h.t_begin, h.epochs);
+    hogwild_dispatch<MT, ANC, PREC>(h, gs, blockIdx.x * blockDim.x + threadIdx.x, h.t_begin, h.epochs);
 }
 
 // One level of each of many graphs in one launch: run x owns the threads
@@ -576,7 +617,7 @@ __global__ void __launch_bounds__(128, 4) k_hogwild(HogwildArgs h, GridSync gs) 
 // gates (all runs have the same number of epochs).  Every run has an
 // ancestor map (level-0 runs the identity), so all threads of a block take
 // the same code path through the gates.
-template <int MT>
+template <int MT, int PREC>
 __global__ void __launch_bounds__(128) k_hogwild_batch(const HogwildArgs* __restrict__ runs,
                                                        const uint32_t* __restrict__ prefix, uint32_t nruns,
                                                        GridSync gs, uint32_t t_begin, uint32_t epochs) {
@@ -584,7 +625,7 @@ __global__ void __launch_bounds__(128) k_hogwild_batch(const HogwildArgs* __rest
     const uint32_t x = find_job(prefix, nruns, gt);
     const HogwildArgs& h = runs[x];
     const uint32_t g = gt - prefix[x];
-    hogwild_dispatch<MT, true>(h, gs, g, t_begin, epochs);
+    hogwild_dispatch<MT, true, PREC>(h, gs, g, t_begin, epochs);
 }
 
 __global__ void k_iota(uint32_t* __restrict__ out, uint32_t n) {
@@ -809,9 +850,14 @@ static uint32_t epoch_grid(drg_ctx*, uint64_t count) { return (uint32_t)((count 
 
 typedef void (*HogwildKernel)(HogwildArgs, GridSync);
 
-static HogwildKernel pick_hogwild(uint32_t M, bool anc) {
-    if (M == 5) return anc ? k_hogwild<5, true> : k_hogwild<5, false>;
-    return anc ? k_hogwild<0, true> : k_hogwild<0, false>;
+static HogwildKernel pick_hogwild(uint32_t M, bool anc, int prec) {
+    static const HogwildKernel tab[2][2][3] = {
+        {{k_hogwild<0, false, 0>, k_hogwild<0, false, 1>, k_hogwild<0, false, 2>},
+         {k_hogwild<0, true, 0>, k_hogwild<0, true, 1>, k_hogwild<0, true, 2>}},
+        {{k_hogwild<5, false, 0>, k_hogwild<5, false, 1>, k_hogwild<5, false, 2>},
+         {k_hogwild<5, true, 0>, k_hogwild<5, true, 1>, k_hogwild<5, true, 2>}},
+    };
+    return tab[M == 5 ? 1 : 0][anc ? 1 : 0][prec];
 }
 
 // Cooperative launch (all blocks resident together); false when the grid
@@ -856,12 +902,14 @@ struct SyncBuf {
     }
 };
 
-// Epochs [t_begin, t_end) of an FP32 Hogwild level run in one cooperative
-// launch of T = min(ceil(n_l / substeps), resident threads) threads (one
-// launch per epoch when the grid cannot be resident at once).
+// Epochs [t_begin, t_end) of a Hogwild level run in one cooperative launch of
+// T = min(ceil(n_l / substeps), resident threads) threads (one launch per
+// epoch when the grid cannot be resident at once).  With half-precision
+// copies (a.Yh, filled before the call) the negatives read the copy, which
+// every thread of the grid helps rewrite at the end of each epoch.
 static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p, uint32_t nl, const float* lr_tab,
                           uint32_t t_begin, uint32_t t_end) {
-    const HogwildKernel k = pick_hogwild(p.M, a.anc != nullptr);
+    const HogwildKernel k = pick_hogwild(p.M, a.anc != nullptr, p.precision);
     int per_sm = 0;
     DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
     const uint64_t resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * 128u;
@@ -881,6 +929,7 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
         h.a.vtab_l = vl.p;
     }
     const uint32_t grid = (h.T + 127) / 128;
+    h.refresh = grid * 128;
     SyncBuf sb(ctx, h.epochs);
     {
         ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)h.epochs * nl, 1);
@@ -901,7 +950,7 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
 // launch.  When their threads exceed what the GPU holds at once, every run's
 // thread count is scaled down in proportion (at least one each), so that all
 // threads are resident together and the bound only tightens.
-static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& runs, uint32_t epochs,
+static void hogwild_batch(drg_ctx* ctx, uint32_t M, int prec, std::vector<HogwildArgs>& runs, uint32_t epochs,
                           uint64_t samples) {
     if (runs.empty()) return;
     std::vector<DBuf<uint4>> tables;     // level node tables
@@ -918,7 +967,10 @@ static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& ru
                    h.a.n0, tables.back().p);
         h.a.vtab_l = tables.back().p;
     }
-    const auto k = M == 5 ? k_hogwild_batch<5> : k_hogwild_batch<0>;
+    typedef void (*BatchKernel)(const HogwildArgs*, const uint32_t*, uint32_t, GridSync, uint32_t, uint32_t);
+    static const BatchKernel tab[2][3] = {{k_hogwild_batch<0, 0>, k_hogwild_batch<0, 1>, k_hogwild_batch<0, 2>},
+                                          {k_hogwild_batch<5, 0>, k_hogwild_batch<5, 1>, k_hogwild_batch<5, 2>}};
+    const BatchKernel k = tab[M == 5 ? 1 : 0][prec];
     int per_sm = 0;
     DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
     const uint64_t resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * 128u;
@@ -930,7 +982,10 @@ static void hogwild_batch(drg_ctx* ctx, uint32_t M, std::vector<HogwildArgs>& ru
         for (auto& h : runs) h.T = (uint32_t)(1 + (uint64_t)h.T * room / want);
     }
     std::vector<uint32_t> prefix(nruns + 1, 0);
-    for (size_t x = 0; x < nruns; ++x) prefix[x + 1] = prefix[x] + runs[x].T;
+    for (size_t x = 0; x < nruns; ++x) {
+        prefix[x + 1] = prefix[x] + runs[x].T;
+        runs[x].refresh = runs[x].T;  // a run's copies are rewritten by its own threads
+    }
     DBuf<HogwildArgs> druns(ctx, nruns);
     DBuf<uint32_t> dprefix(ctx, nruns + 1);
     h2d(ctx, druns.p, runs.data(), nruns);
@@ -1065,7 +1120,7 @@ void layout_level(drg_ctx* ctx, const drg_dmat* d, const drg_hier* h, uint32_t l
         lr_host[t] = (float)((double)p.lr0 * (1.0 - (double)t / (double)p.epochs));
     DBuf<float> lr_tab(ctx, p.epochs);
     h2d(ctx, lr_tab.p, lr_host.data(), p.epochs);
-    if (!sync_mode && prec == DRG_PREC_FP32) {
+    if (!sync_mode) {
         hogwild_level(ctx, a, p, nl, lr_tab.p, t_begin, t_end);
         return;
     }
@@ -1369,7 +1424,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
         const EpochState st_host{0u, p.epochs, lr_host[0], 0u, lr_tab.p};
         const EpochBatchKernel ek = pick_epoch_batch(p.M, sync_mode, prec);
         const EpochArgs proto = epoch_args(gs[0].d, nullptr, nullptr, p, p.gamma, 0);
-        const bool one_launch = !sync_mode && prec == DRG_PREC_FP32;  // Hogwild: one launch per round
+        const bool one_launch = !sync_mode;  // Hogwild: one launch per round
         for (uint32_t r = 0; r <= Lmax; ++r) {
             std::vector<BatchJob> jobs;
             std::vector<HogwildArgs> runs;
@@ -1423,6 +1478,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                     h.a.n0 = J.n0;
                     h.a.anc = J.anc;
                     h.a.Y = J.Y;
+                    h.a.Yh = J.Yh;
                     h.a.tag = J.tag;
                     h.a.gamma = J.gamma;
                     h.a.b = J.b;
@@ -1438,7 +1494,14 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
             }
             const uint32_t njobs = (uint32_t)jobs.size();
             if (one_launch) {
-                hogwild_batch(ctx, p.M, runs, p.epochs, samples * p.epochs);
+                if (prec) {  // first half copies of every run
+                    for (const auto& h : runs) {
+                        const uint32_t gn = grid_for(h.nl, 256, (uint32_t)ctx->num_sms * 8);
+                        if (prec == 1) DRG_LAUNCH(ctx, k_refresh<1>, gn, 256, 0, h.a.Y, const_cast<void*>(h.a.Yh), h.nl);
+                        else DRG_LAUNCH(ctx, k_refresh<2>, gn, 256, 0, h.a.Y, const_cast<void*>(h.a.Yh), h.nl);
+                    }
+                }
+                hogwild_batch(ctx, p.M, prec, runs, p.epochs, samples * p.epochs);
             } else {
                 DBuf<BatchJob> djobs(ctx, njobs);
                 DBuf<uint32_t> dbpre(ctx, njobs + 1), dnpre(ctx, njobs + 1);

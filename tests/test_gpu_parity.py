@@ -466,6 +466,55 @@ def test_mixed_precision_epoch_error(drg, ctx, orc, prec, tol):
     assert err <= tol * _extent(ref), (err, _extent(ref))
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_hogwild_half_copies_touch_only_the_negatives(drg, ctx, prec):
+    # The one-launch Hogwild kernel with half-precision copies reads them for
+    # the negatives' positions only: with gamma = 0 the negatives exert no
+    # force, so one sample in flight gives the FP32 run bit for bit (the
+    # attraction, the atomic adds and the FP32 masters are untouched).
+    g = _graphs()["ba2000"]
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, 2)
+    Y0 = (np.random.default_rng(4).normal(size=(2000, 2)) * 12).astype(np.float32)
+    out = []
+    for precision in (0, prec):
+        p = drg.Params.default(k=2, M=5, epochs=500, b=1.0, mode=1, substeps=2000, multilevel=0, seed=1,
+                               precision=precision)
+        Yd = torch.from_numpy(Y0.reshape(-1).copy()).cuda()
+        drg.layout_level(ctx, D, None, 0, Yd, p, 0.0, 50, 52)
+        torch.cuda.synchronize()
+        out.append(Yd.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    assert np.max(np.abs(out[0] - Y0.reshape(-1))) > 1e-3
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 2e-3), (2, 1e-2)])
+def test_hogwild_half_copies_epoch_error(drg, ctx, orc, prec, tol):
+    # One Hogwild epoch with one sample in flight against the oracle's
+    # sequential loop.  The negatives read a copy rounded to FP16 (unit
+    # roundoff 2^-11) or BF16 (2^-8) and rewritten only at the end of the
+    # epoch, so besides the rounding they see positions up to one epoch old;
+    # the bar is a few units of the copy's rounding relative to the extent,
+    # like the synchronous copies' (the staleness is smaller than that late in
+    # a run: learning rate 0.2, spread layout).
+    g = _graphs()["ba2000"]
+    orp, ocol, gd, tab = _device_tables(orc, g, 2)
+    op = orc.Params(k=2, M=5, epochs=500, b=1.0, mode=1, multilevel=False, seed=1)
+    Y0 = (np.random.default_rng(0).normal(size=(2000, 2)) * 12).astype(np.float32).astype(np.float64)
+    ref = orc.layout_level(tab, Y0.copy(), 0, None, op, 0.1, 400, 401)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, 2)
+    p = drg.Params.default(k=2, M=5, epochs=500, b=1.0, mode=1, substeps=2000, multilevel=0, seed=1, precision=prec)
+    Yd = torch.from_numpy(Y0.astype(np.float32).reshape(-1)).cuda()
+    drg.layout_level(ctx, D, None, 0, Yd, p, 0.1, 400, 401)
+    torch.cuda.synchronize()
+    got = Yd.cpu().numpy().astype(np.float64).reshape(-1, 2)
+    err = np.max(np.abs(got - ref))
+    print(f"half-copy Hogwild epoch error, precision {prec}: {err / _extent(ref):.3g} of the extent")
+    assert err <= tol * _extent(ref), (err, _extent(ref))
+    assert np.max(np.abs(ref - Y0)) > 1e-3
+
+
 # ---------------------------------------------------------------- whole runs
 def _quality(orc, rp, col, Y):
     return orc.neighbourhood_preservation(rp, col, Y), orc.stress(rp, col, Y)

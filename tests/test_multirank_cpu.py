@@ -72,14 +72,21 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "updates/s"
 
 
-def test_traffic_record_only_for_its_configuration():
-    # the committed DRAM-traffic figure of the level kernel feeds the bench's
-    # roofline only for the configuration and kernel source it was taken on
+def test_traffic_record_only_for_its_configuration(tmp_path):
+    # a DRAM-traffic record of the level kernel feeds the bench's roofline
+    # only for the configuration and kernel source it was taken on
     sys.path.insert(0, ROOT)
     import bench
     cfg = {"workload": "dcsbm1m", "k": 2, "coarsen": "hem", "mode": "hogwild", "precision": "fp32",
            "multilevel": True}
-    assert bench.ncu_traffic_per_sample("k_hogwild", cfg) is not None
-    for key, other in (("coarsen", "star"), ("workload", "ba100k"), ("k", 3), ("mode", "sync"), ("multilevel", False)):
-        assert bench.ncu_traffic_per_sample("k_hogwild", dict(cfg, **{key: other})) is None
-    assert bench.ncu_traffic_per_sample("k_no_such_kernel", cfg) is None
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel": "k_hogwild", "kernel_hash": bench.kernel_hash(), "dram_bytes_per_sample": 100.0, "config": cfg}
+    (tmp_path / "profiles" / "k_hogwild_traffic.json").write_text(json.dumps(rec))
+    assert bench.ncu_traffic_per_sample("k_hogwild", cfg, root=str(tmp_path)) == 100.0
+    for key, other in (("coarsen", "star"), ("workload", "ba100k"), ("k", 3), ("mode", "sync"), ("multilevel", False),
+                       ("precision", "bf16")):
+        assert bench.ncu_traffic_per_sample("k_hogwild", dict(cfg, **{key: other}), root=str(tmp_path)) is None
+    assert bench.ncu_traffic_per_sample("k_no_such_kernel", cfg, root=str(tmp_path)) is None
+    # a record taken on other kernel source is not used
+    (tmp_path / "profiles" / "k_hogwild_traffic.json").write_text(json.dumps(dict(rec, kernel_hash="0" * 16)))
+    assert bench.ncu_traffic_per_sample("k_hogwild", cfg, root=str(tmp_path)) is None
