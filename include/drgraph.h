@@ -349,9 +349,11 @@ drg_status drg_layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const
  * (0 when max = min; an affine map changes no crossing), and two edges
  * without a common endpoint cross when each strictly separates the other's
  * endpoints by 64-bit integer orientation tests (touching and collinear
- * pairs do not count).  All pairs are tested (|E|^2 / 2 tests, about 2 s for
- * 4 million edges).  pos: device float[2 n].  DRG_EINVAL for a non-finite
- * coordinate.  Synchronises. */
+ * pairs do not count).  All pairs are tested (|E|^2 / 2 tests at about
+ * 4 x 10^11 tests/s: 19 s for 4 million edges), in launches of at most 2^37
+ * tests each; graphs with more than 2^23 edges return DRG_EUNSUPPORTED.
+ * pos: device float[2 n].  DRG_EINVAL for a non-finite coordinate.
+ * Synchronises. */
 drg_status drg_crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* crossings,
                          double* crosslessness);
 /* Sec. 4.1 Eq. 19, minimum angle: *min_angle = 1 - mean over nodes of
@@ -393,6 +395,29 @@ drg_status drg_profile_reset(drg_ctx* ctx);
 /* Total milliseconds, number of timed launches and units of one family.
  * Synchronises. */
 drg_status drg_profile_read(drg_ctx* ctx, int which, double* ms, uint64_t* launches, uint64_t* units);
+
+/* ---------------------------------------------------------------- launch-shape autotuner */
+/* The Hogwild level runs (drg_layout_level, drg_layout, drg_layout_batch)
+ * use T threads, at most the in-flight bound; their launch shape is tuned
+ * (no counterpart in the paper): the first run of at least 50 epochs for
+ * each (device, kernel, M, precision, ancestor map, size bucket = bit length
+ * of the level's nodes, or of a batch's total threads) times every candidate
+ * -- 64, 128 or 256 threads per block, T = the bound or half of it (a
+ * smaller T only tightens the bound; batches tune the block size only) --
+ * for 3 epochs on scratch copies of its positions, and every later run with
+ * that key uses the fastest.  The table is process-wide.  Results of a run
+ * depend on the shape only as far as Hogwild runs depend on thread timing.
+ * drg_autotune_enable(ctx, 0) keeps the default shape (128 threads per
+ * block, T = the bound) for the context's runs; on by default. */
+drg_status drg_autotune_enable(drg_ctx* ctx, int on);
+/* The tuned entries: *count receives their number; the first `cap` are
+ * written (any array may be NULL): keys[6 i ..] = {kernel (0 single graph,
+ * 1 batch), M (5, or 0 for any other), precision, ancestor map (0 or 1),
+ * size bucket, device}, choice[2 i ..] = {threads per block, divisor of the
+ * bound}, ms_per_epoch[i] = the choice's time per epoch in the tuning run. */
+drg_status drg_autotune_read(uint32_t cap, uint32_t* keys, uint32_t* choice, float* ms_per_epoch, uint32_t* count);
+/* Forget every tuned entry (the next long runs tune again). */
+drg_status drg_autotune_clear(void);
 
 /* ---------------------------------------------------------------- memory probes */
 /* Measured ceilings for the roofline of the level kernels (no counterpart in

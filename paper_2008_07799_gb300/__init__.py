@@ -38,7 +38,7 @@ EXPORTS = [
     "drg_layout_batch", "drg_sample_draws", "drg_profile_enable", "drg_profile_reset", "drg_profile_read",
     "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
     "drg_build_distance_matrix_ex", "drg_dmat_calibration", "drg_crossings", "drg_min_angle",
-    "drg_probe_memory",
+    "drg_probe_memory", "drg_autotune_enable", "drg_autotune_read", "drg_autotune_clear",
 ]
 
 PROBE_LOAD8, PROBE_LOAD16, PROBE_RED8, PROBE_LOAD16_EVICT_FIRST, PROBE_COPY = range(5)
@@ -134,6 +134,9 @@ def lib():
         "drg_sample_draws": (st, [VP, VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, PP, VP, VP, VP]),
         "drg_probe_memory": (st, [VP, C.c_int, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(C.c_double),
                                   C.POINTER(C.c_uint64)]),
+        "drg_autotune_enable": (st, [VP, C.c_int]),
+        "drg_autotune_read": (st, [C.c_uint32, VP, VP, VP, C.POINTER(C.c_uint32)]),
+        "drg_autotune_clear": (st, []),
         "drg_profile_enable": (st, [VP, C.c_int]),
         "drg_profile_reset": (st, [VP]),
         "drg_profile_read": (st, [VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
@@ -194,6 +197,10 @@ class Context:
 
     def profile(self, on=True):
         self.check(lib().drg_profile_enable(self.h, int(on)))
+
+    def autotune(self, on=True):
+        """Tune the Hogwild kernels' launch shape (on by default)."""
+        self.check(lib().drg_autotune_enable(self.h, int(on)))
 
     def profile_reset(self):
         self.check(lib().drg_profile_reset(self.h))
@@ -460,3 +467,22 @@ def probe_memory(ctx: Context, kind, buffer_bytes, accesses, blocks_per_sm=6):
     ctx.check(lib().drg_probe_memory(ctx.h, int(kind), int(buffer_bytes), int(accesses), int(blocks_per_sm),
                                      C.byref(ms), C.byref(done)))
     return ms.value, done.value
+
+
+def autotune_table():
+    """The process-wide tuned launch shapes: a list of dicts."""
+    cnt = C.c_uint32()
+    lib().drg_autotune_read(0, None, None, None, C.byref(cnt))
+    n = cnt.value
+    keys = np.zeros(6 * max(n, 1), np.uint32)
+    choice = np.zeros(2 * max(n, 1), np.uint32)
+    ms = np.zeros(max(n, 1), np.float32)
+    lib().drg_autotune_read(n, _ptr(keys), _ptr(choice), _ptr(ms), C.byref(cnt))
+    return [dict(kernel=("k_hogwild", "k_hogwild_batch")[int(keys[6 * i])], M=int(keys[6 * i + 1]),
+                 precision=int(keys[6 * i + 2]), ancestors=int(keys[6 * i + 3]), bucket=int(keys[6 * i + 4]),
+                 device=int(keys[6 * i + 5]), block=int(choice[2 * i]), divisor=int(choice[2 * i + 1]),
+                 ms_per_epoch=float(ms[i])) for i in range(min(n, cnt.value))]
+
+
+def autotune_clear():
+    lib().drg_autotune_clear()

@@ -486,6 +486,23 @@ drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_h
     API_CATCH(ctx)
 }
 
+drg_status drg_autotune_enable(drg_ctx* ctx, int on) {
+    if (!ctx) return DRG_EINVAL;
+    ctx->autotune = on != 0;
+    return DRG_OK;
+}
+
+drg_status drg_autotune_read(uint32_t cap, uint32_t* keys, uint32_t* choice, float* ms_per_epoch, uint32_t* count) {
+    if (!count) return DRG_EINVAL;
+    *count = drg::autotune_read(cap, keys, choice, ms_per_epoch);
+    return DRG_OK;
+}
+
+drg_status drg_autotune_clear(void) {
+    drg::autotune_clear();
+    return DRG_OK;
+}
+
 drg_status drg_probe_memory(drg_ctx* ctx, int kind, uint64_t buffer_bytes, uint64_t accesses, uint32_t blocks_per_sm,
                             double* ms, uint64_t* done) {
     if (!ctx || !ms || !done) return DRG_EINVAL;

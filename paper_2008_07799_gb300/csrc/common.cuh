@@ -58,6 +58,7 @@ struct drg_ctx {
     std::string err;
     uint64_t launches = 0;
     bool direct_launch = false;             // DRG_DIRECT_LAUNCH=1: no level graphs (for profilers)
+    bool autotune = true;                   // tune the Hogwild kernels' launch shape (drg_autotune_enable)
     int64_t bfs_stage_limit = -1;           // DRG_BFS_STAGE_LIMIT=<entries>: cap the k-order staging
                                             // area (rows past it take the direct traversal); -1: none
     // profiling (drg_profile_*)
@@ -302,6 +303,8 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                   const float* b_per_graph, float* const* pos);
 void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, uint32_t s_begin, uint32_t s_end,
                   const drg_params& p, uint32_t* oi, uint32_t* oj, uint32_t* oneg);
+uint32_t autotune_read(uint32_t cap, uint32_t* keys, uint32_t* choice, float* ms);
+void autotune_clear();
 void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uint32_t blocks_per_sm, double* ms,
                   uint64_t* done);
 

@@ -22,9 +22,11 @@
 #include <cstring>
 #include <cuda.h>
 #include <exception>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <type_traits>
 
 namespace drg {
@@ -608,7 +610,7 @@ __device__ __forceinline__ void hogwild_dispatch(const HogwildArgs& h, const Gri
 // (refreshed at the end of every epoch).  Every thread of the grid (also
 // those past T) runs, for the epoch barriers.
 template <int MT, bool ANC, int PREC>
-__global__ void __launch_bounds__(128, 4) k_hogwild(HogwildArgs h, GridSync gs) {
+__global__ void __launch_bounds__(256, 2) k_hogwild(HogwildArgs h, GridSync gs) {
     hogwild_dispatch<MT, ANC, PREC>(h, gs, blockIdx.x * blockDim.x + threadIdx.x, h.t_begin, h.epochs);
 }
 
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(128, 4) k_hogwild(HogwildArgs h, GridSync gs) 
 // ancestor map (level-0 runs the identity), so all threads of a block take
 // the same code path through the gates.
 template <int MT, int PREC>
-__global__ void __launch_bounds__(128) k_hogwild_batch(const HogwildArgs* __restrict__ runs,
+__global__ void __launch_bounds__(256, 2) k_hogwild_batch(const HogwildArgs* __restrict__ runs,
                                                        const uint32_t* __restrict__ prefix, uint32_t nruns,
                                                        GridSync gs, uint32_t t_begin, uint32_t epochs) {
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -902,24 +904,190 @@ struct SyncBuf {
     }
 };
 
+// ------------------------------------------------------------------ launch-shape autotuner
+// The Hogwild level kernels run a fixed number of threads T <= the in-flight
+// bound, so their launch shape is the one free choice: threads per block
+// (64, 128 or 256: how the warps spread over the SMs) and the samples per
+// thread (T = the bound or half of it; a smaller T only tightens the bound).
+// The first long run of each (device, kernel, M, precision, ancestor map,
+// size bucket) times every candidate for a few epochs on a scratch copy of
+// its positions and keeps the fastest for the process.
+struct TuneKey {
+    int dev, family, prec, anc;
+    uint32_t M, bucket;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, family, prec, anc, M, bucket) < std::tie(o.dev, o.family, o.prec, o.anc, o.M, o.bucket);
+    }
+};
+
+struct TuneChoice {
+    uint32_t block, div;
+    float ms;  // per epoch, of the choice, in the tuning run
+};
+
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneChoice> g_tune;
+constexpr uint32_t kTuneBlocks[3] = {64, 128, 256};
+constexpr uint32_t kTuneDivs[2] = {1, 2};
+constexpr uint32_t kTuneEpochs = 3;      // epochs timed per candidate
+constexpr uint32_t kTuneMinEpochs = 50;  // runs shorter than this use the default shape
+constexpr TuneChoice kTuneDefault{128, 1, 0.f};
+
+static uint32_t bitlen32(uint64_t x) {
+    uint32_t b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+static bool tune_lookup(const TuneKey& key, TuneChoice& out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    out = it->second;
+    return true;
+}
+
+static void tune_store(const TuneKey& key, const TuneChoice& c) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = c;
+}
+
+uint32_t autotune_read(uint32_t cap, uint32_t* keys, uint32_t* choice, float* ms) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    uint32_t i = 0;
+    for (const auto& kv : g_tune) {
+        if (i < cap) {
+            if (keys) {
+                uint32_t* k = keys + 6 * (size_t)i;
+                k[0] = (uint32_t)kv.first.family;
+                k[1] = kv.first.M;
+                k[2] = (uint32_t)kv.first.prec;
+                k[3] = (uint32_t)kv.first.anc;
+                k[4] = kv.first.bucket;
+                k[5] = (uint32_t)kv.first.dev;
+            }
+            if (choice) {
+                choice[2 * (size_t)i] = kv.second.block;
+                choice[2 * (size_t)i + 1] = kv.second.div;
+            }
+            if (ms) ms[i] = kv.second.ms;
+        }
+        ++i;
+    }
+    return i;
+}
+
+void autotune_clear() {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
+}
+
+// Threads of a block size that can be resident at once.
+template <typename K>
+static uint64_t resident_threads(drg_ctx* ctx, K kernel, uint32_t block) {
+    int per_sm = 0;
+    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)block, 0));
+    return (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * block;
+}
+
+// One Hogwild level run of h.T threads in blocks of `block`: one cooperative
+// launch (all epochs, warps kept in step by the gates), or one launch per
+// epoch when the grid cannot be resident at once.  Returns the launches made.
+static uint64_t run_hogwild(drg_ctx* ctx, HogwildKernel k, HogwildArgs h, uint32_t block) {
+    const uint32_t grid = (h.T + block - 1) / block;
+    h.refresh = grid * block;
+    SyncBuf sb(ctx, h.epochs);
+    uint64_t launches = 1;
+    if (!launch_cooperative(ctx, "k_hogwild", k, grid, block, h,
+                            sb.sync(grid * (block / 32), kEpochLag, kGateTimeoutNs))) {
+        launches = h.epochs;
+        for (uint32_t e = 0; e < h.epochs; ++e) {
+            HogwildArgs h1 = h;
+            h1.t_begin = h.t_begin + e;
+            h1.epochs = 1;
+            DRG_LAUNCH(ctx, k, grid, block, 0, h1, GridSync{nullptr, nullptr, grid, 0, 0});
+        }
+    }
+    sb.check(ctx);
+    return launches;
+}
+
+static uint32_t hogwild_threads(drg_ctx* ctx, HogwildKernel k, uint64_t bound, const TuneChoice& c) {
+    const uint64_t want = (bound + c.div - 1) / c.div;
+    const uint64_t res = resident_threads(ctx, k, c.block);
+    return (uint32_t)(want < res ? want : res);
+}
+
+static void refresh_half(drg_ctx* ctx, int prec, const float2* Y, void* Yh, uint32_t n) {
+    const uint32_t gn = grid_for(n, 256, (uint32_t)ctx->num_sms * 8);
+    if (prec == 1) DRG_LAUNCH(ctx, k_refresh<1>, gn, 256, 0, Y, Yh, n);
+    else if (prec == 2) DRG_LAUNCH(ctx, k_refresh<2>, gn, 256, 0, Y, Yh, n);
+}
+
+// Times every candidate shape for kTuneEpochs epochs on scratch copies of
+// the run's positions (and half copies) and returns the fastest.
+static TuneChoice tune_hogwild(drg_ctx* ctx, HogwildKernel k, const HogwildArgs& h0, uint64_t bound, int prec) {
+    DBuf<float2> Yt(ctx, h0.nl);
+    DBuf<uint32_t> Yht;
+    d2d(ctx, Yt.p, h0.a.Y, h0.nl);
+    if (prec) {
+        Yht = DBuf<uint32_t>(ctx, h0.nl);
+        refresh_half(ctx, prec, Yt.p, Yht.p, h0.nl);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DRG_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        fail(DRG_ECUDA, "cudaEventCreate failed");
+    }
+    TuneChoice best{kTuneDefault.block, kTuneDefault.div, 3.4e38f};
+    try {
+        for (uint32_t block : kTuneBlocks) {
+            for (uint32_t div : kTuneDivs) {
+                HogwildArgs h = h0;
+                h.a.Y = Yt.p;
+                h.a.Yh = prec ? Yht.p : nullptr;
+                h.epochs = kTuneEpochs;
+                const TuneChoice c{block, div, 0.f};
+                h.T = hogwild_threads(ctx, k, bound, c);
+                DRG_CUDA(cudaEventRecord(e0, ctx->stream));
+                run_hogwild(ctx, k, h, block);
+                DRG_CUDA(cudaEventRecord(e1, ctx->stream));
+                DRG_CUDA(cudaEventSynchronize(e1));
+                float t = 0.f;
+                DRG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                t /= (float)kTuneEpochs;
+                if (t < best.ms) best = TuneChoice{block, div, t};
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
 // Epochs [t_begin, t_end) of a Hogwild level run in one cooperative launch of
-// T = min(ceil(n_l / substeps), resident threads) threads (one launch per
-// epoch when the grid cannot be resident at once).  With half-precision
-// copies (a.Yh, filled before the call) the negatives read the copy, which
-// every thread of the grid helps rewrite at the end of each epoch.
+// T <= min(ceil(n_l / substeps), resident threads) threads, in the launch
+// shape the autotuner chose (one launch per epoch when the grid cannot be
+// resident at once).  With half-precision copies (a.Yh, filled before the
+// call) the negatives read the copy, which every thread of the grid helps
+// rewrite at the end of each epoch.
 static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p, uint32_t nl, const float* lr_tab,
                           uint32_t t_begin, uint32_t t_end) {
     const HogwildKernel k = pick_hogwild(p.M, a.anc != nullptr, p.precision);
-    int per_sm = 0;
-    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
-    const uint64_t resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * 128u;
     const uint64_t bound = ((uint64_t)nl + p.substeps - 1) / p.substeps;
     HogwildArgs h{};
     h.a = a;
     h.lr_tab = lr_tab;
     h.t_begin = t_begin;
     h.epochs = t_end - t_begin;
-    h.T = (uint32_t)(bound < resident ? bound : resident);
     h.nl = nl;
     DBuf<uint4> vl;
     if (a.anc) {
@@ -928,28 +1096,57 @@ static void hogwild_level(drg_ctx* ctx, const EpochArgs& a, const drg_params& p,
                    vl.p);
         h.a.vtab_l = vl.p;
     }
-    const uint32_t grid = (h.T + 127) / 128;
-    h.refresh = grid * 128;
-    SyncBuf sb(ctx, h.epochs);
-    {
-        ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)h.epochs * nl, 1);
-        if (!launch_cooperative(ctx, "k_hogwild", k, grid, 128, h, sb.sync(grid * 4, kEpochLag, kGateTimeoutNs))) {
-            span.count = h.epochs;
-            for (uint32_t t = t_begin; t < t_end; ++t) {
-                HogwildArgs h1 = h;
-                h1.t_begin = t;
-                h1.epochs = 1;
-                DRG_LAUNCH(ctx, k, grid, 128, 0, h1, GridSync{nullptr, nullptr, grid, 0, 0});
-            }
-        }
+    TuneChoice c = kTuneDefault;
+    const TuneKey key{ctx->device, 0, p.precision, a.anc ? 1 : 0, p.M == 5 ? 5u : 0u, bitlen32(nl)};
+    if (ctx->autotune && bound > 1 && h.epochs >= kTuneMinEpochs && !tune_lookup(key, c)) {
+        c = tune_hogwild(ctx, k, h, bound, p.precision);
+        tune_store(key, c);
     }
-    sb.check(ctx);
+    h.T = hogwild_threads(ctx, k, bound, c);
+    ProfSpan span(ctx, DRG_PROF_EPOCH, (uint64_t)h.epochs * nl, 1);
+    span.count = run_hogwild(ctx, k, h, c.block);
 }
 
 // Hogwild runs of many graphs (each with T = ceil(n_l / substeps) set) in one
 // launch.  When their threads exceed what the GPU holds at once, every run's
 // thread count is scaled down in proportion (at least one each), so that all
-// threads are resident together and the bound only tightens.
+// threads are resident together and the bound only tightens.  The block size
+// is tuned like the single-graph runs' (per total thread count).
+typedef void (*BatchKernel)(const HogwildArgs*, const uint32_t*, uint32_t, GridSync, uint32_t, uint32_t);
+
+static uint64_t run_hogwild_batch(drg_ctx* ctx, BatchKernel k, std::vector<HogwildArgs> runs, uint32_t block,
+                                  uint32_t epochs) {
+    const uint64_t resident = resident_threads(ctx, k, block);
+    uint64_t want = 0;
+    for (const auto& h : runs) want += h.T;
+    const uint64_t nruns = runs.size();
+    if (want > resident) {
+        const uint64_t room = resident > nruns ? resident - nruns : 0;
+        for (auto& h : runs) h.T = (uint32_t)(1 + (uint64_t)h.T * room / want);
+    }
+    std::vector<uint32_t> prefix(nruns + 1, 0);
+    for (size_t x = 0; x < nruns; ++x) {
+        prefix[x + 1] = prefix[x] + runs[x].T;
+        runs[x].refresh = runs[x].T;  // a run's copies are rewritten by its own threads
+    }
+    DBuf<HogwildArgs> druns(ctx, nruns);
+    DBuf<uint32_t> dprefix(ctx, nruns + 1);
+    h2d(ctx, druns.p, runs.data(), nruns);
+    h2d(ctx, dprefix.p, prefix.data(), nruns + 1);
+    const uint32_t grid = (prefix[nruns] + block - 1) / block;
+    SyncBuf sb(ctx, epochs);
+    uint64_t launches = 1;
+    if (!launch_cooperative(ctx, "k_hogwild_batch", k, grid, block, druns.p, dprefix.p, (uint32_t)nruns,
+                            sb.sync(grid * (block / 32), kEpochLag, kGateTimeoutNs), 0u, epochs)) {
+        launches = epochs;
+        for (uint32_t t = 0; t < epochs; ++t)
+            DRG_LAUNCH(ctx, k, grid, block, 0, druns.p, dprefix.p, (uint32_t)nruns,
+                       GridSync{nullptr, nullptr, grid, 0, 0}, t, 1u);
+    }
+    sb.check(ctx);
+    return launches;
+}
+
 static void hogwild_batch(drg_ctx* ctx, uint32_t M, int prec, std::vector<HogwildArgs>& runs, uint32_t epochs,
                           uint64_t samples) {
     if (runs.empty()) return;
@@ -967,42 +1164,63 @@ static void hogwild_batch(drg_ctx* ctx, uint32_t M, int prec, std::vector<Hogwil
                    h.a.n0, tables.back().p);
         h.a.vtab_l = tables.back().p;
     }
-    typedef void (*BatchKernel)(const HogwildArgs*, const uint32_t*, uint32_t, GridSync, uint32_t, uint32_t);
     static const BatchKernel tab[2][3] = {{k_hogwild_batch<0, 0>, k_hogwild_batch<0, 1>, k_hogwild_batch<0, 2>},
                                           {k_hogwild_batch<5, 0>, k_hogwild_batch<5, 1>, k_hogwild_batch<5, 2>}};
     const BatchKernel k = tab[M == 5 ? 1 : 0][prec];
-    int per_sm = 0;
-    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0));
-    const uint64_t resident = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)ctx->num_sms * 128u;
-    uint64_t want = 0;
-    for (const auto& h : runs) want += h.T;
-    const uint64_t nruns = runs.size();
-    if (want > resident) {
-        const uint64_t room = resident > nruns ? resident - nruns : 0;
-        for (auto& h : runs) h.T = (uint32_t)(1 + (uint64_t)h.T * room / want);
+    uint64_t want = 0, nodes = 0;
+    for (const auto& h : runs) {
+        want += h.T;
+        nodes += h.nl;
     }
-    std::vector<uint32_t> prefix(nruns + 1, 0);
-    for (size_t x = 0; x < nruns; ++x) {
-        prefix[x + 1] = prefix[x] + runs[x].T;
-        runs[x].refresh = runs[x].T;  // a run's copies are rewritten by its own threads
-    }
-    DBuf<HogwildArgs> druns(ctx, nruns);
-    DBuf<uint32_t> dprefix(ctx, nruns + 1);
-    h2d(ctx, druns.p, runs.data(), nruns);
-    h2d(ctx, dprefix.p, prefix.data(), nruns + 1);
-    const uint32_t grid = (prefix[nruns] + 127) / 128;
-    SyncBuf sb(ctx, epochs);
-    {
-        ProfSpan span(ctx, DRG_PROF_EPOCH, samples, 1);
-        if (!launch_cooperative(ctx, "k_hogwild_batch", k, grid, 128, druns.p, dprefix.p, (uint32_t)nruns,
-                                sb.sync(grid * 4, kEpochLag, kGateTimeoutNs), 0u, epochs)) {
-            span.count = epochs;
-            for (uint32_t t = 0; t < epochs; ++t)
-                DRG_LAUNCH(ctx, k, grid, 128, 0, druns.p, dprefix.p, (uint32_t)nruns,
-                           GridSync{nullptr, nullptr, grid, 0, 0}, t, 1u);
+    TuneChoice c = kTuneDefault;
+    const TuneKey key{ctx->device, 1, prec, 1, M == 5 ? 5u : 0u, bitlen32(want)};
+    if (ctx->autotune && epochs >= kTuneMinEpochs && !tune_lookup(key, c)) {
+        // every candidate block size on scratch copies of all runs' positions
+        DBuf<float2> Yt(ctx, nodes);
+        DBuf<uint32_t> Yht;
+        if (prec) Yht = DBuf<uint32_t>(ctx, nodes);
+        std::vector<HogwildArgs> trial = runs;
+        uint64_t off = 0;
+        for (auto& h : trial) {
+            d2d(ctx, Yt.p + off, h.a.Y, h.nl);
+            h.a.Y = Yt.p + off;
+            if (prec) {
+                h.a.Yh = Yht.p + off;
+                refresh_half(ctx, prec, h.a.Y, const_cast<void*>(h.a.Yh), h.nl);
+            }
+            h.epochs = kTuneEpochs;
+            off += h.nl;
         }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        DRG_CUDA(cudaEventCreate(&e0));
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            fail(DRG_ECUDA, "cudaEventCreate failed");
+        }
+        TuneChoice best{kTuneDefault.block, 1, 3.4e38f};
+        try {
+            for (uint32_t block : kTuneBlocks) {
+                DRG_CUDA(cudaEventRecord(e0, ctx->stream));
+                run_hogwild_batch(ctx, k, trial, block, kTuneEpochs);
+                DRG_CUDA(cudaEventRecord(e1, ctx->stream));
+                DRG_CUDA(cudaEventSynchronize(e1));
+                float t = 0.f;
+                DRG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                t /= (float)kTuneEpochs;
+                if (t < best.ms) best = TuneChoice{block, 1, t};
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c = best;
+        tune_store(key, c);
     }
-    sb.check(ctx);
+    ProfSpan span(ctx, DRG_PROF_EPOCH, samples, 1);
+    span.count = run_hogwild_batch(ctx, k, runs, c.block, epochs);
 }
 
 // Gate check: `blocks` one-warp blocks run `rounds` empty epochs through
@@ -1202,6 +1420,7 @@ struct WorkerCtx {
         c.num_sms = parent->num_sms;
         c.max_smem_optin = parent->max_smem_optin;
         c.direct_launch = parent->direct_launch;
+        c.autotune = parent->autotune;
         c.bfs_stage_limit = parent->bfs_stage_limit;
         DRG_CUDA(cudaSetDevice(c.device));
         DRG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));

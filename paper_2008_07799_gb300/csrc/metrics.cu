@@ -120,19 +120,21 @@ __device__ __forceinline__ bool crosses(const SegQ& s, uint2 se, const SegQ& t, 
 }
 
 constexpr uint32_t kCrossTile = 256;
+constexpr uint64_t kCrossPairsPerLaunch = 1ull << 21;  // tile pairs per launch (2^37 pair tests)
+constexpr uint32_t kCrossMaxEdges = 1u << 23;
 
-// All pairs of edges, as pairs of tiles (I <= J) taken from a persistent
-// grid: tile pair p is (I, J) with J(J+1)/2 <= p < (J+1)(J+2)/2, I = p -
-// J(J+1)/2.  Thread x of a block owns edge I*256 + x and tests it against
-// every edge of tile J (staged in shared memory) with a larger index.
+// Tile pairs [p0, p1) of all pairs of edges, taken from a persistent grid:
+// tile pair p is (I, J) with J(J+1)/2 <= p < (J+1)(J+2)/2, I = p - J(J+1)/2.
+// Thread x of a block owns edge I*256 + x and tests it against every edge of
+// tile J (staged in shared memory) with a larger index.
 __global__ void __launch_bounds__(kCrossTile) k_crossings(const SegQ* __restrict__ seg, const uint2* __restrict__ ends,
-                                                           uint32_t m, uint64_t pairs,
+                                                           uint32_t m, uint64_t p0, uint64_t p1,
                                                            unsigned long long* __restrict__ total) {
     __shared__ SegQ ts[kCrossTile];
     __shared__ uint2 te[kCrossTile];
     __shared__ unsigned long long wsum[kCrossTile / 32];
     unsigned long long acc = 0;
-    for (uint64_t p = blockIdx.x; p < pairs; p += gridDim.x) {
+    for (uint64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
         uint64_t J = (uint64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
         while (J * (J + 1) / 2 > p) --J;
         while ((J + 1) * (J + 2) / 2 <= p) ++J;
@@ -210,6 +212,8 @@ void crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* c_o
     DRG_LAUNCH(ctx, k_upper_count, gt, 256, 0, g->rp, g->col, n, cnt.p);
     scan<uint32_t>(ctx, LoadArr<uint32_t>{cnt.p}, n, off.p, false, m_dev.p);
     const uint32_t m = read1(ctx, m_dev.p);
+    DRG_CHECK(m <= kCrossMaxEdges, DRG_EUNSUPPORTED,
+              "crossing count limited to 8388608 edges (all-pairs test, about 80 s at that size)");
     DBuf<unsigned long long> acc(ctx, 2);
     DRG_CUDA(cudaMemsetAsync(acc.p, 0, 2 * sizeof(unsigned long long), ctx->stream));
     DRG_LAUNCH(ctx, k_adjacent_pairs, gt, 256, 0, g->rp, n, acc.p + 1);
@@ -218,10 +222,15 @@ void crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* c_o
         DBuf<uint2> ends(ctx, m);
         DRG_LAUNCH(ctx, k_edge_list, gt, 256, 0, g->rp, g->col, n, off.p, cnt.p, Y, lo[0], span[0], lo[1], span[1],
                    seg.p, ends.p);
+        // bounded launches: at most kCrossPairsPerLaunch tile pairs (2^37
+        // pair tests, about a third of a second) each
         const uint64_t tiles = (m + kCrossTile - 1) / kCrossTile;
         const uint64_t pairs = tiles * (tiles + 1) / 2;
-        const uint32_t grid = (uint32_t)std::min<uint64_t>(pairs, (uint64_t)ctx->num_sms * 8);
-        DRG_LAUNCH(ctx, k_crossings, grid, kCrossTile, 0, seg.p, ends.p, m, pairs, acc.p);
+        for (uint64_t p0 = 0; p0 < pairs; p0 += kCrossPairsPerLaunch) {
+            const uint64_t p1 = std::min<uint64_t>(pairs, p0 + kCrossPairsPerLaunch);
+            const uint32_t grid = (uint32_t)std::min<uint64_t>(p1 - p0, (uint64_t)ctx->num_sms * 8);
+            DRG_LAUNCH(ctx, k_crossings, grid, kCrossTile, 0, seg.p, ends.p, m, p0, p1, acc.p);
+        }
     }
     unsigned long long h[2];
     DRG_CUDA(cudaMemcpyAsync(h, acc.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));

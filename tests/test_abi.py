@@ -77,6 +77,8 @@ def test_status_strings_and_null_arguments(drg):
     assert L.drg_layout(None, None, None, None) == 1
     assert L.drg_kernel_launches(None) == 0
     assert L.drg_probe_memory(None, 0, 1 << 25, 1000, 1, None, None) == 1
+    assert L.drg_autotune_enable(None, 1) == 1
+    assert L.drg_autotune_read(0, None, None, None, None) == 1
 
 
 def test_missing_library_fails_loudly():
