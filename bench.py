@@ -308,6 +308,7 @@ def make_params(drg, wl, args, gid):
     p.coarsen = {"hem": 0, "star": 1}[args.coarsen]
     p.level_tables = 1 if args.level_tables else 0
     p.perplexity = args.perplexity
+    p.row_cap = args.row_cap
     return p
 
 
@@ -468,6 +469,9 @@ def main():
                     help="each coarse level samples its own distance matrix and tables (the conventional "
                          "multilevel scheme) instead of G^0's through the ancestor map")
     ap.add_argument("--substeps", type=int, default=None, help="override the in-flight bound n_l / substeps (profiling cases)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the level kernels' default launch shape")
+    ap.add_argument("--row-cap", type=int, default=0,
+                    help="> 0: every row of the distance matrix keeps its row-cap nearest nodes (pattern K u K^T)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -502,8 +506,11 @@ def main():
         wl["desc"] += "; each coarse level samples its own distance matrix and tables"
     if args.perplexity > 0:
         wl["desc"] += f"; sigma_i per node at perplexity {args.perplexity:g}"
+    if args.row_cap > 0:
+        wl["desc"] += f"; rows capped to their {args.row_cap} nearest nodes (pattern K u K^T)"
     stream = torch.cuda.current_stream()
     ctx = drg.Context(local, stream.cuda_stream)
+    ctx.autotune(not args.no_autotune)
     p = make_params(drg, wl, args, gid=rank)
     probes = None if args.once else measure_probes(drg, ctx)
     job = Job(drg, ctx, wl, p, np, torch)
@@ -589,7 +596,7 @@ def main():
     coarse = max(ep_samples - s0, 0)
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
     kname = epoch_kernel(wl["graph"], args.mode, args.precision)
-    tps = None if (args.level_tables or args.perplexity > 0) else ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
+    tps = None if (args.level_tables or args.perplexity > 0 or args.row_cap > 0) else ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
                                          "mode": args.mode, "precision": args.precision,
                                          "multilevel": bool(wl.get("multilevel", 1))})
     avg_launch_samples = ep_samples / max(ep_launches, 1)
@@ -622,7 +629,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "mode": args.mode, "precision": args.precision,
                    "coarsen": args.coarsen, "level_tables": bool(args.level_tables),
-                   "perplexity": args.perplexity, "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
+                   "perplexity": args.perplexity, "row_cap": args.row_cap, "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
                    "samples_per_step": samples_per_step, "layout_time_ms": ms,
                    "l2": "1 GiB buffer written between timed steps (flush)",
                    "parallelism": f"replicas x{world}"},
@@ -630,6 +637,7 @@ def main():
         "phases_note": "CUDA-event timers of one profiled step, in which builds that the timed steps run "
                        "concurrently (hierarchy beside the distance matrix; a batch's graphs) run one after another",
         "gpu_launches": launches,
+        "autotune": drg.autotune_table(),
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 2 * m * 4,
                 "d2h_bytes_per_step": 2 * n * 4, "seconds_per_step": e2e_s},

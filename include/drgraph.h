@@ -100,6 +100,8 @@ typedef struct {
                                 level runs and freed after it (the conventional scheme) */
     float perplexity;        /* whole-path runs: > 0 sets sigma_i of Eq. 9 per node by this
                                 perplexity (drg_build_distance_matrix_ex); 0 uses sigma */
+    uint32_t row_cap;        /* whole-path runs: > 0 caps every row of the distance matrix to its
+                                row_cap nearest nodes (drg_build_distance_matrix_capped); 0: none */
 } drg_params;
 
 /* Mode and precision values. */
@@ -204,6 +206,25 @@ drg_status drg_dmat_download_range(drg_ctx* ctx, const drg_dmat* d, uint64_t e_b
  * or non-finite perplexity or one of 4.2e9 or more.  Synchronises. */
 drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity,
                                         drg_dmat** out);
+/* drg_build_distance_matrix with a per-row neighbour cap, for graphs whose
+ * k-order rows do not fit in memory (Sec. 3.2.1 notes that large k becomes
+ * infeasible).  Row i keeps K_i, its row_cap nearest nodes of NNG(v_i, k) by
+ * (hop distance, node id): all nodes of the levels whose cumulative count
+ * stays below row_cap, then the smallest ids of the next level.  The matrix's
+ * pattern is the union K u K^T (an entry (i, j) for j in K_i or i in K_j,
+ * rows sorted by j, dist the hop distance); the similarity of Eq. 9 is taken
+ * over each row's kept set, Z_i = sum over d = 1..k of count of K_i at
+ * distance d times g(d) (FP32, in order), and Eq. 4 symmetrises it over the
+ * union:
+ *   q[e] = floor((a + b) * 2^30), a = fl(g(d)/Z_i) when j is in K_i, else 0,
+ *                                 b = fl(g(d)/Z_j) when i is in K_j, else 0;
+ * r, the node table and the edge table as drg_build_distance_matrix.  With
+ * row_cap at least the longest row it is that matrix bit for bit.  The
+ * traversal stops at the level that fills the cap, so k = 3 stays feasible
+ * where the full rows are not.  DRG_EINVAL for row_cap = 0;
+ * DRG_EUNSUPPORTED when the kept entries reach 2^31.  Synchronises. */
+drg_status drg_build_distance_matrix_capped(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma,
+                                            uint32_t row_cap, drg_dmat** out);
 /* Host copy of beta_i = 1/(2 sigma_i^2) of every node (n doubles; 0 for an
  * empty row) of a perplexity-calibrated matrix; DRG_EINVAL for a matrix
  * built with a global sigma.  Synchronises. */

@@ -39,6 +39,7 @@ EXPORTS = [
     "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
     "drg_build_distance_matrix_ex", "drg_dmat_calibration", "drg_crossings", "drg_min_angle",
     "drg_probe_memory", "drg_autotune_enable", "drg_autotune_read", "drg_autotune_clear",
+    "drg_build_distance_matrix_capped",
 ]
 
 PROBE_LOAD8, PROBE_LOAD16, PROBE_RED8, PROBE_LOAD16_EVICT_FIRST, PROBE_COPY = range(5)
@@ -61,7 +62,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("gid", C.c_uint32), ("mode", C.c_int32), ("precision", C.c_int32),
         ("substeps", C.c_uint32), ("stop_nodes", C.c_uint32), ("match_rounds", C.c_uint32),
         ("max_levels", C.c_uint32), ("multilevel", C.c_int32), ("coarsen", C.c_int32),
-        ("level_tables", C.c_int32), ("perplexity", C.c_float),
+        ("level_tables", C.c_int32), ("perplexity", C.c_float), ("row_cap", C.c_uint32),
     ]
 
     @classmethod
@@ -114,6 +115,7 @@ def lib():
         "drg_dmat_destroy": (st, [VP]),
         "drg_build_distance_matrix_ex": (st, [VP, VP, C.c_uint32, C.c_float, C.c_float, C.POINTER(VP)]),
         "drg_dmat_calibration": (st, [VP, VP, VP]),
+        "drg_build_distance_matrix_capped": (st, [VP, VP, C.c_uint32, C.c_float, C.c_uint32, C.POINTER(VP)]),
         "drg_crossings": (st, [VP, VP, VP, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
         "drg_min_angle": (st, [VP, VP, VP, C.POINTER(C.c_double)]),
         "drg_dmat_download_range": (st, [VP, VP, C.c_uint64, C.c_uint64, VP, VP, VP, VP, VP]),
@@ -369,11 +371,14 @@ def graph_from_edges(ctx: Context, n, src, dst) -> Graph:
 
 
 def build_distance_matrix(ctx: Context, g: Graph, k: int, sigma: float = 1.0,
-                          perplexity: float = 0.0) -> DistanceMatrix:
+                          perplexity: float = 0.0, row_cap: int = 0) -> DistanceMatrix:
     """perplexity > 0: sigma_i per node calibrated to that perplexity (any
-    other non-zero value is refused by the library)."""
+    other non-zero value is refused by the library); row_cap > 0: every row
+    keeps its row_cap nearest nodes, pattern K u K^T."""
     h = VP()
-    if perplexity != 0.0:
+    if row_cap:
+        ctx.check(lib().drg_build_distance_matrix_capped(ctx.h, g.h, int(k), float(sigma), int(row_cap), C.byref(h)))
+    elif perplexity != 0.0:
         ctx.check(lib().drg_build_distance_matrix_ex(ctx.h, g.h, int(k), float(sigma), float(perplexity),
                                                      C.byref(h)))
     else:

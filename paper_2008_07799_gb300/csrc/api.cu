@@ -161,6 +161,7 @@ void drg_params_default(drg_params* p) {
     p->coarsen = DRG_COARSEN_HEM;
     p->level_tables = 0;
     p->perplexity = 0.f;
+    p->row_cap = 0;
 }
 
 const char* drg_status_string(drg_status s) {
@@ -322,6 +323,15 @@ drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32
     *out = nullptr;
     API_TRY
     *out = drg::build_dmat(ctx, g, k, sigma, perplexity);
+    API_CATCH(ctx)
+}
+
+drg_status drg_build_distance_matrix_capped(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma,
+                                            uint32_t row_cap, drg_dmat** out) {
+    if (!ctx || !g || !out || row_cap == 0) return DRG_EINVAL;
+    *out = nullptr;
+    API_TRY
+    *out = drg::build_dmat(ctx, g, k, sigma, 0.f, row_cap);
     API_CATCH(ctx)
 }
 

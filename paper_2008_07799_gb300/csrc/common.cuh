@@ -102,6 +102,7 @@ struct drg_dmat {
     uint64_t nnz = 0;
     float sigma = 1.f;
     float perplexity = 0.f;      // > 0: sigma_i calibrated per node (beta below)
+    uint32_t row_cap = 0;        // > 0: rows capped to their row_cap nearest nodes, pattern K u K^T
     uint32_t shift = 0;
     uint64_t* rp = nullptr;      // [n + 1]
     uint32_t* col = nullptr;     // [nnz]
@@ -282,7 +283,8 @@ void build_csr_from_keys(drg_ctx* ctx, uint32_t n, uint64_t* keys, uint32_t* val
 drg_graph* graph_from_edges(drg_ctx* ctx, uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                             bool on_device);
 void graph_free(drg_graph* g);
-drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity = 0.f);
+drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity = 0.f,
+                     uint32_t row_cap = 0);
 void crossings(drg_ctx* ctx, const drg_graph* g, const float* pos, uint64_t* c, double* crosslessness);
 double min_angle(drg_ctx* ctx, const drg_graph* g, const float* pos);
 void dmat_free(drg_dmat* d);

@@ -29,7 +29,10 @@ __global__ void k_expand_rows(const uint64_t* __restrict__ rp, uint32_t n, uint3
 // an atomic cursor (one traversal gives the counts and the rows); direct mode
 // writes at the final row offsets and is the fallback when the staging area
 // overflows.
-constexpr int BFS_THREADS = 512;
+#ifndef DRG_BFS_THREADS
+#define DRG_BFS_THREADS 512
+#endif
+constexpr int BFS_THREADS = DRG_BFS_THREADS;
 
 struct BfsArgs {
     const uint64_t* rp;
@@ -50,6 +53,7 @@ struct BfsArgs {
     uint64_t cap;             // staged: staging capacity
     uint64_t* row_off;        // staged: staging offset of each row
     uint32_t* overflow;       // staged: set when a row did not fit
+    uint32_t row_cap;         // > 0: each row keeps its row_cap nearest nodes by (hop distance, id) (k_bfs<false>)
     const uint64_t* gd_rp;    // direct: row offsets
     uint32_t* out_col;        // staging or final column array
     uint8_t* out_dist;        // staging or final distance array
@@ -94,8 +98,17 @@ __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t v) {
     if (!(*(volatile uint32_t*)&summ[w >> 5] & sbit)) atomicOr(&summ[w >> 5], sbit);
 }
 
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, off);
+        if (lane >= (uint32_t)off) v += t;
+    }
+    return v;
+}
+
 template <bool K2>
-__global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
+__global__ void __launch_bounds__(BFS_THREADS, 1024 / BFS_THREADS) k_bfs(BfsArgs a) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint64_t s_off[BFS_THREADS];
     __shared__ uint64_t s_start[BFS_THREADS];
@@ -146,7 +159,8 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
         __syncthreads();
         uint32_t lo = 0, hi = s_len;
         __syncthreads();
-        for (uint32_t d = 2; d <= a.k && lo < hi; ++d) {
+        // with a row cap: no further level once the levels so far hold cap nodes
+        for (uint32_t d = 2; d <= a.k && lo < hi && !(a.row_cap && hi >= a.row_cap); ++d) {
             for (uint32_t c = lo; c < hi; c += BFS_THREADS) {
                 const uint32_t idx = c + threadIdx.x;
                 uint64_t deg = 0, start = 0;
@@ -163,19 +177,27 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
                 const uint32_t cnt = (hi - c) < (uint32_t)BFS_THREADS ? (hi - c) : (uint32_t)BFS_THREADS;
                 const bool store = d < a.k;
                 for (uint64_t x0 = 0; x0 < tot; x0 += (uint64_t)BFS_UNROLL * BFS_THREADS) {
+                    // each thread takes BFS_UNROLL consecutive slots of the
+                    // concatenated adjacency: one search for the owner of the
+                    // first (the last frontier slot whose offset is <= x),
+                    // then a walk forward for the others
                     uint32_t v[BFS_UNROLL];
+                    const uint64_t xb = x0 + (uint64_t)threadIdx.x * BFS_UNROLL;
+                    uint32_t own = 0;
+                    if (xb < tot) {
+                        uint32_t hi2 = cnt;
+                        while (hi2 - own > 1) {
+                            const uint32_t mid = (own + hi2) >> 1;
+                            if (s_off[mid] <= xb) own = mid; else hi2 = mid;
+                        }
+                    }
 #pragma unroll
                     for (int u = 0; u < BFS_UNROLL; ++u) {
-                        const uint64_t x = x0 + (uint64_t)u * BFS_THREADS + threadIdx.x;
+                        const uint64_t x = xb + u;
                         v[u] = 0xFFFFFFFFu;
                         if (x < tot) {
-                            // owner: last frontier slot whose offset is <= x
-                            uint32_t lo2 = 0, hi2 = cnt;
-                            while (hi2 - lo2 > 1) {
-                                const uint32_t mid = (lo2 + hi2) >> 1;
-                                if (s_off[mid] <= x) lo2 = mid; else hi2 = mid;
-                            }
-                            v[u] = a.col[s_start[lo2] + (x - s_off[lo2])];
+                            while (own + 1 < cnt && s_off[own + 1] <= x) ++own;
+                            v[u] = a.col[s_start[own] + (x - s_off[own])];
                         }
                     }
                     if (K2 && !store) {
@@ -230,6 +252,53 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
         const uint64_t wper = (nw + NW - 1) / NW;
         const uint64_t w0 = (uint64_t)warp * wper < nw ? (uint64_t)warp * wper : nw;
         const uint64_t w1 = w0 + wper < nw ? w0 + wper : nw;
+        if (!K2 && a.row_cap && hi > a.row_cap) {
+            // row cap: the levels before the last ([0, lo) of the list, fewer
+            // than cap nodes) stay whole; of the last level only its cap - lo
+            // smallest ids.  Unmark the earlier levels, cut the bitmap after
+            // its (cap - lo)-th set bit in id order, mark them again.
+            const uint32_t keep = a.row_cap - lo;
+            for (uint32_t x = threadIdx.x; x < lo; x += BFS_THREADS) {
+                const uint32_t v = list[x];
+                atomicAnd(&bm[v >> 5], ~(1u << (v & 31)));
+            }
+            __syncthreads();
+            uint32_t cwc = 0;
+            for (uint64_t x = w0 + lane; x < w1; x += 32) cwc += __popc(bm[wlist[x]]);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) cwc += __shfl_xor_sync(0xFFFFFFFFu, cwc, off);
+            if (lane == 0) s_wcnt[warp] = cwc;
+            __syncthreads();
+            uint32_t before = 0;  // last-level nodes in the words of earlier warps
+            for (uint32_t w = 0; w < warp; ++w) before += s_wcnt[w];
+            for (uint64_t x0 = w0; x0 < w1; x0 += 32) {
+                const uint64_t x = x0 + lane;
+                const uint32_t wi = x < w1 ? wlist[x] : 0u;
+                const uint32_t w = x < w1 ? bm[wi] : 0u;
+                const uint32_t c = __popc(w);
+                const uint32_t incl = warp_incl_scan(c, lane);
+                const uint32_t excl = before + incl - c;
+                if (x < w1 && excl + c > keep) {
+                    // keep only the first keep - excl bits of this word (none when excl >= keep)
+                    uint32_t m = w, left = excl < keep ? keep - excl : 0u;
+                    uint32_t kept = 0;
+                    while (m && left) {
+                        const uint32_t b = m & (0u - m);
+                        kept |= b;
+                        m ^= b;
+                        --left;
+                    }
+                    bm[wi] = kept;
+                }
+                before += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            }
+            __syncthreads();
+            for (uint32_t x = threadIdx.x; x < lo; x += BFS_THREADS) {
+                const uint32_t v = list[x];
+                atomicOr(&bm[v >> 5], 1u << (v & 31));
+            }
+            __syncthreads();
+        }
         uint32_t cw = 0;
         for (uint64_t x = w0 + lane; x < w1; x += 32) cw += __popc(bm[wlist[x]]);
 #pragma unroll
@@ -349,14 +418,6 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(BfsArgs a) {
 constexpr uint32_t SMALL_CAP = 2048;
 constexpr int SMALL_WARPS = 8;
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, off);
-        if (lane >= (uint32_t)off) v += t;
-    }
-    return v;
-}
 
 __global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
     extern __shared__ uint32_t small_smem[];
@@ -567,10 +628,10 @@ struct DegSq {
 // aligned 16-byte pieces (bytes outside the row are masked).
 static size_t dist_bytes(uint64_t nnz) { return (size_t)((nnz + 15) / 16 + 1) * 16; }
 
-static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat* d) {
+static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat* d, uint32_t row_cap) {
     const uint32_t n = g->n;
     d->rp = static_cast<uint64_t*>(dalloc(ctx, sizeof(uint64_t) * ((size_t)n + 1)));
-    if (k == 1) {
+    if (k == 1 && row_cap == 0) {
         // NNG(v_i, 1) is the adjacency itself, already sorted by column
         d->nnz = g->nnz;
         d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (d->nnz ? d->nnz : 1)));
@@ -580,7 +641,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         DRG_LAUNCH(ctx, k_fill_u8, grid_for(d->nnz, 256, 65536), 256, 0, d->dist, d->nnz, (uint8_t)1);
         return;
     }
-    const bool k2 = k == 2;
+    const bool k2 = k == 2 && row_cap == 0;  // capped rows take the general kernel (it knows every hop distance)
     auto kern = k2 ? k_bfs<true> : k_bfs<false>;
     const uint32_t words = (n + 31) / 32;
     const uint32_t swords = (words + 31) / 32;
@@ -622,6 +683,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         cap = read1(ctx, s2.p);
     }
     if (!k2) cap *= 4;  // a guess: rows that overflow it are traversed again
+    if (row_cap) cap = std::min<uint64_t>(cap, (uint64_t)n * row_cap);  // no row holds more
     if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
     cap += 16ull * n;  // each staged row is padded to a multiple of 16 entries
     if (ctx->bfs_stage_limit >= 0 && (uint64_t)ctx->bfs_stage_limit < cap) cap = (uint64_t)ctx->bfs_stage_limit;
@@ -647,6 +709,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     a.next_row = counter.p; a.counts = counts.p;
     a.staged = 1; a.cursor = cursor.p; a.cap = cap; a.row_off = row_off.p; a.overflow = overflow.p;
     a.out_col = scol.p; a.out_dist = sdist.p;
+    a.row_cap = row_cap;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(overflow.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(cursor.p, 0, 8, ctx->stream));
@@ -706,10 +769,99 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
 }
 
-// ------------------------------------------------------------------ similarity
 struct Gauss {
     float g[16];
 };
+
+// ------------------------------------------------------------------ row cap: the union pattern
+// Kept rows K (each row's row_cap nearest nodes) -> the sampling pattern
+// K u K^T: every kept pair in both orientations, sorted by (row, column), the
+// equal keys of a pair kept in both rows merged; each entry of the union
+// carries flag 1 (j in K_i, "own") and / or flag 2 (i in K_j, "back").
+__global__ void k_cap_pairs(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
+                            const uint8_t* __restrict__ dist, uint64_t nK, uint32_t cb, uint64_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nK; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = esrc[e], j = col[e];
+        const uint32_t dd = dist[e];
+        keys[2 * e] = (i << cb) | j;
+        vals[2 * e] = dd | 0x100u;
+        keys[2 * e + 1] = (j << cb) | i;
+        vals[2 * e + 1] = dd | 0x200u;
+    }
+}
+
+__global__ void k_cap_heads(const uint64_t* __restrict__ keys, uint64_t m, uint32_t* __restrict__ head) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < m; x += (uint64_t)gridDim.x * blockDim.x)
+        head[x] = (x == 0 || keys[x] != keys[x - 1]) ? 1u : 0u;
+}
+
+// The first key of each run (a run holds one pair, once or twice) writes the
+// union entry at its place pos[x]; rows are counted for the row pointers.
+__global__ void k_cap_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                             const uint32_t* __restrict__ head, const uint32_t* __restrict__ pos, uint64_t m,
+                             uint32_t cb, uint32_t* __restrict__ ucol, uint8_t* __restrict__ udist,
+                             uint8_t* __restrict__ uflag, unsigned long long* __restrict__ rowcnt) {
+    const uint64_t mask = (1ull << cb) - 1;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < m; x += (uint64_t)gridDim.x * blockDim.x) {
+        if (!head[x]) continue;
+        uint32_t f = vals[x] >> 8;
+        if (x + 1 < m && keys[x + 1] == keys[x]) f |= vals[x + 1] >> 8;
+        const uint32_t p = pos[x];
+        ucol[p] = (uint32_t)(keys[x] & mask);
+        udist[p] = (uint8_t)(vals[x] & 0xFFu);
+        uflag[p] = (uint8_t)f;
+        atomicAdd(&rowcnt[keys[x] >> cb], 1ull);
+    }
+}
+
+// Z_i of the kept set K_i: sum over d = 1..k of fl32(count of own entries at
+// distance d) * g(d), in that order, FP32 correctly rounded, no fused
+// multiply-add (one warp per row).
+__global__ void k_row_Z_own(const uint64_t* __restrict__ rp, const uint8_t* __restrict__ dist,
+                            const uint8_t* __restrict__ flag, uint32_t n, uint32_t k, Gauss gs, float* __restrict__ Z) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        uint32_t cnt[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) cnt[c] = 0;
+        for (uint64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+            if (!(flag[e] & 1u)) continue;
+            const uint32_t dd = dist[e];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) cnt[c] += (dd == (uint32_t)(c + 1)) ? 1u : 0u;
+        }
+        float z = 0.f;
+        for (uint32_t c = 0; c < k; ++c) {
+            uint32_t t = cnt[c];
+#pragma unroll
+            for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+            z = __fadd_rn(z, __fmul_rn((float)t, gs.g[c]));
+        }
+        if (lane == 0) Z[i] = z;
+    }
+}
+
+// q over the union: fl32(a + b) 2^30 truncated, a = fl32(g/Z_i) when the
+// entry is in K_i, b = fl32(g/Z_j) when it is in K_j, each else 0; r_i the
+// row sums (r must start at zero).
+__global__ void k_quantise_flags(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
+                                 const uint8_t* __restrict__ dist, const uint8_t* __restrict__ flag,
+                                 const float* __restrict__ Z, Gauss gs, uint64_t nnz, uint32_t* __restrict__ q,
+                                 unsigned long long* __restrict__ r) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = esrc[e], j = col[e], f = flag[e];
+        const float g = gs.g[dist[e] - 1];
+        const float av = (f & 1u) ? __fdiv_rn(g, Z[i]) : 0.f;
+        const float bv = (f & 2u) ? __fdiv_rn(g, Z[j]) : 0.f;
+        const uint32_t qe = __float2uint_rz(__fmul_rn(__fadd_rn(av, bv), 1073741824.0f));
+        q[e] = qe;
+        atomicAdd(&r[i], (unsigned long long)qe);
+    }
+}
+
+// ------------------------------------------------------------------ similarity
 
 // Bytes [lo, hi) of a 16-byte piece, as a mask per 32-bit word q.
 __device__ __forceinline__ uint32_t byte_mask(uint32_t q, uint32_t lo, uint32_t hi) {
@@ -1404,8 +1556,54 @@ void dmat_free(drg_dmat* d) {
     delete d;
 }
 
-drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity) {
+// Replaces d's kept rows K by the union pattern K u K^T (rows, columns,
+// distances) and returns each union entry's flags (1: own, 2: back).
+static DBuf<uint8_t> cap_union(drg_ctx* ctx, drg_dmat* d) {
+    const uint32_t n = d->n;
+    const uint64_t nK = d->nnz;
+    DRG_CHECK(2 * nK < (1ull << 32), DRG_EUNSUPPORTED, "the capped rows hold 2^31 entries or more");
+    const uint64_t m = 2 * nK;
+    const uint32_t cb = (uint32_t)std::max(1, bitlen(n > 1 ? n - 1 : 1));
+    DBuf<uint64_t> keys(ctx, m), kalt(ctx, m);
+    DBuf<uint32_t> vals(ctx, m), valt(ctx, m);
+    {
+        DBuf<uint32_t> esrc(ctx, nK);
+        DRG_LAUNCH(ctx, k_expand_rows, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, d->rp, n,
+                   esrc.p);
+        DRG_LAUNCH(ctx, k_cap_pairs, grid_for(nK, 256, 65536), 256, 0, esrc.p, d->col, d->dist, nK, cb, keys.p,
+                   vals.p);
+    }
+    uint64_t* kp = keys.p;
+    uint64_t* ap = kalt.p;
+    uint32_t* vp = vals.p;
+    uint32_t* vq = valt.p;
+    radix_sort(ctx, kp, ap, vp, vq, m, 0, (int)(2 * cb));
+    DBuf<uint32_t> head(ctx, m), pos(ctx, m), nu_d(ctx, 1);
+    DRG_LAUNCH(ctx, k_cap_heads, grid_for(m, 256, 65536), 256, 0, kp, m, head.p);
+    scan<uint32_t>(ctx, LoadArr<uint32_t>{head.p}, m, pos.p, false, nu_d.p);
+    const uint32_t nu = read1(ctx, nu_d.p);
+    dfree(ctx, d->col);
+    dfree(ctx, d->dist);
+    d->col = nullptr;
+    d->dist = nullptr;
+    d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (nu ? nu : 1)));
+    d->dist = static_cast<uint8_t*>(dalloc(ctx, dist_bytes(nu)));
+    DRG_CUDA(cudaMemsetAsync(d->dist, 0, dist_bytes(nu), ctx->stream));
+    DBuf<uint8_t> flag(ctx, nu);
+    DBuf<uint64_t> cnt(ctx, n), tot(ctx, 1);
+    DRG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(uint64_t) * n, ctx->stream));
+    DRG_LAUNCH(ctx, k_cap_unique, grid_for(m, 256, 65536), 256, 0, kp, vp, head.p, pos.p, m, cb, d->col, d->dist,
+               flag.p, reinterpret_cast<unsigned long long*>(cnt.p));
+    scan<uint64_t>(ctx, LoadArr<uint64_t>{cnt.p}, n, d->rp, false, tot.p);
+    d2d(ctx, d->rp + n, tot.p, 1);
+    d->nnz = nu;
+    return flag;
+}
+
+drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, float perplexity, uint32_t row_cap) {
     DRG_CHECK(g, DRG_EINVAL, "null graph");
+    DRG_CHECK(row_cap == 0 || perplexity == 0.f, DRG_EUNSUPPORTED,
+              "a row cap together with perplexity-calibrated sigma is not supported");
     DRG_CHECK(k >= 1 && k <= 15, DRG_EINVAL, "k must be in [1, 15]");
     DRG_CHECK(sigma > 0.f, DRG_EINVAL, "sigma must be positive");
     DRG_CHECK(perplexity >= 0.f && perplexity < 4.2e9f, DRG_EINVAL, "perplexity must be in [0, 4.2e9)");
@@ -1418,7 +1616,10 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
     try {
         DRG_CHECK(g->nnz > 0, DRG_EEMPTY, "graph has no edges");
         ProfSpan span(ctx, DRG_PROF_DMAT, 0);
-        build_korder(ctx, g, k, d);
+        build_korder(ctx, g, k, d, row_cap);
+        DBuf<uint8_t> flag;  // row cap: own / back flag of every union entry
+        if (row_cap) flag = cap_union(ctx, d);
+        d->row_cap = row_cap;
         span.units = d->nnz;
         const uint32_t n = d->n;
         const uint64_t nnz = d->nnz;
@@ -1441,19 +1642,25 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
             DRG_LAUNCH(ctx, k_row_Z<true>, gw, 256, 0, d->rp, d->dist, n, k, gs, d->Z, cnt.p);
             DRG_LAUNCH(ctx, k_calibrate, grid_for(n, 128, (uint32_t)ctx->num_sms * 16), 128, 0, cnt.p, n, k,
                        (double)perplexity, P, d->beta, d->Z, W.p);
+        } else if (row_cap) {
+            DRG_LAUNCH(ctx, k_row_Z_own, gw, 256, 0, d->rp, d->dist, flag.p, n, k, gs, d->Z);
         } else {
             DRG_LAUNCH(ctx, k_row_Z<false>, gw, 256, 0, d->rp, d->dist, n, k, gs, d->Z, (uint32_t*)nullptr);
         }
         DBuf<uint32_t> esrc(ctx, nnz);
         DRG_LAUNCH(ctx, k_expand_rows, gw, 256, 0, d->rp, n, esrc.p);
         DRG_CUDA(cudaMemsetAsync(d->r, 0, sizeof(uint64_t) * n, ctx->stream));
-        if (perplexity > 0.f)
+        if (row_cap)
+            DRG_LAUNCH(ctx, k_quantise_flags, grid_for(nnz, 256, 65536), 256, 0, esrc.p, d->col, d->dist, flag.p,
+                       d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r));
+        else if (perplexity > 0.f)
             DRG_LAUNCH(ctx, k_quantise_r<true>, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist,
                        d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r), (const float*)W.p, k);
         else
             DRG_LAUNCH(ctx, k_quantise_r<false>, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist,
                        d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r), (const float*)nullptr, k);
         W.reset();
+        flag.reset();
         DBuf<unsigned long long> rmax(ctx, 1);
         DRG_CUDA(cudaMemsetAsync(rmax.p, 0, 8, ctx->stream));
         DRG_LAUNCH(ctx, k_rmax, grid_for(n, 256, (uint32_t)ctx->num_sms * 8), 256, 0, d->r, n, rmax.p);

@@ -377,16 +377,24 @@ struct Resolved {
     uint32_t ia, ic, jm[MT];
 };
 
+// The sample's random words: call 0 first, so that the edge record (the one
+// access that goes to HBM) is requested before anything else; the other
+// calls are independent chains computed side by side.
 template <int MT, bool ANC>
 __device__ __forceinline__ void hw_request(const EpochArgs& a, uint32_t s, uint32_t t, Requested<MT, ANC>& r) {
-    Words W(s, t, a.tag, a.key);
-    const uint64_t R = (uint64_t)W(0) | ((uint64_t)W(1) << 32);
-    r.Ue = W(2);
+    constexpr int kCalls = (3 + 3 * MT + 3) / 4;  // words 0 .. 2 + 3 MT
+    uint4 w[kCalls];
+    w[0] = philox(make_uint4(s, t, a.tag, 0u), a.key);
+    const uint64_t R = (uint64_t)w[0].x | ((uint64_t)w[0].y << 32);
+    r.Ue = w[0].z;
     load_edge(a, alias_bucket(R, a.nnz), r.e, r.j1);
 #pragma unroll
+    for (int c = 1; c < kCalls; ++c) w[c] = philox(make_uint4(s, t, a.tag, (uint32_t)c), a.key);
+#pragma unroll
     for (int m = 0; m < MT; ++m) {
-        const uint64_t Rm = (uint64_t)W(3 + 3 * m) | ((uint64_t)W(4 + 3 * m) << 32);
-        r.Uv[m] = W(5 + 3 * m);
+        const int w0 = 3 + 3 * m, w1 = 4 + 3 * m, w2 = 5 + 3 * m;
+        const uint64_t Rm = (uint64_t)lane_word(w[w0 >> 2], w0 & 3) | ((uint64_t)lane_word(w[w1 >> 2], w1 & 3) << 32);
+        r.Uv[m] = lane_word(w[w2 >> 2], w2 & 3);
         r.bkt[m] = (uint32_t)alias_bucket(Rm, a.n0);
         if constexpr (ANC) r.v[m] = __ldg(&a.vtab_l[r.bkt[m]]);
         else r.v[m] = __ldg(&a.vtab[r.bkt[m]]);
@@ -1444,7 +1452,7 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
     std::unique_ptr<WorkerCtx> hw;  // owns h when built concurrently; freed after h
     try {
         if (ctx->prof) {
-            d = build_dmat(ctx, g, p.k, p.sigma, p.perplexity);
+            d = build_dmat(ctx, g, p.k, p.sigma, p.perplexity, p.row_cap);
             h = build_hierarchy(ctx, g, p);
         } else {
             // the hierarchy does not need the distance matrix: a worker thread
@@ -1461,7 +1469,7 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
                 }
             });
             try {
-                d = build_dmat(ctx, g, p.k, p.sigma, p.perplexity);
+                d = build_dmat(ctx, g, p.k, p.sigma, p.perplexity, p.row_cap);
             } catch (...) {
                 th.join();
                 throw;
@@ -1482,7 +1490,7 @@ void layout_full(drg_ctx* ctx, const drg_graph* g, const drg_params& p, float* p
             const float gamma = (l == (int)L && L > 0) ? p.gamma_coarsest : p.gamma;
             if (p.level_tables && l > 0) {
                 // the conventional scheme: this level's own matrix and tables
-                drg_dmat* dl = build_dmat(ctx, h->g[l], p.k, p.sigma, p.perplexity);
+                drg_dmat* dl = build_dmat(ctx, h->g[l], p.k, p.sigma, p.perplexity, p.row_cap);
                 try {
                     layout_level(ctx, dl, h, (uint32_t)l, cur_pos, p, gamma, 0, p.epochs);
                     sync(ctx);
@@ -1586,7 +1594,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
             for (uint32_t g = 0; g < count; ++g) {
                 drg_params q = p;
                 q.gid = g;
-                gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma, p.perplexity);
+                gs[g].d = build_dmat(ctx, graphs[g], p.k, p.sigma, p.perplexity, p.row_cap);
                 gs[g].h = build_hierarchy(ctx, graphs[g], q);
             }
         } else {
@@ -1605,7 +1613,7 @@ void layout_batch(drg_ctx* ctx, uint32_t count, const drg_graph* const* graphs, 
                             if (g >= count || failed.load()) break;
                             drg_params q = p;
                             q.gid = g;
-                            gs[g].d = build_dmat(wc, graphs[g], p.k, p.sigma, p.perplexity);
+                            gs[g].d = build_dmat(wc, graphs[g], p.k, p.sigma, p.perplexity, p.row_cap);
                             gs[g].h = build_hierarchy(wc, graphs[g], q);
                         }
                         sync(wc);

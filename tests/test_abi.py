@@ -47,6 +47,7 @@ def test_params_layout_and_defaults(drg):
     assert p.b == 1.0 and p.lr0 == 1.0 and p.sigma == 1.0 and p.clip == 5.0 and abs(p.rho - 0.8) < 1e-7
     assert p.init_scale == float(np.float32(1e-4))
     assert p.seed == 0 and p.mode == 0 and p.precision == 0 and p.multilevel == 1 and p.coarsen == 0 and p.level_tables == 0 and p.perplexity == 0.0
+    assert p.row_cap == 0
     assert C.sizeof(drg.Params) == 104
 
 

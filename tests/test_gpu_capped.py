@@ -1,0 +1,129 @@
+"""The per-row neighbour cap of the sparse distance matrix on the GPU
+(drg_build_distance_matrix_capped; Sec. 3.2.1 with the cap that keeps large k
+feasible) against the oracle's korder_capped / similarity_capped: the union
+pattern K u K^T, hop distances, Z over each kept set, the quantised weights,
+the row sums and both alias tables bit for bit on small graphs (caps that bind
+at level 1, 2 and 3, ragged inputs, and a cap that does not bind); at full
+size (DC-SBM 1M nodes, k = 3, where the uncapped matrix would exceed 2^32
+entries) sampled rows are checked against single-row traversals of the
+oracle."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def env():
+    import paper_2008_07799_gb300 as drg
+    from paper_2008_07799_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return drg, drg.Context(0, torch.cuda.current_stream().cuda_stream)
+
+
+GRAPHS = {
+    "ba2000": lambda: gg.barabasi_albert(2000, 3, 11),
+    "grid32": lambda: gg.grid(32, 32),
+    "tree3000": lambda: gg.random_binary_tree(3000, 5),
+    "er_ragged": lambda: gg.erdos_renyi(1537, 2100, 3),   # duplicates, self-loops, isolated nodes
+}
+
+
+@pytest.mark.parametrize("name,k,cap", [("ba2000", 1, 3), ("ba2000", 2, 8), ("ba2000", 3, 40), ("grid32", 3, 10),
+                                        ("grid32", 2, 10 ** 6), ("tree3000", 3, 4), ("er_ragged", 2, 5),
+                                        ("er_ragged", 3, 17)])
+def test_capped_matrix_matches_oracle(env, orc, name, k, cap):
+    drg, ctx = env
+    g = GRAPHS[name]()
+    orp, ocol = orc.canonical_graph(*g)
+    u_rp, u_col, u_dist, own, back = orc.korder_capped(orp, ocol, k, cap)
+    sc = orc.similarity_capped(u_rp, u_col, u_dist, own, back, k, 1.0)
+    et = orc.alias_build(sc["q"])
+    r32, shift = orc.node_weights_u32(sc["r"])
+    vt = orc.alias_build(r32)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, k, row_cap=cap)
+    got = D.download()
+    assert np.array_equal(got["rp"], u_rp)
+    assert np.array_equal(got["col"], u_col) and np.array_equal(got["dist"], u_dist)
+    assert np.array_equal(got["Z"].view(np.uint32), sc["Z"].view(np.uint32))
+    assert np.array_equal(got["q"], sc["q"]) and np.array_equal(got["r"], sc["r"]) and got["shift"] == shift
+    assert np.array_equal(got["e_thresh"], et[0]) and np.array_equal(got["e_alias"], et[1])
+    assert np.array_equal(got["v_thresh"], vt[0]) and np.array_equal(got["v_alias"], vt[1])
+    if cap >= 10 ** 6:
+        # a cap that does not bind gives the uncapped matrix
+        full = drg.build_distance_matrix(ctx, G, k).download()
+        for key in ("rp", "col", "dist", "q", "e_thresh", "v_thresh"):
+            assert np.array_equal(got[key], full[key]), key
+
+
+def test_capped_whole_run(env, orc):
+    # the whole path with capped rows: k = 3, rows of at most 30 nodes
+    drg, ctx = env
+    g = gg.barabasi_albert(5000, 3, 2)
+    n = g[0]
+    p = drg.Params.default(k=3, M=5, epochs=100, b=1.0, mode=1, stop_nodes=500, seed=1, row_cap=30)
+    pos = torch.zeros(2 * n, device="cuda")
+    drg.layout_edges(ctx, n, g[1], g[2], p, pos)
+    Y = pos.cpu().numpy().astype(np.float64).reshape(n, 2)
+    assert np.all(np.isfinite(Y)) and np.ptp(Y) > 1.0
+    rp, col = orc.canonical_graph(*g)
+    assert orc.neighbourhood_preservation(rp, col, Y, 2) > 0.02
+
+
+def _kept(row_col, row_dist, cap):
+    order = np.lexsort((row_col.astype(np.int64), row_dist.astype(np.int64)))[:cap]
+    return dict(zip(row_col[order].tolist(), row_dist[order].tolist()))
+
+
+def test_dcsbm1m_k3_capped_rows(env, orc):
+    drg, ctx = env
+    cap, k = 128, 3
+    g = gg.workload("dcsbm1m")
+    orp, ocol = orc.canonical_graph(*g)
+    G = drg.graph_from_edges(ctx, *g)
+    D = drg.build_distance_matrix(ctx, G, k, row_cap=cap)
+    nodes = D.download_nodes()
+    rp, Z = nodes["rp"], nodes["Z"]
+    assert nodes["nnz"] <= 2 * g[0] * cap
+    gz = orc.gaussians(k)
+    bfs = orc.RowBFS(orp, ocol, k)
+    deg = np.diff(orp).astype(np.int64)
+    rng = np.random.default_rng(7)
+    rows = np.r_[rng.choice(np.nonzero(deg > 0)[0], 20, replace=False), [int(np.argmax(deg))]]
+    kept_of = {}
+
+    def kept(v):
+        if v not in kept_of:
+            kept_of[v] = _kept(*bfs.row(v), cap)
+        return kept_of[v]
+
+    for i in rows:
+        Ki = kept(int(i))
+        got = D.download_range(int(rp[i]), int(rp[i + 1]))
+        gcol, gdist, gq = got["col"], got["dist"], got["q"]
+        assert np.all(np.diff(gcol.astype(np.int64)) > 0)
+        entry = {int(c): (int(d), int(x)) for c, d, x in zip(gcol, gdist, gq)}
+        # K_i lies in the row with its hop distances
+        for j, d in Ki.items():
+            assert entry[j][0] == d
+        # Z_i over K_i (FP32, classes in order)
+        z = np.float32(0.0)
+        for c in range(1, k + 1):
+            z = np.float32(z + np.float32(np.float32(sum(1 for d in Ki.values() if d == c)) * gz[c - 1]))
+        assert np.float32(Z[i]).view(np.uint32) == z.view(np.uint32)
+        # every other entry is there because i is kept by j; q exactly, for a few
+        others = [j for j in entry if j not in Ki]
+        for j in others[:4]:
+            assert int(i) in kept(j)
+        for j in list(Ki)[:3] + others[:3]:
+            d = entry[j][0]
+            gd = gz[d - 1]
+            a = np.float32(gd / Z[i]) if j in Ki else np.float32(0.0)
+            b = np.float32(gd / Z[j]) if int(i) in kept(j) else np.float32(0.0)
+            assert entry[j][1] == int(np.float32(np.float32(a + b) * np.float32(2.0 ** 30)))

@@ -52,7 +52,7 @@ def test_replicas_draw_their_own_streams():
     import paper_2008_07799_gb300 as drg
 
     class A:
-        mode, precision, seed, substeps, coarsen, level_tables, perplexity = "hogwild", "fp32", 0, None, "hem", False, 0.0
+        mode, precision, seed, substeps, coarsen, level_tables, perplexity, row_cap = "hogwild", "fp32", 0, None, "hem", False, 0.0, 0
     wl = bench.WORKLOADS["dcsbm1m"]
     gids = [bench.make_params(drg, wl, A, gid=r).gid for r in range(3)]
     assert gids == [0, 1, 2]
