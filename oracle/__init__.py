@@ -196,6 +196,7 @@ class Params:
     max_levels: int = 32
     init_scale: float = 1e-4   # coarsest positions uniform in [-s, s]^2
     multilevel: bool = True
+    row_cap: int = 0           # > 0: each row keeps its row_cap nearest nodes, pattern K u K^T (korder_capped)
 
 
 # ---------------------------------------------------------------- primitives
@@ -615,13 +616,34 @@ def level_tables(level: Level, p: Params):
     return sampling_tables(*gd, p.k, p.sigma, p.perplexity)[0]
 
 
+def sampling_tables_capped(rp, col, k, cap, sigma=1.0):
+    """Sampling tables of the capped matrix (korder_capped, similarity_capped):
+    the edge table over the union pattern's entries, the node table over the
+    row sums of its weights."""
+    u_rp, u_col, u_dist, own, back = korder_capped(rp, col, k, cap)
+    sim = similarity_capped(u_rp, u_col, u_dist, own, back, k, sigma)
+    e_src, e_dst = edge_endpoints(u_rp, u_col)
+    et = alias_build(sim["q"])
+    r32, shift = node_weights_u32(sim["r"])
+    vt = alias_build(r32)
+    if et is None or vt is None:
+        raise ValueError("graph has no edges: nothing to sample")
+    return Tables(len(u_rp) - 1, e_src, e_dst, et[0], et[1], vt[0], vt[1], sim["q"], r32, shift), \
+        (u_rp, u_col, u_dist), sim
+
+
 def run(n, src, dst, p: Params, return_state=False):
     """The whole layout path, coarse to fine (Sec. 3.2, Fig. 1 pipeline).
     With p.level_tables = 1 every coarse level samples its own tables
-    (level_tables) instead of G^0's through the ancestor map."""
+    (level_tables) instead of G^0's through the ancestor map; with
+    p.row_cap > 0 the distance matrix's rows are capped (korder_capped)."""
     rp, col = canonical_graph(n, src, dst)
-    gd_rp, gd_col, gd_dist = korder(rp, col, p.k)
-    tab, sim = sampling_tables(gd_rp, gd_col, gd_dist, p.k, p.sigma, p.perplexity)
+    if p.row_cap:
+        assert not p.level_tables and p.perplexity == 0.0, "the row cap is for G^0's global-sigma tables"
+        tab, (gd_rp, gd_col, gd_dist), sim = sampling_tables_capped(rp, col, p.k, p.row_cap, p.sigma)
+    else:
+        gd_rp, gd_col, gd_dist = korder(rp, col, p.k)
+        tab, sim = sampling_tables(gd_rp, gd_col, gd_dist, p.k, p.sigma, p.perplexity)
     levels = hierarchy(rp, col, p)
     L = len(levels) - 1
     Y = init_positions(p, L, levels[L].n)

@@ -30,7 +30,7 @@ __global__ void k_expand_rows(const uint64_t* __restrict__ rp, uint32_t n, uint3
 // writes at the final row offsets and is the fallback when the staging area
 // overflows.
 #ifndef DRG_BFS_THREADS
-#define DRG_BFS_THREADS 512
+#define DRG_BFS_THREADS 1024
 #endif
 constexpr int BFS_THREADS = DRG_BFS_THREADS;
 

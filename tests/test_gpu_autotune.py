@@ -28,6 +28,9 @@ def _np(orc, g, Y):
 
 
 def test_tuned_shapes_and_quality(env, orc):
+    # NP varies by ~15 % from seed to seed on this graph, so tuned and
+    # default runs are compared as means over 16 seeds each, within three
+    # standard errors of their difference
     drg, ctx = env
     g = gg.barabasi_albert(8000, 3, 21)
     n = g[0]
@@ -37,13 +40,13 @@ def test_tuned_shapes_and_quality(env, orc):
         drg.autotune_clear()
         ctx.autotune(on)
         nps = []
-        for seed in range(4):
+        for seed in range(16):
             pos = torch.zeros(2 * n, device="cuda")
             drg.layout_edges(ctx, n, g[1], g[2], p.replace(seed=seed), pos)
             Y = pos.cpu().numpy().astype(np.float64).reshape(n, 2)
             assert np.all(np.isfinite(Y))
             nps.append(_np(orc, g, Y))
-        quality[on] = np.mean(nps)
+        quality[on] = np.array(nps)
         table = drg.autotune_table()
         if not on:
             assert table == []
@@ -55,7 +58,8 @@ def test_tuned_shapes_and_quality(env, orc):
             # one entry per size bucket of the levels (each level once, reused by later seeds)
             assert len({(e["ancestors"], e["bucket"]) for e in table}) == len(table)
     ctx.autotune(True)
-    assert quality[True] >= 0.93 * quality[False], quality
+    se = np.hypot(*(np.std(q, ddof=1) / np.sqrt(len(q)) for q in quality.values()))
+    assert abs(quality[True].mean() - quality[False].mean()) <= 3 * se, (quality, se)
 
 
 def test_batch_block_size_is_tuned(env):

@@ -62,18 +62,48 @@ def test_capped_matrix_matches_oracle(env, orc, name, k, cap):
             assert np.array_equal(got[key], full[key]), key
 
 
-def test_capped_whole_run(env, orc):
-    # the whole path with capped rows: k = 3, rows of at most 30 nodes
+def test_capped_whole_run_matches_oracle(env, orc):
+    # The whole path with capped rows (BA 3000, k = 3, rows of at most 30
+    # nodes, Hogwild as in the bench) against the oracle's whole runs with the
+    # same cap (tests/golden/capped_quality.json, written by
+    # make_capped_quality.py from oracle/ alone), 96 seeds each, compared as
+    # 10 %-trimmed means: NP within 1 % (resolved by the seeds: twice the
+    # standard error of the difference is ~0.6 %); stress, which the cap makes
+    # vary by ~28 % from seed to seed (fewer long-range pairs leave some
+    # layouts' global structure distorted), within three standard errors.
+    import json
+    from conftest import golden
+    from scipy.stats import trim_mean
     drg, ctx = env
-    g = gg.barabasi_albert(5000, 3, 2)
-    n = g[0]
-    p = drg.Params.default(k=3, M=5, epochs=100, b=1.0, mode=1, stop_nodes=500, seed=1, row_cap=30)
-    pos = torch.zeros(2 * n, device="cuda")
-    drg.layout_edges(ctx, n, g[1], g[2], p, pos)
-    Y = pos.cpu().numpy().astype(np.float64).reshape(n, 2)
-    assert np.all(np.isfinite(Y)) and np.ptp(Y) > 1.0
-    rp, col = orc.canonical_graph(*g)
-    assert orc.neighbourhood_preservation(rp, col, Y, 2) > 0.02
+    gold = json.load(open(golden("capped_quality.json")))
+    n, s, d = getattr(gg, gold["graph"]["gen"])(*gold["graph"]["args"])
+    prm = gold["params"]
+    rp, col = orc.canonical_graph(n, s, d)
+    src = torch.from_numpy(s.view(np.int32)).cuda()
+    dst = torch.from_numpy(d.view(np.int32)).cuda()
+    got = []
+    for seed in range(gold["seeds"]):
+        p = drg.Params.default(k=prm["k"], M=prm["M"], epochs=prm["epochs"], b=prm["b"], stop_nodes=prm["stop_nodes"],
+                               mode=prm["mode"], seed=seed, row_cap=prm["row_cap"])
+        pos = torch.zeros(2 * n, device="cuda")
+        drg.layout_edges(ctx, n, src, dst, p, pos)
+        Y = pos.cpu().numpy().astype(np.float64).reshape(n, 2)
+        assert np.all(np.isfinite(Y))
+        got.append((orc.neighbourhood_preservation(rp, col, Y, 2), orc.stress(rp, col, Y)))
+    got, ref = np.array(got), np.array(gold["runs"])
+    rng = np.random.default_rng(0)
+
+    def boot_se(x):
+        return float(np.std([trim_mean(x[rng.integers(0, len(x), len(x))], 0.1) for _ in range(2000)]))
+
+    for c, what, bar in ((0, "NP", None), (1, "stress", 3.0)):
+        m_ref, m_got = trim_mean(ref[:, c], 0.1), trim_mean(got[:, c], 0.1)
+        se = np.hypot(boot_se(ref[:, c]), boot_se(got[:, c]))
+        print(f"capped {what}: GPU {m_got:.5f} oracle {m_ref:.5f} ({(m_got / m_ref - 1) * 100:+.2f} %, SE {se / m_ref * 100:.2f} %)")
+        if bar is None:
+            assert 2 * se < 0.01 * m_ref and abs(m_got - m_ref) <= 0.01 * m_ref, (what, m_got, m_ref, se)
+        else:
+            assert abs(m_got - m_ref) <= bar * se, (what, m_got, m_ref, se)
 
 
 def _kept(row_col, row_dist, cap):
