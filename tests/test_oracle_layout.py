@@ -607,3 +607,15 @@ def test_openmp_loop_keeps_quality(orc):
         nps[1].append(orc.neighbourhood_preservation(rp, col, orc.layout_level(tab, Y0.copy(), 0, None, p, 0.1), 2))
         nps[4].append(orc.neighbourhood_preservation(rp, col, orc.layout_level_omp(tab, Y0.copy(), 0, None, p, 0.1, 4), 2))
     assert np.mean(nps[4]) >= 0.85 * np.mean(nps[1]), nps
+
+
+def test_whole_run_with_a_cap_that_does_not_bind_is_the_whole_run(orc):
+    # capped tables with a cap no row reaches are the uncapped tables, so the
+    # whole run is the same layout bit for bit
+    g = gg.barabasi_albert(600, 3, 4)
+    p = dict(k=2, M=5, epochs=20, b=1.0, mode=1, stop_nodes=200, seed=3)
+    a = orc.run(*g, orc.Params(**p))
+    b = orc.run(*g, orc.Params(**p, row_cap=10 ** 6))
+    assert np.array_equal(a, b)
+    c = orc.run(*g, orc.Params(**p, row_cap=6))
+    assert np.all(np.isfinite(c)) and not np.array_equal(a, c)
