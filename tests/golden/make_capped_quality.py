@@ -20,7 +20,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 GRAPH = dict(gen="barabasi_albert", args=[3000, 3, 2])
-PARAMS = dict(k=3, M=5, epochs=100, b=1.0, stop_nodes=500, row_cap=30, mode=1)
+PARAMS = dict(k=3, M=5, epochs=100, b=1.0, stop_nodes=500, row_cap=30, mode=0)
 SEEDS = 96
 
 
