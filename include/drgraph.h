@@ -473,6 +473,24 @@ drg_status drg_autotune_clear(void);
 drg_status drg_probe_memory(drg_ctx* ctx, int kind, uint64_t buffer_bytes, uint64_t accesses, uint32_t blocks_per_sm,
                             double* ms, uint64_t* done);
 
+/* ---------------------------------------------------------------- caller-given samples (tests) */
+/* One synchronous step of Eqs. 11-12 over S samples fixed by the caller
+ * instead of drawn (no counterpart in the paper's API: it serves closed-form
+ * tests of the gradient).  Sample s is the term with source src[s], positive
+ * target dst[s] and negatives neg[s M .. s M + M) (level node ids < n; device
+ * arrays); negatives equal to the source or target are skipped.  Every force
+ * is computed from the positions at the start of the call with the level
+ * kernels' arithmetic (attraction -2b d^{2b-2} (y_a - y_c)/(1 + d^{2b}),
+ * repulsion gamma 2b (y_a - y_m)/(d^2 (1 + d^{2b})), each component clipped
+ * to [-clip, clip], zero at distance 0), moving the source by attraction +
+ * sum of repulsions, the target by -attraction and each negative by -its
+ * repulsion; the sums per node are then applied, pos += lr G.  pos: device
+ * float[2 n], updated in place.  DRG_EINVAL for an id >= n, M > 64, b or clip
+ * not positive or gamma negative.  Synchronises. */
+drg_status drg_layout_step_explicit(drg_ctx* ctx, uint32_t n, float* pos, uint32_t S, const uint32_t* src,
+                                    const uint32_t* dst, const uint32_t* neg, uint32_t M, float gamma, float b,
+                                    float lr, float clip);
+
 /* ---------------------------------------------------------------- inspection */
 /* The draws of samples [s_begin, s_end) of epoch t at `level`: out_i, out_j
  * (level-0 ids of the positive entry) and out_neg[M per sample], device

@@ -39,7 +39,7 @@ EXPORTS = [
     "drg_layout_level_noalloc", "drg_dmat_download_range", "drg_check_epoch_barrier",
     "drg_build_distance_matrix_ex", "drg_dmat_calibration", "drg_crossings", "drg_min_angle",
     "drg_probe_memory", "drg_autotune_enable", "drg_autotune_read", "drg_autotune_clear",
-    "drg_build_distance_matrix_capped",
+    "drg_build_distance_matrix_capped", "drg_layout_step_explicit",
 ]
 
 PROBE_LOAD8, PROBE_LOAD16, PROBE_RED8, PROBE_LOAD16_EVICT_FIRST, PROBE_COPY = range(5)
@@ -136,6 +136,8 @@ def lib():
         "drg_sample_draws": (st, [VP, VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, PP, VP, VP, VP]),
         "drg_probe_memory": (st, [VP, C.c_int, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(C.c_double),
                                   C.POINTER(C.c_uint64)]),
+        "drg_layout_step_explicit": (st, [VP, C.c_uint32, VP, C.c_uint32, VP, VP, VP, C.c_uint32, C.c_float,
+                                          C.c_float, C.c_float, C.c_float]),
         "drg_autotune_enable": (st, [VP, C.c_int]),
         "drg_autotune_read": (st, [C.c_uint32, VP, VP, VP, C.POINTER(C.c_uint32)]),
         "drg_autotune_clear": (st, []),
@@ -491,3 +493,13 @@ def autotune_table():
 
 def autotune_clear():
     lib().drg_autotune_clear()
+
+
+def layout_step_explicit(ctx: Context, pos, src, dst, neg, M, gamma, b, lr, clip=5.0):
+    """One synchronous step over caller-given samples (device tensors: src,
+    dst of S node ids, neg of S * M); pos is updated in place."""
+    S = int(src.numel())
+    n = int(pos.numel()) // 2
+    ctx.check(lib().drg_layout_step_explicit(ctx.h, n, _ptr(pos), S, _ptr(src), _ptr(dst),
+                                             _ptr(neg) if M else None, int(M), float(gamma), float(b), float(lr),
+                                             float(clip)))

@@ -496,6 +496,15 @@ drg_status drg_layout_level_noalloc(drg_ctx* ctx, const drg_dmat* d, const drg_h
     API_CATCH(ctx)
 }
 
+drg_status drg_layout_step_explicit(drg_ctx* ctx, uint32_t n, float* pos, uint32_t S, const uint32_t* src,
+                                    const uint32_t* dst, const uint32_t* neg, uint32_t M, float gamma, float b,
+                                    float lr, float clip) {
+    if (!ctx) return DRG_EINVAL;
+    API_TRY
+    drg::layout_step_explicit(ctx, n, pos, S, src, dst, neg, M, gamma, b, lr, clip);
+    API_CATCH(ctx)
+}
+
 drg_status drg_autotune_enable(drg_ctx* ctx, int on) {
     if (!ctx) return DRG_EINVAL;
     ctx->autotune = on != 0;

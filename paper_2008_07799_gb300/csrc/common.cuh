@@ -307,6 +307,8 @@ void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, u
                   const drg_params& p, uint32_t* oi, uint32_t* oj, uint32_t* oneg);
 uint32_t autotune_read(uint32_t cap, uint32_t* keys, uint32_t* choice, float* ms);
 void autotune_clear();
+void layout_step_explicit(drg_ctx* ctx, uint32_t n, float* pos, uint32_t S, const uint32_t* sa, const uint32_t* sc,
+                          const uint32_t* sneg, uint32_t M, float gamma, float b, float lr, float clip);
 void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uint32_t blocks_per_sm, double* ms,
                   uint64_t* done);
 

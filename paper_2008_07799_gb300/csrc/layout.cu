@@ -1419,6 +1419,73 @@ void sample_draws(drg_ctx* ctx, const drg_dmat* d, uint32_t level, uint32_t t, u
     DRG_LAUNCH(ctx, k_draws, grid_for(s_end - s_begin, 256, (uint32_t)ctx->num_sms * 8), 256, 0, a, oi, oj, oneg);
 }
 
+// ------------------------------------------------------------------ caller-given samples
+// One synchronous step over S samples the caller fixes (for closed-form tests
+// of Eq. 12): the forces of every sampled term are computed from the
+// positions at the start, summed per node with the level kernels' arithmetic
+// (attract, repel, the skip rule for negatives that hit the source or
+// target), then applied, Y += lr G.
+__global__ void k_explicit_check(const uint32_t* __restrict__ sa, const uint32_t* __restrict__ sc,
+                                 const uint32_t* __restrict__ sneg, uint32_t S, uint32_t M, uint32_t n,
+                                 uint32_t* __restrict__ bad) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S; s += (uint64_t)gridDim.x * blockDim.x) {
+        bool ok = sa[s] < n && sc[s] < n;
+        for (uint32_t m = 0; m < M; ++m) ok = ok && sneg[s * M + m] < n;
+        if (!ok) atomicOr(bad, 1u);
+    }
+}
+
+__global__ void k_explicit_forces(EpochArgs a, const uint32_t* __restrict__ sa, const uint32_t* __restrict__ sc,
+                                  const uint32_t* __restrict__ sneg, uint32_t S) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S; s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t ia = sa[s], ic = sc[s];
+        const float2 ya = a.Y[ia], yc = a.Y[ic];
+        const float2 fa = attract(a, ya, yc);
+        float Fx = fa.x, Fy = fa.y;
+        for (uint32_t m = 0; m < a.M; ++m) {
+            const uint32_t cm = sneg[s * a.M + m];
+            if (cm == ia || cm == ic) continue;
+            const float2 fr = repel(a, ya, a.Y[cm]);
+            Fx += fr.x;
+            Fy += fr.y;
+            push<true>(a, cm, -fr.x, -fr.y);
+        }
+        push<true>(a, ia, Fx, Fy);
+        push<true>(a, ic, -fa.x, -fa.y);
+    }
+}
+
+void layout_step_explicit(drg_ctx* ctx, uint32_t n, float* pos, uint32_t S, const uint32_t* sa, const uint32_t* sc,
+                          const uint32_t* sneg, uint32_t M, float gamma, float b, float lr, float clip) {
+    DRG_CHECK(pos && n >= 1, DRG_EINVAL, "null positions or no node");
+    DRG_CHECK(S == 0 || (sa && sc && (sneg || M == 0)), DRG_EINVAL, "null sample array");
+    DRG_CHECK(M <= 64 && b > 0.f && clip > 0.f && gamma >= 0.f, DRG_EINVAL,
+              "M must be at most 64, b and clip positive, gamma non-negative");
+    if (S == 0) return;
+    DBuf<uint32_t> bad(ctx, 1);
+    DRG_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(uint32_t), ctx->stream));
+    const uint32_t gs = grid_for(S, 256, (uint32_t)ctx->num_sms * 8);
+    DRG_LAUNCH(ctx, k_explicit_check, gs, 256, 0, sa, sc, sneg, S, M, n, bad.p);
+    DRG_CHECK(read1(ctx, bad.p) == 0, DRG_EINVAL, "a sample names a node id >= n");
+    DBuf<float2> G(ctx, n);
+    DRG_CUDA(cudaMemsetAsync(G.p, 0, sizeof(float2) * n, ctx->stream));
+    EpochArgs a{};
+    a.Y = reinterpret_cast<float2*>(pos);
+    a.G = G.p;
+    a.M = M;
+    a.gamma = gamma;
+    a.b = b;
+    a.twob = 2.f * b;
+    a.clip = clip;
+    a.bint = int_b(b);
+    DRG_LAUNCH(ctx, k_explicit_forces, gs, 256, 0, a, sa, sc, sneg, S);
+    DBuf<EpochState> st(ctx, 1);
+    DRG_LAUNCH(ctx, k_set_epoch, 1, 1, 0, st.p, 0u, 1u, lr);
+    DRG_LAUNCH(ctx, k_apply<0>, grid_for(n, 256, (uint32_t)ctx->num_sms * 8), 256, 0, a.Y, G.p, (void*)nullptr, n,
+               (const EpochState*)st.p);
+    sync(ctx);
+}
+
 // A context for a host worker thread: the parent's device and settings, its
 // own stream, no profiling events.
 struct WorkerCtx {
