@@ -522,6 +522,171 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ capped rows, one warp each
+// Rows of the capped matrix (R24) whose levels fit SMALL_CAP candidates: the
+// warp keeps the row's discovered nodes sorted in shared memory as keys
+// (v << 4 | d) -- level 1 is the source's sorted adjacency -- and grows it a
+// level at a time while fewer than row_cap nodes are known: the adjacencies
+// of the last level's nodes are appended as (v << 4 | d), the keys sorted
+// (bitonic) and only the first key of each node kept (its smallest
+// distance).  The row is then every node of the levels before the last plus
+// the last level's row_cap - (those) smallest ids, written in id order to the
+// staging area.  Rows whose candidates overflow the buffer go to `big` for
+// the block kernel.
+__device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t lane) {
+    uint32_t P = 1;
+    while (P < m) P <<= 1;
+    for (uint32_t x = m + lane; x < P; x += 32) buf[x] = 0xFFFFFFFFu;
+    __syncwarp();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = lane; t < P / 2; t += 32) {
+                const uint32_t i = (t / j) * 2 * j + (t % j), l = i + j;
+                const uint32_t u = buf[i], w = buf[l];
+                if ((u > w) == ((i & k) == 0)) {
+                    buf[i] = w;
+                    buf[l] = u;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Keeps the first key of each node of the sorted buf[0, m) (in place); returns the count.
+__device__ __forceinline__ uint32_t warp_unique(uint32_t* buf, uint32_t m, uint32_t lane) {
+    uint32_t out = 0, prev = 0xFFFFFFFFu;
+    for (uint32_t x0 = 0; x0 < m; x0 += 32) {
+        const uint32_t x = x0 + lane;
+        const uint32_t key = x < m ? buf[x] : 0xFFFFFFFFu;
+        uint32_t before = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+        if (lane == 0) before = prev;
+        const bool first = x < m && (x == 0 || (key >> 4) != (before >> 4));
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
+        prev = __shfl_sync(0xFFFFFFFFu, key, 31);
+        __syncwarp();
+        if (first) buf[out + __popc(bal & lanemask_lt())] = key;
+        out += __popc(bal);
+        __syncwarp();
+    }
+    return out;
+}
+
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_cap_small(BfsArgs a, uint32_t* __restrict__ big,
+                                                                uint32_t* __restrict__ nbig) {
+    extern __shared__ uint32_t small_smem[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* buf = small_smem + (size_t)warp * SMALL_CAP;
+    for (;;) {
+        uint32_t row = 0;
+        if (lane == 0) row = atomicAdd(a.next_row, 1u);
+        row = __shfl_sync(0xFFFFFFFFu, row, 0);
+        if (row >= a.nrows) break;
+        const uint64_t ab = a.rp[row], ae = a.rp[row + 1];
+        const uint32_t deg = (uint32_t)(ae - ab);
+        bool fits = deg <= SMALL_CAP;
+        uint32_t m = 0, dlast = 1;
+        if (fits) {
+            for (uint32_t x = lane; x < deg; x += 32) buf[x] = (a.col[ab + x] << 4) | 1u;
+            m = deg;
+            __syncwarp();
+        }
+        // further levels while fewer than row_cap nodes are known
+        for (uint32_t d = 2; fits && d <= a.k && m < a.row_cap; ++d) {
+            const uint32_t m0 = m;
+            uint32_t add = 0;
+            // the adjacencies of the level-(d-1) nodes, 32 list entries at a time
+            for (uint32_t c = 0; c < m0 && fits; c += 32) {
+                uint64_t st = 0;
+                uint32_t dg = 0;
+                if (c + lane < m0 && (buf[c + lane] & 15u) == d - 1) {
+                    const uint32_t u = buf[c + lane] >> 4;
+                    st = a.rp[u];
+                    dg = (uint32_t)(a.rp[u + 1] - st);
+                }
+                const uint32_t incl = warp_incl_scan(dg, lane);
+                const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                const uint32_t excl = incl - dg;
+                if (m0 + add + tot > SMALL_CAP) {
+                    fits = false;
+                    break;
+                }
+                for (uint32_t x0 = 0; x0 < tot; x0 += 32) {
+                    const uint32_t x = x0 + lane;
+                    uint32_t lo = 0, hi = 32;
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
+                    }
+                    const uint64_t so = __shfl_sync(0xFFFFFFFFu, st, lo);
+                    const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                    uint32_t key = 0xFFFFFFFFu;
+                    if (x < tot) {
+                        const uint32_t v = a.col[so + (x - eo)];
+                        if (v != row) key = (v << 4) | d;
+                    }
+                    const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
+                    if (key != 0xFFFFFFFFu) buf[m0 + add + __popc(keep & lanemask_lt())] = key;
+                    add += __popc(keep);
+                }
+                __syncwarp();
+            }
+            if (!fits) break;
+            if (add == 0) break;
+            warp_bitonic(buf, m0 + add, lane);
+            m = warp_unique(buf, m0 + add, lane);
+            dlast = d;
+            if (m == m0) break;  // no new node: nothing further either
+        }
+        if (!fits) {
+            if (lane == 0) big[atomicAdd(nbig, 1u)] = row;
+            __syncwarp();
+            continue;
+        }
+        // nodes before the last level, and how many of the last level stay
+        uint32_t last = 0;
+        for (uint32_t x = lane; x < m; x += 32) last += (buf[x] & 15u) == dlast ? 1u : 0u;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) last += __shfl_xor_sync(0xFFFFFFFFu, last, off);
+        const uint32_t keep_last = m <= a.row_cap ? last : a.row_cap - (m - last);
+        const uint32_t total = (m - last) + keep_last;
+        uint64_t base = 0;
+        int skip = 0;
+        if (lane == 0) {
+            a.counts[row] = total;
+            const uint64_t span = ((uint64_t)total + 15) & ~15ull;
+            base = atomicAdd(a.cursor, (unsigned long long)span);
+            if (base + span > a.cap) {
+                skip = 1;
+                atomicExch(a.overflow, 1u);
+            }
+            a.row_off[row] = base;
+        }
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        skip = __shfl_sync(0xFFFFFFFFu, skip, 0);
+        if (!skip) {
+            uint64_t o = base;
+            uint32_t seen_last = 0;
+            for (uint32_t x0 = 0; x0 < m; x0 += 32) {
+                const uint32_t x = x0 + lane;
+                const uint32_t key = x < m ? buf[x] : 0u;
+                const bool is_last = x < m && (key & 15u) == dlast;
+                const uint32_t lb = __ballot_sync(0xFFFFFFFFu, is_last);
+                const bool take = x < m && (!is_last || seen_last + __popc(lb & lanemask_lt()) < keep_last);
+                const uint32_t tb = __ballot_sync(0xFFFFFFFFu, take);
+                if (take) {
+                    const uint64_t at = o + __popc(tb & lanemask_lt());
+                    a.out_col[at] = key >> 4;
+                    a.out_dist[at] = (uint8_t)(key & 15u);
+                }
+                o += __popc(tb);
+                seen_last += __popc(lb);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Splits the rows into those of at most SMALL_CAP candidates (small) and the
 // rest (big), as two lists (in no particular order).
 __global__ void k_bfs_classify(const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col, uint32_t n,
@@ -739,6 +904,24 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
             DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
             a.rows = big.p;
             a.nrows = nc[1];
+        } else if (row_cap && n <= (1u << 28) && cap > 0) {
+            // capped rows: one warp each where the levels fit, the rest by blocks
+            big = DBuf<uint32_t>(ctx, n);
+            DBuf<uint32_t> nb(ctx, 1);
+            DRG_CUDA(cudaMemsetAsync(nb.p, 0, 4, ctx->stream));
+            const size_t ssm = (size_t)SMALL_WARPS * SMALL_CAP * 4;
+            DRG_CUDA(cudaFuncSetAttribute(k_cap_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+            int sper = 0;
+            DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, k_cap_small, SMALL_WARPS * 32, ssm));
+            BfsArgs as = a;
+            as.rows = nullptr;
+            as.nrows = n;
+            DRG_LAUNCH(ctx, k_cap_small, (uint32_t)ctx->num_sms * (uint32_t)(sper > 0 ? sper : 1), SMALL_WARPS * 32,
+                       ssm, as, big.p, nb.p);
+            const uint32_t nbig = read1(ctx, nb.p);
+            DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
+            a.rows = big.p;
+            a.nrows = nbig;
         }
         DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
     }
@@ -1466,10 +1649,16 @@ struct Sum64 {
 
 // Alias table over N items with 32-bit weights q, written as `out` says.
 // Returns false (nothing written) when the weights sum to zero.
-bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& out) {
+// parts / nparts: when the weights' row sums are at hand (the edge table's
+// r), their sum is the capacity W, a reduction over n values instead of N.
+bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& out, const uint64_t* parts = nullptr,
+                 uint64_t nparts = 0) {
     DRG_CHECK(N > 0 && N < (1ull << 32), DRG_EUNSUPPORTED, "alias table size must be in [1, 2^32)");
     DBuf<uint64_t> Wd(ctx, 1);
-    {
+    if (parts) {
+        DBuf<uint64_t> tmp(ctx, nparts);
+        scan<uint64_t>(ctx, LoadArr<uint64_t>{parts}, nparts, tmp.p, false, Wd.p);
+    } else {
         DBuf<uint64_t> sums(ctx, (N + ScanShape<uint64_t>::TILE - 1) / ScanShape<uint64_t>::TILE);
         const uint32_t nb = (uint32_t)sums.n;
         DRG_LAUNCH(ctx, (k_scan_reduce<uint64_t, Sum64>), nb, 256, 0, Sum64{q}, (size_t)N, sums.p);
@@ -1674,7 +1863,8 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
             d->erec_bytes = packed ? 16u : (uint32_t)sizeof(EdgeRec);
             d->etab = dalloc(ctx, (size_t)d->erec_bytes * nnz);
             AliasOut out{packed ? kOutEdges16 : kOutEdges32, nullptr, d->etab, esrc.p, d->col};
-            DRG_CHECK(build_alias(ctx, d->q, nnz, out), DRG_EEMPTY, "all edge weights are zero");
+            // W = sum of q = sum of the row sums r (exact integers)
+            DRG_CHECK(build_alias(ctx, d->q, nnz, out, d->r, n), DRG_EEMPTY, "all edge weights are zero");
         }
         // node table (negative samples)
         {
