@@ -76,12 +76,17 @@ class Job:
                     for g in self.graphs]
         self.pos = [torch.zeros(2 * g[0], dtype=torch.float32, device="cuda") for g in self.graphs]
         self.host = None
+        self.one_by_one = False
 
     def _run(self, edges, pos):
         drg, ctx = self.drg, self.ctx
         if self.b is None:
             n, s, d = edges[0]
             drg.layout_edges(ctx, n, s, d, self.p, pos[0])
+        elif self.one_by_one:
+            # the same graphs laid out one after another, each as its own job
+            for g, ((n, s, d), x, b) in enumerate(zip(edges, pos, self.b)):
+                drg.layout_edges(ctx, n, s, d, self.p.replace(b=b, gid=g), x)
         else:
             gs = [drg.graph_from_edges(ctx, n, s, d) for n, s, d in edges]
             dpos = pos if pos[0].is_cuda else [self.torch.zeros(x.shape, device="cuda") for x in pos]
@@ -470,6 +475,8 @@ def main():
                          "multilevel scheme) instead of G^0's through the ancestor map")
     ap.add_argument("--substeps", type=int, default=None, help="override the in-flight bound n_l / substeps (profiling cases)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the level kernels' default launch shape")
+    ap.add_argument("--one-by-one", action="store_true",
+                    help="batch256: lay the graphs out one after another (the single-graph form) instead of as one job")
     ap.add_argument("--row-cap", type=int, default=0,
                     help="> 0: every row of the distance matrix keeps its row-cap nearest nodes (pattern K u K^T)")
     args = ap.parse_args()
@@ -514,6 +521,9 @@ def main():
     p = make_params(drg, wl, args, gid=rank)
     probes = None if args.once else measure_probes(drg, ctx)
     job = Job(drg, ctx, wl, p, np, torch)
+    job.one_by_one = bool(args.one_by_one)
+    if args.one_by_one:
+        wl["desc"] += "; the graphs laid out one after another, each as its own job"
     n, m = job.n, job.m
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 1 GiB > L2
     step = job.step
@@ -595,7 +605,7 @@ def main():
     s0 = n0 * wl["epochs"]
     coarse = max(ep_samples - s0, 0)
     prec = {"fp32": 0, "fp16": 1, "bf16": 2}[args.precision]
-    kname = epoch_kernel(wl["graph"], args.mode, args.precision)
+    kname = epoch_kernel("single" if args.one_by_one else wl["graph"], args.mode, args.precision)
     tps = None if (args.level_tables or args.perplexity > 0 or args.row_cap > 0) else ncu_traffic_per_sample(kname, {"workload": args.workload, "k": wl["k"], "coarsen": args.coarsen,
                                          "mode": args.mode, "precision": args.precision,
                                          "multilevel": bool(wl.get("multilevel", 1))})
@@ -629,7 +639,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "mode": args.mode, "precision": args.precision,
                    "coarsen": args.coarsen, "level_tables": bool(args.level_tables),
-                   "perplexity": args.perplexity, "row_cap": args.row_cap, "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
+                   "perplexity": args.perplexity, "row_cap": args.row_cap, "one_by_one": bool(args.one_by_one), "n": n, "edges_in": m, "distance_matrix_entries": nnz, "levels": levels,
                    "samples_per_step": samples_per_step, "layout_time_ms": ms,
                    "l2": "1 GiB buffer written between timed steps (flush)",
                    "parallelism": f"replicas x{world}"},

@@ -29,10 +29,9 @@ __global__ void k_expand_rows(const uint64_t* __restrict__ rp, uint32_t n, uint3
 // an atomic cursor (one traversal gives the counts and the rows); direct mode
 // writes at the final row offsets and is the fallback when the staging area
 // overflows.
-#ifndef DRG_BFS_THREADS
-#define DRG_BFS_THREADS 1024
-#endif
-constexpr int BFS_THREADS = DRG_BFS_THREADS;
+// Block sizes of the block kernel: 1024 threads when the bitmap leaves room
+// for one block per SM (large graphs), else 512 (several blocks per SM).
+constexpr int BFS_THREADS_BIG = 1024, BFS_THREADS_SMALL = 512;
 
 struct BfsArgs {
     const uint64_t* rp;
@@ -107,8 +106,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
     return v;
 }
 
-template <bool K2>
-__global__ void __launch_bounds__(BFS_THREADS, 1024 / BFS_THREADS) k_bfs(BfsArgs a) {
+template <bool K2, int BFS_THREADS>
+__global__ void __launch_bounds__(BFS_THREADS, BFS_THREADS == 512 ? 3 : 1) k_bfs(BfsArgs a) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint64_t s_off[BFS_THREADS];
     __shared__ uint64_t s_start[BFS_THREADS];
@@ -807,13 +806,17 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         return;
     }
     const bool k2 = k == 2 && row_cap == 0;  // capped rows take the general kernel (it knows every hop distance)
-    auto kern = k2 ? k_bfs<true> : k_bfs<false>;
     const uint32_t words = (n + 31) / 32;
     const uint32_t swords = (words + 31) / 32;
     const size_t bm_bytes = (size_t)words * 4, extra = bfs_extra_smem(swords);
     const bool smem_bm = bm_bytes + extra + 16384 <= (size_t)ctx->max_smem_optin;
     DRG_CHECK(extra + 16384 <= (size_t)ctx->max_smem_optin, DRG_EUNSUPPORTED, "graph too large for the BFS");
     const size_t dyn = (smem_bm ? bm_bytes : 0) + extra;
+    // 512-thread blocks when three of them fit an SM's shared memory, else 1024
+    const bool small_blocks = 3 * (dyn + 8 * 1024) <= (size_t)ctx->max_smem_optin;
+    const int bfs_threads = small_blocks ? BFS_THREADS_SMALL : BFS_THREADS_BIG;
+    auto kern = k2 ? (small_blocks ? k_bfs<true, BFS_THREADS_SMALL> : k_bfs<true, BFS_THREADS_BIG>)
+                   : (small_blocks ? k_bfs<false, BFS_THREADS_SMALL> : k_bfs<false, BFS_THREADS_BIG>);
     // The limit is process-wide per kernel and graphs differ in size (and may
     // be built by several host threads at once): allow the kernel's maximum
     // always; each launch passes its own size, which sets the occupancy.
@@ -824,7 +827,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
                                       ctx->max_smem_optin - (int)fa.sharedSizeBytes));
     }
     int per_sm = 0;
-    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BFS_THREADS, dyn));
+    DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bfs_threads, dyn));
     if (per_sm < 1) per_sm = 1;
     uint32_t blocks = (uint32_t)ctx->num_sms * (uint32_t)per_sm;
     if (blocks > n) blocks = n;
@@ -923,7 +926,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
             a.rows = big.p;
             a.nrows = nbig;
         }
-        DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
+        DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
     }
     DBuf<uint64_t> tot(ctx, 1);
     scan<uint64_t>(ctx, LoadArr<uint64_t>{counts.p}, n, d->rp, false, tot.p);
@@ -949,7 +952,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     a.out_dist = d->dist;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
     ProfSpan sb(ctx, DRG_PROF_BFS, 0);
-    DRG_LAUNCH(ctx, kern, blocks, BFS_THREADS, dyn, a);
+    DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
 }
 
 struct Gauss {
