@@ -423,7 +423,7 @@ drg_status drg_profile_read(drg_ctx* ctx, int which, double* ms, uint64_t* launc
  * (no counterpart in the paper): the first run of at least 50 epochs for
  * each (device, kernel, M, precision, ancestor map, size bucket = bit length
  * of the level's nodes, or of a batch's total threads) times every candidate
- * -- 64, 128 or 256 threads per block, T = the bound or half of it (a
+ * -- 64, 128 or 256 threads per block, T = the bound, half or a quarter of it (a
  * smaller T only tightens the bound; batches tune the block size only) --
  * for 3 epochs on scratch copies of its positions, and every later run with
  * that key uses the fastest.  The table is process-wide.  Results of a run

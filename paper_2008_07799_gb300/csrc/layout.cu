@@ -916,7 +916,8 @@ struct SyncBuf {
 // The Hogwild level kernels run a fixed number of threads T <= the in-flight
 // bound, so their launch shape is the one free choice: threads per block
 // (64, 128 or 256: how the warps spread over the SMs) and the samples per
-// thread (T = the bound or half of it; a smaller T only tightens the bound).
+// thread (T = the bound, half or a quarter of it; a smaller T only tightens the
+// bound).
 // The first long run of each (device, kernel, M, precision, ancestor map,
 // size bucket) times every candidate for a few epochs on a scratch copy of
 // its positions and keeps the fastest for the process.
@@ -936,7 +937,7 @@ struct TuneChoice {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneChoice> g_tune;
 constexpr uint32_t kTuneBlocks[3] = {64, 128, 256};
-constexpr uint32_t kTuneDivs[2] = {1, 2};
+constexpr uint32_t kTuneDivs[3] = {1, 2, 4};
 constexpr uint32_t kTuneEpochs = 3;      // epochs timed per candidate
 constexpr uint32_t kTuneMinEpochs = 50;  // runs shorter than this use the default shape
 constexpr TuneChoice kTuneDefault{128, 1, 0.f};
