@@ -522,16 +522,22 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
 }
 
 // ------------------------------------------------------------------ capped rows, one warp each
-// Rows of the capped matrix (R24) whose levels fit SMALL_CAP candidates: the
-// warp keeps the row's discovered nodes sorted in shared memory as keys
-// (v << 4 | d) -- level 1 is the source's sorted adjacency -- and grows it a
-// level at a time while fewer than row_cap nodes are known: the adjacencies
-// of the last level's nodes are appended as (v << 4 | d), the keys sorted
-// (bitonic) and only the first key of each node kept (its smallest
-// distance).  The row is then every node of the levels before the last plus
-// the last level's row_cap - (those) smallest ids, written in id order to the
-// staging area.  Rows whose candidates overflow the buffer go to `big` for
-// the block kernel.
+// Rows of the capped matrix (R24), one warp each.  The warp keeps the row's
+// known nodes as sorted keys (v << 4 | d) in shared memory -- level 1 is the
+// source's sorted adjacency -- and grows them a level at a time while fewer
+// than row_cap nodes are known: the adjacencies of the last level's nodes
+// stream through the buffer as keys (v << 4 | d); whenever it fills, and at
+// the end of the level, the keys are sorted (bitonic), only the first key of
+// each node is kept (its smallest distance) and, once more than row_cap
+// nodes are known, the new level is cut to its row_cap - (nodes before it)
+// smallest ids.  A node cut that way never returns: at least that many
+// smaller ids of the level are kept.  The row is written in id order to the
+// staging area.  A source of degree >= row_cap keeps the first row_cap of its
+// sorted adjacency directly.
+constexpr uint32_t CAPW_BUF = 1024, CAPW_FRONT = 512;
+constexpr uint32_t CAPW_MAX = CAPW_FRONT - 32;  // largest row_cap this kernel takes
+constexpr int CAPW_WARPS = 8;
+
 __device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t lane) {
     uint32_t P = 1;
     while (P < m) P <<= 1;
@@ -552,8 +558,13 @@ __device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t
     }
 }
 
-// Keeps the first key of each node of the sorted buf[0, m) (in place); returns the count.
-__device__ __forceinline__ uint32_t warp_unique(uint32_t* buf, uint32_t m, uint32_t lane) {
+// Sorts buf[0, m), keeps the first key of each node and, when more than cap
+// nodes remain, only the first cap - lower keys of level d (lower = nodes of
+// the levels before d, all kept).  Returns the new size (<= cap when cut).
+__device__ __forceinline__ uint32_t capw_flush(uint32_t* buf, uint32_t m, uint32_t lower, uint32_t cap, uint32_t d,
+                                               uint32_t lane) {
+    warp_bitonic(buf, m, lane);
+    // first key of each node (in place)
     uint32_t out = 0, prev = 0xFFFFFFFFu;
     for (uint32_t x0 = 0; x0 < m; x0 += 32) {
         const uint32_t x = x0 + lane;
@@ -568,14 +579,32 @@ __device__ __forceinline__ uint32_t warp_unique(uint32_t* buf, uint32_t m, uint3
         out += __popc(bal);
         __syncwarp();
     }
-    return out;
+    if (out <= cap) return out;
+    // keep the levels before d and the first cap - lower nodes of level d (in place)
+    const uint32_t keep_d = cap - lower;
+    uint32_t kept = 0, seen_d = 0;
+    for (uint32_t x0 = 0; x0 < out; x0 += 32) {
+        const uint32_t x = x0 + lane;
+        const uint32_t key = x < out ? buf[x] : 0u;
+        const bool at_d = x < out && (key & 15u) == d;
+        const uint32_t db = __ballot_sync(0xFFFFFFFFu, at_d);
+        const bool take = x < out && (!at_d || seen_d + __popc(db & lanemask_lt()) < keep_d);
+        const uint32_t tb = __ballot_sync(0xFFFFFFFFu, take);
+        __syncwarp();
+        if (take) buf[kept + __popc(tb & lanemask_lt())] = key;
+        kept += __popc(tb);
+        seen_d += __popc(db);
+        __syncwarp();
+    }
+    return kept;
 }
 
-__global__ void __launch_bounds__(SMALL_WARPS * 32) k_cap_small(BfsArgs a, uint32_t* __restrict__ big,
-                                                                uint32_t* __restrict__ nbig) {
+__global__ void __launch_bounds__(CAPW_WARPS * 32) k_cap_small(BfsArgs a) {
     extern __shared__ uint32_t small_smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* buf = small_smem + (size_t)warp * SMALL_CAP;
+    uint32_t* buf = small_smem + (size_t)warp * (CAPW_BUF + CAPW_FRONT);
+    uint32_t* fr = buf + CAPW_BUF;
+    const uint32_t C = a.row_cap;
     for (;;) {
         uint32_t row = 0;
         if (lane == 0) row = atomicAdd(a.next_row, 1u);
@@ -583,77 +612,69 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_cap_small(BfsArgs a, uint3
         if (row >= a.nrows) break;
         const uint64_t ab = a.rp[row], ae = a.rp[row + 1];
         const uint32_t deg = (uint32_t)(ae - ab);
-        bool fits = deg <= SMALL_CAP;
-        uint32_t m = 0, dlast = 1;
-        if (fits) {
+        uint32_t m;
+        bool direct = deg >= C;  // the first C of the sorted adjacency
+        if (direct) {
+            m = C;
+        } else {
             for (uint32_t x = lane; x < deg; x += 32) buf[x] = (a.col[ab + x] << 4) | 1u;
             m = deg;
             __syncwarp();
-        }
-        // further levels while fewer than row_cap nodes are known
-        for (uint32_t d = 2; fits && d <= a.k && m < a.row_cap; ++d) {
-            const uint32_t m0 = m;
-            uint32_t add = 0;
-            // the adjacencies of the level-(d-1) nodes, 32 list entries at a time
-            for (uint32_t c = 0; c < m0 && fits; c += 32) {
-                uint64_t st = 0;
-                uint32_t dg = 0;
-                if (c + lane < m0 && (buf[c + lane] & 15u) == d - 1) {
-                    const uint32_t u = buf[c + lane] >> 4;
-                    st = a.rp[u];
-                    dg = (uint32_t)(a.rp[u + 1] - st);
-                }
-                const uint32_t incl = warp_incl_scan(dg, lane);
-                const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                const uint32_t excl = incl - dg;
-                if (m0 + add + tot > SMALL_CAP) {
-                    fits = false;
-                    break;
-                }
-                for (uint32_t x0 = 0; x0 < tot; x0 += 32) {
+            for (uint32_t d = 2; d <= a.k && m < C; ++d) {
+                // the level-(d-1) nodes, copied out of the buffer
+                uint32_t nf = 0;
+                for (uint32_t x0 = 0; x0 < m; x0 += 32) {
                     const uint32_t x = x0 + lane;
-                    uint32_t lo = 0, hi = 32;
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
-                    }
-                    const uint64_t so = __shfl_sync(0xFFFFFFFFu, st, lo);
-                    const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
-                    uint32_t key = 0xFFFFFFFFu;
-                    if (x < tot) {
-                        const uint32_t v = a.col[so + (x - eo)];
-                        if (v != row) key = (v << 4) | d;
-                    }
-                    const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
-                    if (key != 0xFFFFFFFFu) buf[m0 + add + __popc(keep & lanemask_lt())] = key;
-                    add += __popc(keep);
+                    const bool f = x < m && (buf[x] & 15u) == d - 1;
+                    const uint32_t fb = __ballot_sync(0xFFFFFFFFu, f);
+                    if (f) fr[nf + __popc(fb & lanemask_lt())] = buf[x] >> 4;
+                    nf += __popc(fb);
                 }
                 __syncwarp();
+                if (nf == 0) break;
+                const uint32_t lower = m;
+                uint32_t mm = m;
+                for (uint32_t c = 0; c < nf; c += 32) {
+                    uint64_t st = 0;
+                    uint32_t dg = 0;
+                    if (c + lane < nf) {
+                        const uint32_t u = fr[c + lane];
+                        st = a.rp[u];
+                        dg = (uint32_t)(a.rp[u + 1] - st);
+                    }
+                    const uint32_t incl = warp_incl_scan(dg, lane);
+                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                    const uint32_t excl = incl - dg;
+                    for (uint32_t x0 = 0; x0 < tot; x0 += 32) {
+                        if (mm + 32 > CAPW_BUF) mm = capw_flush(buf, mm, lower, C, d, lane);
+                        const uint32_t x = x0 + lane;
+                        uint32_t lo = 0, hi = 32;
+                        while (hi - lo > 1) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
+                        }
+                        const uint64_t so = __shfl_sync(0xFFFFFFFFu, st, lo);
+                        const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                        uint32_t key = 0xFFFFFFFFu;
+                        if (x < tot) {
+                            const uint32_t v = a.col[so + (x - eo)];
+                            if (v != row) key = (v << 4) | d;
+                        }
+                        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
+                        if (key != 0xFFFFFFFFu) buf[mm + __popc(keep & lanemask_lt())] = key;
+                        mm += __popc(keep);
+                        __syncwarp();
+                    }
+                }
+                m = capw_flush(buf, mm, lower, C, d, lane);
+                if (m == lower) break;  // no new node: nothing further either
             }
-            if (!fits) break;
-            if (add == 0) break;
-            warp_bitonic(buf, m0 + add, lane);
-            m = warp_unique(buf, m0 + add, lane);
-            dlast = d;
-            if (m == m0) break;  // no new node: nothing further either
         }
-        if (!fits) {
-            if (lane == 0) big[atomicAdd(nbig, 1u)] = row;
-            __syncwarp();
-            continue;
-        }
-        // nodes before the last level, and how many of the last level stay
-        uint32_t last = 0;
-        for (uint32_t x = lane; x < m; x += 32) last += (buf[x] & 15u) == dlast ? 1u : 0u;
-#pragma unroll
-        for (int off = 16; off; off >>= 1) last += __shfl_xor_sync(0xFFFFFFFFu, last, off);
-        const uint32_t keep_last = m <= a.row_cap ? last : a.row_cap - (m - last);
-        const uint32_t total = (m - last) + keep_last;
         uint64_t base = 0;
         int skip = 0;
         if (lane == 0) {
-            a.counts[row] = total;
-            const uint64_t span = ((uint64_t)total + 15) & ~15ull;
+            a.counts[row] = m;
+            const uint64_t span = ((uint64_t)m + 15) & ~15ull;
             base = atomicAdd(a.cursor, (unsigned long long)span);
             if (base + span > a.cap) {
                 skip = 1;
@@ -664,22 +685,14 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_cap_small(BfsArgs a, uint3
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         skip = __shfl_sync(0xFFFFFFFFu, skip, 0);
         if (!skip) {
-            uint64_t o = base;
-            uint32_t seen_last = 0;
-            for (uint32_t x0 = 0; x0 < m; x0 += 32) {
-                const uint32_t x = x0 + lane;
-                const uint32_t key = x < m ? buf[x] : 0u;
-                const bool is_last = x < m && (key & 15u) == dlast;
-                const uint32_t lb = __ballot_sync(0xFFFFFFFFu, is_last);
-                const bool take = x < m && (!is_last || seen_last + __popc(lb & lanemask_lt()) < keep_last);
-                const uint32_t tb = __ballot_sync(0xFFFFFFFFu, take);
-                if (take) {
-                    const uint64_t at = o + __popc(tb & lanemask_lt());
-                    a.out_col[at] = key >> 4;
-                    a.out_dist[at] = (uint8_t)(key & 15u);
+            for (uint32_t x = lane; x < m; x += 32) {
+                if (direct) {
+                    a.out_col[base + x] = a.col[ab + x];
+                    a.out_dist[base + x] = 1;
+                } else {
+                    a.out_col[base + x] = buf[x] >> 4;
+                    a.out_dist[base + x] = (uint8_t)(buf[x] & 15u);
                 }
-                o += __popc(tb);
-                seen_last += __popc(lb);
             }
         }
         __syncwarp();
@@ -907,26 +920,20 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
             DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
             a.rows = big.p;
             a.nrows = nc[1];
-        } else if (row_cap && n <= (1u << 28) && cap > 0) {
-            // capped rows: one warp each where the levels fit, the rest by blocks
-            big = DBuf<uint32_t>(ctx, n);
-            DBuf<uint32_t> nb(ctx, 1);
-            DRG_CUDA(cudaMemsetAsync(nb.p, 0, 4, ctx->stream));
-            const size_t ssm = (size_t)SMALL_WARPS * SMALL_CAP * 4;
+        } else if (row_cap && row_cap <= CAPW_MAX && n <= (1u << 28) && cap > 0) {
+            // capped rows of a small cap: every row by one warp
+            const size_t ssm = (size_t)CAPW_WARPS * (CAPW_BUF + CAPW_FRONT) * 4;
             DRG_CUDA(cudaFuncSetAttribute(k_cap_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
             int sper = 0;
-            DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, k_cap_small, SMALL_WARPS * 32, ssm));
+            DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, k_cap_small, CAPW_WARPS * 32, ssm));
             BfsArgs as = a;
             as.rows = nullptr;
             as.nrows = n;
-            DRG_LAUNCH(ctx, k_cap_small, (uint32_t)ctx->num_sms * (uint32_t)(sper > 0 ? sper : 1), SMALL_WARPS * 32,
-                       ssm, as, big.p, nb.p);
-            const uint32_t nbig = read1(ctx, nb.p);
-            DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
-            a.rows = big.p;
-            a.nrows = nbig;
+            DRG_LAUNCH(ctx, k_cap_small, (uint32_t)ctx->num_sms * (uint32_t)(sper > 0 ? sper : 1), CAPW_WARPS * 32,
+                       ssm, as);
+            a.nrows = 0;  // no row left for the block kernel
         }
-        DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
+        if (a.nrows) DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
     }
     DBuf<uint64_t> tot(ctx, 1);
     scan<uint64_t>(ctx, LoadArr<uint64_t>{counts.p}, n, d->rp, false, tot.p);

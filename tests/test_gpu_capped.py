@@ -3,7 +3,8 @@
 feasible) against the oracle's korder_capped / similarity_capped: the union
 pattern K u K^T, hop distances, Z over each kept set, the quantised weights,
 the row sums and both alias tables bit for bit on small graphs (caps that bind
-at level 1, 2 and 3, ragged inputs, and a cap that does not bind); at full
+at level 1, 2 and 3, ragged inputs, a cap above what one warp's buffer
+takes, and a cap that does not bind); at full
 size (DC-SBM 1M nodes, k = 3, where the uncapped matrix would exceed 2^32
 entries) sampled rows are checked against single-row traversals of the
 oracle."""
@@ -36,7 +37,7 @@ GRAPHS = {
 
 @pytest.mark.parametrize("name,k,cap", [("ba2000", 1, 3), ("ba2000", 2, 8), ("ba2000", 3, 40), ("grid32", 3, 10),
                                         ("grid32", 2, 10 ** 6), ("tree3000", 3, 4), ("er_ragged", 2, 5),
-                                        ("er_ragged", 3, 17)])
+                                        ("er_ragged", 3, 17), ("ba2000", 3, 600)])
 def test_capped_matrix_matches_oracle(env, orc, name, k, cap):
     drg, ctx = env
     g = GRAPHS[name]()
