@@ -526,29 +526,37 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
 // known nodes as sorted keys (v << 4 | d) in shared memory -- level 1 is the
 // source's sorted adjacency -- and grows them a level at a time while fewer
 // than row_cap nodes are known: the adjacencies of the last level's nodes
-// stream through the buffer as keys (v << 4 | d); whenever it fills, and at
-// the end of the level, the keys are sorted (bitonic), only the first key of
-// each node is kept (its smallest distance) and, once more than row_cap
-// nodes are known, the new level is cut to its row_cap - (nodes before it)
-// smallest ids.  A node cut that way never returns: at least that many
-// smaller ids of the level are kept.  The row is written in id order to the
-// staging area.  A source of degree >= row_cap keeps the first row_cap of its
-// sorted adjacency directly.
+// stream through the buffer as keys; whenever it fills, and at the end of the
+// level, the keys are sorted (bitonic), only the first key of each node is
+// kept (its smallest distance) and, once more than row_cap nodes are known,
+// the new level is cut to its row_cap - (nodes before it) smallest ids.  A
+// node cut that way never returns: at least that many smaller ids of the
+// level are kept.  From the first cut on, the largest kept id of the level
+// bounds what can still enter, so the candidates at or above it are dropped
+// as they are read, and each adjacency (sorted by id) is read only up to it.
+// The row is written in id order to the staging area.  A source of degree
+// >= row_cap keeps the first row_cap of its sorted adjacency directly.
 constexpr uint32_t CAPW_BUF = 1024, CAPW_FRONT = 512;
 constexpr uint32_t CAPW_MAX = CAPW_FRONT - 32;  // largest row_cap this kernel takes
 constexpr int CAPW_WARPS = 8;
 
+// Ascending bitonic sort of buf[0, m) (m <= CAPW_BUF) by one warp; pads to a
+// power of two with all-ones keys.
 __device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t lane) {
-    uint32_t P = 1;
-    while (P < m) P <<= 1;
+    uint32_t P = 1, lp = 0;
+    while (P < m) {
+        P <<= 1;
+        ++lp;
+    }
     for (uint32_t x = m + lane; x < P; x += 32) buf[x] = 0xFFFFFFFFu;
     __syncwarp();
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+    for (uint32_t lk = 1; lk <= lp; ++lk) {
+        for (int lj = (int)lk - 1; lj >= 0; --lj) {
+            const uint32_t j = 1u << lj;
             for (uint32_t t = lane; t < P / 2; t += 32) {
-                const uint32_t i = (t / j) * 2 * j + (t % j), l = i + j;
+                const uint32_t i = ((t >> lj) << (lj + 1)) | (t & (j - 1)), l = i + j;
                 const uint32_t u = buf[i], w = buf[l];
-                if ((u > w) == ((i & k) == 0)) {
+                if ((u > w) == (((i >> lk) & 1u) == 0)) {
                     buf[i] = w;
                     buf[l] = u;
                 }
@@ -560,9 +568,10 @@ __device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t
 
 // Sorts buf[0, m), keeps the first key of each node and, when more than cap
 // nodes remain, only the first cap - lower keys of level d (lower = nodes of
-// the levels before d, all kept).  Returns the new size (<= cap when cut).
+// the levels before d, all kept); *tau becomes the largest id of level d
+// kept after such a cut.  Returns the new size (cap when cut).
 __device__ __forceinline__ uint32_t capw_flush(uint32_t* buf, uint32_t m, uint32_t lower, uint32_t cap, uint32_t d,
-                                               uint32_t lane) {
+                                               uint32_t lane, uint32_t* tau) {
     warp_bitonic(buf, m, lane);
     // first key of each node (in place)
     uint32_t out = 0, prev = 0xFFFFFFFFu;
@@ -582,7 +591,7 @@ __device__ __forceinline__ uint32_t capw_flush(uint32_t* buf, uint32_t m, uint32
     if (out <= cap) return out;
     // keep the levels before d and the first cap - lower nodes of level d (in place)
     const uint32_t keep_d = cap - lower;
-    uint32_t kept = 0, seen_d = 0;
+    uint32_t kept = 0, seen_d = 0, last_d = 0;
     for (uint32_t x0 = 0; x0 < out; x0 += 32) {
         const uint32_t x = x0 + lane;
         const uint32_t key = x < out ? buf[x] : 0u;
@@ -590,13 +599,27 @@ __device__ __forceinline__ uint32_t capw_flush(uint32_t* buf, uint32_t m, uint32
         const uint32_t db = __ballot_sync(0xFFFFFFFFu, at_d);
         const bool take = x < out && (!at_d || seen_d + __popc(db & lanemask_lt()) < keep_d);
         const uint32_t tb = __ballot_sync(0xFFFFFFFFu, take);
+        const uint32_t tdb = tb & db;
+        if (tdb) last_d = __shfl_sync(0xFFFFFFFFu, key, 31 - __clz(tdb)) >> 4;
         __syncwarp();
         if (take) buf[kept + __popc(tb & lanemask_lt())] = key;
         kept += __popc(tb);
         seen_d += __popc(db);
         __syncwarp();
     }
+    *tau = last_d;
     return kept;
+}
+
+// First index in [lo, hi) whose col entry is >= tau (hi if none); col is
+// ascending there.
+__device__ __forceinline__ uint64_t capw_clip(const uint32_t* __restrict__ col, uint64_t lo, uint64_t hi,
+                                              uint32_t tau) {
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (col[mid] < tau) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
 __global__ void __launch_bounds__(CAPW_WARPS * 32) k_cap_small(BfsArgs a) {
@@ -633,40 +656,51 @@ __global__ void __launch_bounds__(CAPW_WARPS * 32) k_cap_small(BfsArgs a) {
                 __syncwarp();
                 if (nf == 0) break;
                 const uint32_t lower = m;
-                uint32_t mm = m;
+                uint32_t mm = m, tau = 0xFFFFFFFFu;
                 for (uint32_t c = 0; c < nf; c += 32) {
-                    uint64_t st = 0;
-                    uint32_t dg = 0;
+                    // each lane walks one frontier node's adjacency [cur, end)
+                    uint64_t cur = 0, end = 0;
                     if (c + lane < nf) {
                         const uint32_t u = fr[c + lane];
-                        st = a.rp[u];
-                        dg = (uint32_t)(a.rp[u + 1] - st);
+                        cur = a.rp[u];
+                        end = a.rp[u + 1];
                     }
-                    const uint32_t incl = warp_incl_scan(dg, lane);
-                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                    const uint32_t excl = incl - dg;
-                    for (uint32_t x0 = 0; x0 < tot; x0 += 32) {
-                        if (mm + 32 > CAPW_BUF) mm = capw_flush(buf, mm, lower, C, d, lane);
-                        const uint32_t x = x0 + lane;
-                        uint32_t lo = 0, hi = 32;
-                        while (hi - lo > 1) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
+                    if (tau != 0xFFFFFFFFu) end = capw_clip(a.col, cur, end, tau);
+                    for (;;) {
+                        const uint64_t r64 = end - cur;
+                        const uint32_t rem = r64 > (1ull << 26) ? (1u << 26) : (uint32_t)r64;
+                        const uint32_t incl = warp_incl_scan(rem, lane);
+                        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                        if (tot == 0) break;
+                        const uint32_t excl = incl - rem;
+                        const uint32_t take = min(tot, CAPW_BUF - mm);
+                        for (uint32_t x0 = 0; x0 < take; x0 += 32) {
+                            const uint32_t x = x0 + lane;
+                            uint32_t lo = 0, hi = 32;
+                            while (hi - lo > 1) {
+                                const uint32_t mid = (lo + hi) >> 1;
+                                if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
+                            }
+                            const uint64_t so = __shfl_sync(0xFFFFFFFFu, cur, lo);
+                            const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                            uint32_t key = 0xFFFFFFFFu;
+                            if (x < take) {
+                                const uint32_t v = a.col[so + (x - eo)];
+                                if (v != row && v < tau) key = (v << 4) | d;
+                            }
+                            const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
+                            if (key != 0xFFFFFFFFu) buf[mm + __popc(keep & lanemask_lt())] = key;
+                            mm += __popc(keep);
+                            __syncwarp();
                         }
-                        const uint64_t so = __shfl_sync(0xFFFFFFFFu, st, lo);
-                        const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
-                        uint32_t key = 0xFFFFFFFFu;
-                        if (x < tot) {
-                            const uint32_t v = a.col[so + (x - eo)];
-                            if (v != row) key = (v << 4) | d;
+                        cur += min(rem, take > excl ? take - excl : 0u);
+                        if (take < tot) {  // the buffer is full
+                            mm = capw_flush(buf, mm, lower, C, d, lane, &tau);
+                            if (tau != 0xFFFFFFFFu) end = capw_clip(a.col, cur, end, tau);
                         }
-                        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
-                        if (key != 0xFFFFFFFFu) buf[mm + __popc(keep & lanemask_lt())] = key;
-                        mm += __popc(keep);
-                        __syncwarp();
                     }
                 }
-                m = capw_flush(buf, mm, lower, C, d, lane);
+                m = capw_flush(buf, mm, lower, C, d, lane, &tau);
                 if (m == lower) break;  // no new node: nothing further either
             }
         }
