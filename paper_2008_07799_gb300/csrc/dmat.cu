@@ -1001,44 +1001,102 @@ struct Gauss {
 };
 
 // ------------------------------------------------------------------ row cap: the union pattern
-// Kept rows K (each row's row_cap nearest nodes) -> the sampling pattern
-// K u K^T: every kept pair in both orientations, sorted by (row, column), the
-// equal keys of a pair kept in both rows merged; each entry of the union
-// carries flag 1 (j in K_i, "own") and / or flag 2 (i in K_j, "back").
-__global__ void k_cap_pairs(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
-                            const uint8_t* __restrict__ dist, uint64_t nK, uint32_t cb, uint64_t* __restrict__ keys,
-                            uint32_t* __restrict__ vals) {
+// Kept rows K (each row's row_cap nearest nodes, sorted by (row, column)) ->
+// the sampling pattern K u K^T, sorted by (row, column); each entry carries
+// flag 1 (j in K_i, "own") and / or flag 2 (i in K_j, "back").  T = K^T is
+// K's entries sorted stably by their column, so T_i lists, in ascending j,
+// the rows j that kept i.  A pair kept on both sides appears once in K_i and
+// once in T_i ("dup"); row i of the union is K_i merged with T_i \ K_i, and
+// the place of each entry in it is the count of union entries below it:
+//   j in K_i at index a:       a + #{T_i < j} - #{dups of K_i before a}
+//   j in T_i \ K_i at index b: b + #{K_i < j} - #{dups of K_i below j}
+
+// T's keys: row j of the transposed entry in the low 32 bits, hop distance
+// above; values: the column (= the kept row's source).
+__global__ void k_cap_transpose(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
+                                const uint8_t* __restrict__ dist, uint64_t nK, uint64_t* __restrict__ tkey,
+                                uint32_t* __restrict__ tval) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nK; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i = esrc[e], j = col[e];
-        const uint32_t dd = dist[e];
-        keys[2 * e] = (i << cb) | j;
-        vals[2 * e] = dd | 0x100u;
-        keys[2 * e + 1] = (j << cb) | i;
-        vals[2 * e + 1] = dd | 0x200u;
+        tkey[e] = (uint64_t)col[e] | ((uint64_t)dist[e] << 32);
+        tval[e] = esrc[e];
     }
 }
 
-__global__ void k_cap_heads(const uint64_t* __restrict__ keys, uint64_t m, uint32_t* __restrict__ head) {
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < m; x += (uint64_t)gridDim.x * blockDim.x)
-        head[x] = (x == 0 || keys[x] != keys[x - 1]) ? 1u : 0u;
+// Row pointers of keys sorted by row (low 32 bits): the first entry of each
+// row writes the pointers of the rows after the previous entry's row up to
+// its own, the last entry those of the rows after it.
+__global__ void k_rows_of_sorted(const uint64_t* __restrict__ key, uint64_t m, uint32_t n, uint32_t* __restrict__ rp) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < m; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = (uint32_t)key[x];
+        if (x + 1 == m)
+            for (uint64_t t = i + 1; t <= n; ++t) rp[t] = (uint32_t)m;
+        const uint64_t from = x == 0 ? 0 : (uint64_t)(uint32_t)key[x - 1] + 1;
+        for (uint64_t t = from; t <= i; ++t) rp[t] = (uint32_t)x;
+    }
 }
 
-// The first key of each run (a run holds one pair, once or twice) writes the
-// union entry at its place pos[x]; rows are counted for the row pointers.
-__global__ void k_cap_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                             const uint32_t* __restrict__ head, const uint32_t* __restrict__ pos, uint64_t m,
-                             uint32_t cb, uint32_t* __restrict__ ucol, uint8_t* __restrict__ udist,
-                             uint8_t* __restrict__ uflag, unsigned long long* __restrict__ rowcnt) {
-    const uint64_t mask = (1ull << cb) - 1;
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < m; x += (uint64_t)gridDim.x * blockDim.x) {
-        if (!head[x]) continue;
-        uint32_t f = vals[x] >> 8;
-        if (x + 1 < m && keys[x + 1] == keys[x]) f |= vals[x + 1] >> 8;
-        const uint32_t p = pos[x];
-        ucol[p] = (uint32_t)(keys[x] & mask);
-        udist[p] = (uint8_t)(vals[x] & 0xFFu);
-        uflag[p] = (uint8_t)f;
-        atomicAdd(&rowcnt[keys[x] >> cb], 1ull);
+// First index in [lo, hi) of a sorted u32 array holding a value >= v.
+__device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t* __restrict__ a, uint64_t lo, uint64_t hi,
+                                                    uint32_t v) {
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// For each entry e = (i, j) of K: tlo[e] = #{T_i < j} and dup[e] = (j in T_i).
+__global__ void k_cap_dups(const uint64_t* __restrict__ rpK, const uint32_t* __restrict__ esrc,
+                           const uint32_t* __restrict__ col, const uint32_t* __restrict__ rpT,
+                           const uint32_t* __restrict__ tval, uint64_t nK, uint32_t* __restrict__ tlo,
+                           uint32_t* __restrict__ dup) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nK; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = esrc[e], j = col[e];
+        const uint64_t t0 = rpT[i], t1 = rpT[i + 1];
+        const uint64_t lb = lower_bound_u32(tval, t0, t1, j);
+        tlo[e] = (uint32_t)(lb - t0);
+        dup[e] = (lb < t1 && tval[lb] == j) ? 1u : 0u;
+    }
+}
+
+// Union row sizes |K_i| + |T_i| - dups_i (dpre: exclusive prefix of dup over
+// K, with the total at index nK).
+__global__ void k_cap_rowsize(const uint64_t* __restrict__ rpK, const uint32_t* __restrict__ rpT,
+                              const uint32_t* __restrict__ dpre, uint32_t n, uint64_t* __restrict__ cnt) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        cnt[i] = (rpK[i + 1] - rpK[i]) + (rpT[i + 1] - rpT[i]) - (dpre[rpK[i + 1]] - dpre[rpK[i]]);
+}
+
+__global__ void k_cap_write_own(const uint64_t* __restrict__ rpK, const uint32_t* __restrict__ esrc,
+                                const uint32_t* __restrict__ col, const uint8_t* __restrict__ dist,
+                                const uint32_t* __restrict__ tlo, const uint32_t* __restrict__ dup,
+                                const uint32_t* __restrict__ dpre, const uint64_t* __restrict__ rpU, uint64_t nK,
+                                uint32_t* __restrict__ ucol, uint8_t* __restrict__ udist, uint8_t* __restrict__ uflag) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nK; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = esrc[e];
+        const uint64_t k0 = rpK[i];
+        const uint64_t p = rpU[i] + (e - k0) + tlo[e] - (dpre[e] - dpre[k0]);
+        ucol[p] = col[e];
+        udist[p] = dist[e];
+        uflag[p] = (uint8_t)(1u | (dup[e] << 1));
+    }
+}
+
+__global__ void k_cap_write_back(const uint64_t* __restrict__ rpK, const uint32_t* __restrict__ col,
+                                 const uint32_t* __restrict__ rpT, const uint64_t* __restrict__ tkey,
+                                 const uint32_t* __restrict__ tval, const uint32_t* __restrict__ dpre,
+                                 const uint64_t* __restrict__ rpU, uint64_t nK, uint32_t* __restrict__ ucol,
+                                 uint8_t* __restrict__ udist, uint8_t* __restrict__ uflag) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nK; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = tkey[x];
+        const uint32_t i = (uint32_t)key, j = tval[x];
+        const uint64_t k0 = rpK[i], k1 = rpK[i + 1];
+        const uint64_t ub = lower_bound_u32(col, k0, k1, j);
+        if (ub < k1 && col[ub] == j) continue;  // kept by both: written as i's own entry
+        const uint64_t p = rpU[i] + (x - rpT[i]) + (ub - k0) - (dpre[ub] - dpre[k0]);
+        ucol[p] = j;
+        udist[p] = (uint8_t)(key >> 32);
+        uflag[p] = 2u;
     }
 }
 
@@ -1067,24 +1125,6 @@ __global__ void k_row_Z_own(const uint64_t* __restrict__ rp, const uint8_t* __re
             z = __fadd_rn(z, __fmul_rn((float)t, gs.g[c]));
         }
         if (lane == 0) Z[i] = z;
-    }
-}
-
-// q over the union: fl32(a + b) 2^30 truncated, a = fl32(g/Z_i) when the
-// entry is in K_i, b = fl32(g/Z_j) when it is in K_j, each else 0; r_i the
-// row sums (r must start at zero).
-__global__ void k_quantise_flags(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
-                                 const uint8_t* __restrict__ dist, const uint8_t* __restrict__ flag,
-                                 const float* __restrict__ Z, Gauss gs, uint64_t nnz, uint32_t* __restrict__ q,
-                                 unsigned long long* __restrict__ r) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t i = esrc[e], j = col[e], f = flag[e];
-        const float g = gs.g[dist[e] - 1];
-        const float av = (f & 1u) ? __fdiv_rn(g, Z[i]) : 0.f;
-        const float bv = (f & 2u) ? __fdiv_rn(g, Z[j]) : 0.f;
-        const uint32_t qe = __float2uint_rz(__fmul_rn(__fadd_rn(av, bv), 1073741824.0f));
-        q[e] = qe;
-        atomicAdd(&r[i], (unsigned long long)qe);
     }
 }
 
@@ -1233,13 +1273,17 @@ __device__ __forceinline__ uint32_t quantise1(float gd, float zi, float zj) {
 // so a thread adds any run of its own entries that ends inside its four, and
 // the warp sums the open runs by row (segmented suffix sums over the lanes)
 // and adds each row's total with one atomic.  r must start at zero.
-// With PERNODE the two conditional similarities come from the calibrated
-// per-node table W (fl32(g_i(d) / Z_i), row-major n x k) instead.
-template <bool PERNODE>
+// Kinds: Q_GLOBAL_SIGMA uses g(d) / Z; Q_PER_NODE takes the two conditional
+// similarities from the calibrated per-node table W (fl32(g_i(d) / Z_i),
+// row-major n x k); Q_CAPPED (the union of kept rows) takes fl32(g/Z_i) only
+// where the entry's flag has bit 1 (j in K_i) and fl32(g/Z_j) only where it
+// has bit 2 (i in K_j), each else 0.
+enum { Q_GLOBAL_SIGMA = 0, Q_PER_NODE = 1, Q_CAPPED = 2 };
+template <int KIND>
 __global__ void k_quantise_r(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col,
                              const uint8_t* __restrict__ dist, const float* __restrict__ Z, Gauss gs, uint64_t nnz,
                              uint32_t* __restrict__ q, unsigned long long* __restrict__ r,
-                             const float* __restrict__ W, uint32_t k) {
+                             const float* __restrict__ W, uint32_t k, const uint8_t* __restrict__ flag) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t nv = (nnz + 3) / 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -1250,15 +1294,19 @@ __global__ void k_quantise_r(const uint32_t* __restrict__ esrc, const uint32_t* 
         if (v < nv) {
             const uint64_t e = 4 * v;
             const uint32_t cnt = nnz - e < 4 ? (uint32_t)(nnz - e) : 4u;
-            uint32_t ii[4], jj[4], dd[4], qq[4];
+            uint32_t ii[4], jj[4], dd[4], ff[4], qq[4];
             if (cnt == 4) {
                 const uint4 a4 = __ldg(reinterpret_cast<const uint4*>(esrc + e));
                 const uint4 b4 = __ldg(reinterpret_cast<const uint4*>(col + e));
                 const uint32_t dw = __ldg(reinterpret_cast<const uint32_t*>(dist + e));
+                const uint32_t fw = KIND == Q_CAPPED ? __ldg(reinterpret_cast<const uint32_t*>(flag + e)) : 0u;
                 ii[0] = a4.x; ii[1] = a4.y; ii[2] = a4.z; ii[3] = a4.w;
                 jj[0] = b4.x; jj[1] = b4.y; jj[2] = b4.z; jj[3] = b4.w;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) dd[t] = (dw >> (8 * t)) & 0xFFu;
+                for (int t = 0; t < 4; ++t) {
+                    dd[t] = (dw >> (8 * t)) & 0xFFu;
+                    ff[t] = (fw >> (8 * t)) & 0xFFu;
+                }
             } else {
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -1266,13 +1314,19 @@ __global__ void k_quantise_r(const uint32_t* __restrict__ esrc, const uint32_t* 
                     ii[t] = ok ? esrc[e + t] : 0u;
                     jj[t] = ok ? col[e + t] : 0u;
                     dd[t] = ok ? dist[e + t] : 1u;
+                    ff[t] = (KIND == Q_CAPPED && ok) ? flag[e + t] : 0u;
                 }
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                if (PERNODE) {
+                if (KIND == Q_PER_NODE) {
                     const float s = __fadd_rn(W[(uint64_t)ii[t] * k + dd[t] - 1], W[(uint64_t)jj[t] * k + dd[t] - 1]);
                     qq[t] = __float2uint_rz(__fmul_rn(s, 1073741824.0f));
+                } else if (KIND == Q_CAPPED) {
+                    const float g = gs.g[dd[t] - 1];
+                    const float av = (ff[t] & 1u) ? __fdiv_rn(g, Z[ii[t]]) : 0.f;
+                    const float bv = (ff[t] & 2u) ? __fdiv_rn(g, Z[jj[t]]) : 0.f;
+                    qq[t] = __float2uint_rz(__fmul_rn(__fadd_rn(av, bv), 1073741824.0f));
                 } else {
                     qq[t] = quantise1(gs.g[dd[t] - 1], Z[ii[t]], Z[jj[t]]);
                 }
@@ -1795,40 +1849,44 @@ static DBuf<uint8_t> cap_union(drg_ctx* ctx, drg_dmat* d) {
     const uint32_t n = d->n;
     const uint64_t nK = d->nnz;
     DRG_CHECK(2 * nK < (1ull << 32), DRG_EUNSUPPORTED, "the capped rows hold 2^31 entries or more");
-    const uint64_t m = 2 * nK;
     const uint32_t cb = (uint32_t)std::max(1, bitlen(n > 1 ? n - 1 : 1));
-    DBuf<uint64_t> keys(ctx, m), kalt(ctx, m);
-    DBuf<uint32_t> vals(ctx, m), valt(ctx, m);
-    {
-        DBuf<uint32_t> esrc(ctx, nK);
-        DRG_LAUNCH(ctx, k_expand_rows, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, d->rp, n,
-                   esrc.p);
-        DRG_LAUNCH(ctx, k_cap_pairs, grid_for(nK, 256, 65536), 256, 0, esrc.p, d->col, d->dist, nK, cb, keys.p,
-                   vals.p);
-    }
-    uint64_t* kp = keys.p;
-    uint64_t* ap = kalt.p;
-    uint32_t* vp = vals.p;
-    uint32_t* vq = valt.p;
-    radix_sort(ctx, kp, ap, vp, vq, m, 0, (int)(2 * cb));
-    DBuf<uint32_t> head(ctx, m), pos(ctx, m), nu_d(ctx, 1);
-    DRG_LAUNCH(ctx, k_cap_heads, grid_for(m, 256, 65536), 256, 0, kp, m, head.p);
-    scan<uint32_t>(ctx, LoadArr<uint32_t>{head.p}, m, pos.p, false, nu_d.p);
-    const uint32_t nu = read1(ctx, nu_d.p);
+    const uint32_t gk = grid_for(nK, 256, 65536);
+    DBuf<uint32_t> esrc(ctx, nK);
+    DRG_LAUNCH(ctx, k_expand_rows, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, d->rp, n,
+               esrc.p);
+    // T = K^T sorted by row (stable: ascending column within a row)
+    DBuf<uint64_t> tkey(ctx, nK), tkalt(ctx, nK);
+    DBuf<uint32_t> tval(ctx, nK), tvalt(ctx, nK);
+    DRG_LAUNCH(ctx, k_cap_transpose, gk, 256, 0, esrc.p, d->col, d->dist, nK, tkey.p, tval.p);
+    uint64_t* kp = tkey.p;
+    uint64_t* ap = tkalt.p;
+    uint32_t* vp = tval.p;
+    uint32_t* vq = tvalt.p;
+    radix_sort(ctx, kp, ap, vp, vq, nK, 0, (int)cb);
+    DBuf<uint32_t> rpT(ctx, (size_t)n + 1);
+    DRG_LAUNCH(ctx, k_rows_of_sorted, gk, 256, 0, kp, nK, n, rpT.p);
+    // pairs kept on both sides, and each own entry's count of smaller back entries
+    DBuf<uint32_t> tlo(ctx, nK), dup(ctx, nK), dpre(ctx, nK + 1);
+    DRG_LAUNCH(ctx, k_cap_dups, gk, 256, 0, d->rp, esrc.p, d->col, rpT.p, vp, nK, tlo.p, dup.p);
+    scan<uint32_t>(ctx, LoadArr<uint32_t>{dup.p}, nK, dpre.p, false, dpre.p + nK);
+    DBuf<uint64_t> cnt(ctx, n), rpU(ctx, (size_t)n + 1), tot(ctx, 1);
+    DRG_LAUNCH(ctx, k_cap_rowsize, grid_for(n, 256, 65536), 256, 0, d->rp, rpT.p, dpre.p, n, cnt.p);
+    scan<uint64_t>(ctx, LoadArr<uint64_t>{cnt.p}, n, rpU.p, false, tot.p);
+    const uint64_t nu = read1(ctx, tot.p);
+    uint32_t* ucol = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (nu ? nu : 1)));
+    uint8_t* udist = static_cast<uint8_t*>(dalloc(ctx, dist_bytes(nu)));
+    DRG_CUDA(cudaMemsetAsync(udist, 0, dist_bytes(nu), ctx->stream));
+    DBuf<uint8_t> flag(ctx, nu);
+    DRG_LAUNCH(ctx, k_cap_write_own, gk, 256, 0, d->rp, esrc.p, d->col, d->dist, tlo.p, dup.p, dpre.p, rpU.p, nK,
+               ucol, udist, flag.p);
+    DRG_LAUNCH(ctx, k_cap_write_back, gk, 256, 0, d->rp, d->col, rpT.p, kp, vp, dpre.p, rpU.p, nK, ucol, udist,
+               flag.p);
+    d2d(ctx, d->rp, rpU.p, (size_t)n);
+    d2d(ctx, d->rp + n, tot.p, 1);
     dfree(ctx, d->col);
     dfree(ctx, d->dist);
-    d->col = nullptr;
-    d->dist = nullptr;
-    d->col = static_cast<uint32_t*>(dalloc(ctx, sizeof(uint32_t) * (nu ? nu : 1)));
-    d->dist = static_cast<uint8_t*>(dalloc(ctx, dist_bytes(nu)));
-    DRG_CUDA(cudaMemsetAsync(d->dist, 0, dist_bytes(nu), ctx->stream));
-    DBuf<uint8_t> flag(ctx, nu);
-    DBuf<uint64_t> cnt(ctx, n), tot(ctx, 1);
-    DRG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(uint64_t) * n, ctx->stream));
-    DRG_LAUNCH(ctx, k_cap_unique, grid_for(m, 256, 65536), 256, 0, kp, vp, head.p, pos.p, m, cb, d->col, d->dist,
-               flag.p, reinterpret_cast<unsigned long long*>(cnt.p));
-    scan<uint64_t>(ctx, LoadArr<uint64_t>{cnt.p}, n, d->rp, false, tot.p);
-    d2d(ctx, d->rp + n, tot.p, 1);
+    d->col = ucol;
+    d->dist = udist;
     d->nnz = nu;
     return flag;
 }
@@ -1883,15 +1941,17 @@ drg_dmat* build_dmat(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma, 
         DBuf<uint32_t> esrc(ctx, nnz);
         DRG_LAUNCH(ctx, k_expand_rows, gw, 256, 0, d->rp, n, esrc.p);
         DRG_CUDA(cudaMemsetAsync(d->r, 0, sizeof(uint64_t) * n, ctx->stream));
+        const uint32_t gq = grid_for((nnz + 3) / 4, 256, 65536);
+        unsigned long long* rr = reinterpret_cast<unsigned long long*>(d->r);
         if (row_cap)
-            DRG_LAUNCH(ctx, k_quantise_flags, grid_for(nnz, 256, 65536), 256, 0, esrc.p, d->col, d->dist, flag.p,
-                       d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r));
+            DRG_LAUNCH(ctx, k_quantise_r<Q_CAPPED>, gq, 256, 0, esrc.p, d->col, d->dist, d->Z, gs, nnz, d->q, rr,
+                       (const float*)nullptr, k, (const uint8_t*)flag.p);
         else if (perplexity > 0.f)
-            DRG_LAUNCH(ctx, k_quantise_r<true>, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist,
-                       d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r), (const float*)W.p, k);
+            DRG_LAUNCH(ctx, k_quantise_r<Q_PER_NODE>, gq, 256, 0, esrc.p, d->col, d->dist, d->Z, gs, nnz, d->q, rr,
+                       (const float*)W.p, k, (const uint8_t*)nullptr);
         else
-            DRG_LAUNCH(ctx, k_quantise_r<false>, grid_for((nnz + 3) / 4, 256, 65536), 256, 0, esrc.p, d->col, d->dist,
-                       d->Z, gs, nnz, d->q, reinterpret_cast<unsigned long long*>(d->r), (const float*)nullptr, k);
+            DRG_LAUNCH(ctx, k_quantise_r<Q_GLOBAL_SIGMA>, gq, 256, 0, esrc.p, d->col, d->dist, d->Z, gs, nnz, d->q, rr,
+                       (const float*)nullptr, k, (const uint8_t*)nullptr);
         W.reset();
         flag.reset();
         DBuf<unsigned long long> rmax(ctx, 1);
