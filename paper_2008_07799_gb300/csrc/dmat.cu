@@ -1391,23 +1391,27 @@ __global__ void k_shift_u32(const uint64_t* __restrict__ r, uint32_t n, uint32_t
 // place in the light or heavy list and its Dl or S value, written straight
 // into the lists.
 
-// Running sums of the split scan.
+// Running sums of the split scan: the lights' count and weight, the heavies'
+// weight.  The deficits and excesses follow from them exactly, so the lists
+// hold 64-bit weight prefixes instead of 128-bit mass sums:
+//   Dl(x) = x W - N QL(x)          QL(x): weight of the lights before light x
+//   S(y)  = N QH(y) - (y + 1) W    QH(y): weight of the heavies up to heavy y
 struct SplitAcc {
-    u128 D, E;     // lights' deficit, heavies' excess
-    uint64_t c;    // lights
+    uint64_t QL, QH;  // lights' weight, heavies' weight
+    uint64_t c;       // lights
     SplitAcc() = default;  // trivial, so that it can live in shared memory
-    __host__ __device__ SplitAcc(int) : D(0), E(0), c(0) {}  // from 0
+    __host__ __device__ SplitAcc(int) : QL(0), QH(0), c(0) {}  // from 0
     __host__ __device__ SplitAcc& operator+=(const SplitAcc& o) {
-        D += o.D;
-        E += o.E;
+        QL += o.QL;
+        QH += o.QH;
         c += o.c;
         return *this;
     }
     __host__ __device__ SplitAcc operator+(const SplitAcc& o) const { SplitAcc r = *this; r += o; return r; }
     __host__ __device__ SplitAcc operator-(const SplitAcc& o) const {
         SplitAcc r = *this;
-        r.D -= o.D;
-        r.E -= o.E;
+        r.QL -= o.QL;
+        r.QH -= o.QH;
         r.c -= o.c;
         return r;
     }
@@ -1415,20 +1419,19 @@ struct SplitAcc {
 
 __device__ __forceinline__ SplitAcc shfl_up(const SplitAcc& v, int d) {
     SplitAcc r;
-    r.D = shfl_up(v.D, d);
-    r.E = shfl_up(v.E, d);
+    r.QL = shfl_up(v.QL, d);
+    r.QH = shfl_up(v.QH, d);
     r.c = shfl_up(v.c, d);
     return r;
 }
 
 __device__ __forceinline__ SplitAcc split_item(uint32_t qi, uint64_t N, uint64_t W) {
     SplitAcc r(0);
-    const uint64_t a = (uint64_t)qi * N;
-    if (a < W) {
-        r.D = (u128)(W - a);
+    if ((uint64_t)qi * N < W) {
+        r.QL = qi;
         r.c = 1;
     } else {
-        r.E = (u128)(a - W);
+        r.QH = qi;
     }
     return r;
 }
@@ -1447,10 +1450,8 @@ __device__ __forceinline__ SplitAcc warp_sum(SplitAcc v) {
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
         SplitAcc o;
-        o.D = ((u128)__shfl_xor_sync(0xFFFFFFFFu, (uint64_t)(v.D >> 64), off) << 64) |
-              __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)v.D, off);
-        o.E = ((u128)__shfl_xor_sync(0xFFFFFFFFu, (uint64_t)(v.E >> 64), off) << 64) |
-              __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)v.E, off);
+        o.QL = __shfl_xor_sync(0xFFFFFFFFu, v.QL, off);
+        o.QH = __shfl_xor_sync(0xFFFFFFFFu, v.QH, off);
         o.c = __shfl_xor_sync(0xFFFFFFFFu, v.c, off);
         v += o;
     }
@@ -1486,19 +1487,19 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_reduce(const uint32_t* 
     }
 }
 
-// Lists: Dl[x] = deficit of the lights before the x-th light; H[y] = y-th
-// heavy, S[y] = excess of the heavies up to and including it.  Each piece's
-// lights and heavies are gathered in shared memory (lights first) and written
-// out in order.
-constexpr size_t SPLIT_DOWN_SMEM = (size_t)SPLIT_SUB * (4 + 4 + 16);
+// Lists, in index order: light x is item L[x] with QL[x] = weight of the
+// lights before it; heavy y is item H[y] with QH[y] = weight of the heavies
+// up to and including it.  Each piece's lights and heavies are gathered in
+// shared memory (lights first) and written out in order.
+constexpr size_t SPLIT_DOWN_SMEM = (size_t)SPLIT_SUB * (4 + 4 + 8);
 
 __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __restrict__ q, uint64_t N, uint64_t W,
                                                               const SplitAcc* __restrict__ tile_pre,
-                                                              u128* __restrict__ Dl, uint32_t* __restrict__ H,
-                                                              u128* __restrict__ S) {
+                                                              uint64_t* __restrict__ QL, uint32_t* __restrict__ L,
+                                                              uint64_t* __restrict__ QH, uint32_t* __restrict__ H) {
     extern __shared__ __align__(16) unsigned char split_smem[];
-    u128* s_val = reinterpret_cast<u128*>(split_smem);
-    uint32_t* s_idx = reinterpret_cast<uint32_t*>(split_smem + (size_t)SPLIT_SUB * 16);
+    uint64_t* s_val = reinterpret_cast<uint64_t*>(split_smem);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(split_smem + (size_t)SPLIT_SUB * 8);
     uint32_t* qs = s_idx + SPLIT_SUB;
     __shared__ SplitAcc wt[SPLIT_THREADS / 32];
     constexpr int IT = SPLIT_SUB / SPLIT_THREADS;
@@ -1527,11 +1528,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __
             const SplitAcc it = split_item(qs[t], N, W);
             if (it.c) {
                 s_idx[run.c] = (uint32_t)(sb + t);
-                s_val[run.c] = run0.D + run.D;
+                s_val[run.c] = run0.QL + run.QL;
             } else {
                 const uint32_t h = nl + (t - (uint32_t)run.c);
                 s_idx[h] = (uint32_t)(sb + t);
-                s_val[h] = run0.E + run.E + it.E;
+                s_val[h] = run0.QH + run.QH + it.QH;
             }
             run += it;
         }
@@ -1539,10 +1540,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __
         const uint64_t xb = run0.c, yb = sb - run0.c;  // lights and heavies before the piece
         for (uint32_t t = threadIdx.x; t < cnt; t += SPLIT_THREADS) {
             if (t < nl) {
-                Dl[xb + t] = s_val[t];
+                QL[xb + t] = s_val[t];
+                L[xb + t] = s_idx[t];
             } else {
+                QH[yb + t - nl] = s_val[t];
                 H[yb + t - nl] = s_idx[t];
-                S[yb + t - nl] = s_val[t];
             }
         }
         run0 += bt;
@@ -1550,11 +1552,34 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __
     }
 }
 
-__device__ __forceinline__ uint64_t merge_path(const u128* A, uint64_t nA, const u128* B, uint64_t nB, uint64_t diag) {
-    uint64_t lo = diag > nB ? diag - nB : 0;
-    uint64_t hi = diag < nA ? diag : nA;
+// The two sorted sequences of the merge, from their weight prefixes.
+struct SweepLists {
+    const uint64_t* QL;  // [nL + 1] (QL[nL] = all lights' weight)
+    const uint64_t* QH;  // [nH]
+    uint64_t nL, nH, N, W;
+    __device__ __forceinline__ u128 Dl(uint64_t x) const { return (u128)x * W - (u128)N * QL[x]; }
+    __device__ __forceinline__ u128 S(uint64_t y) const { return (u128)N * QH[y] - (u128)(y + 1) * W; }
+};
+
+// Lights before diagonal `diag` of the merge (a light precedes a heavy iff
+// Dl < S), on the sequences in memory ...
+__device__ __forceinline__ uint64_t merge_path(const SweepLists& l, uint64_t diag) {
+    uint64_t lo = diag > l.nH ? diag - l.nH : 0;
+    uint64_t hi = diag < l.nL ? diag : l.nL;
     while (lo < hi) {
         const uint64_t mid = (lo + hi) >> 1;
+        if (l.Dl(mid) < l.S(diag - mid - 1)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ... and on a tile's values in shared memory.
+__device__ __forceinline__ uint32_t merge_path(const u128* A, uint32_t nA, const u128* B, uint32_t nB, uint32_t diag) {
+    uint32_t lo = diag > nB ? diag - nB : 0;
+    uint32_t hi = diag < nA ? diag : nA;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
         if (A[mid] < B[diag - mid - 1]) lo = mid + 1;
         else hi = mid;
     }
@@ -1565,12 +1590,11 @@ constexpr int MERGE_THREADS = 256, MERGE_ITEMS = 8, MERGE_TILE = MERGE_THREADS *
 
 // Merge-path split of every tile boundary (diagonal t * MERGE_TILE, and the
 // end): one thread per boundary, all searches in flight together.
-__global__ void k_merge_partition(const u128* __restrict__ A, uint64_t nA, const u128* __restrict__ B, uint64_t nB,
-                                  uint64_t tiles, uint64_t* __restrict__ part) {
-    const uint64_t total = nA + nB;
+__global__ void k_merge_partition(SweepLists l, uint64_t tiles, uint64_t* __restrict__ part) {
+    const uint64_t total = l.nL + l.nH;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= tiles; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t d = t * MERGE_TILE < total ? t * MERGE_TILE : total;
-        part[t] = merge_path(A, nA, B, nB, d);
+        part[t] = merge_path(l, d);
     }
 }
 
@@ -1615,64 +1639,6 @@ __device__ __forceinline__ uint32_t frac32(uint64_t own, const InvDiv& D) {
     return (uint32_t)q1;
 }
 
-struct MergeArgs {
-    const u128* Dl;          // [nL + 1] (Dl[nL] = total deficit)
-    const u128* S;           // [nH]
-    const uint32_t* H;
-    uint64_t nL, nH, W;
-    InvDiv D;
-    const uint64_t* part;    // [tiles + 1] merge-path splits
-    uint32_t* l_alias;       // [nL] alias of each light (kSelf: itself)
-    uint32_t* h_thresh;      // [nH] threshold of each heavy
-    uint32_t* h_alias;       // [nH] alias of each heavy (kSelf: itself)
-};
-
-constexpr uint32_t kSelf = 0xFFFFFFFFu;
-
-// The merge, tile by tile, recording each list element's result in list
-// order: light x placed after y heavies -> alias H[y]; heavy y placed after x
-// lights -> its own mass S[y] + W - Dl[x] fills the bucket (thresh all ones,
-// alias itself) or takes the next heavy as alias.
-__global__ void __launch_bounds__(MERGE_THREADS) k_merge_alias(MergeArgs m) {
-    __shared__ u128 s[MERGE_TILE];
-    const uint64_t total = m.nL + m.nH;
-    const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_TILE;
-    const uint64_t d1 = d0 + MERGE_TILE < total ? d0 + MERGE_TILE : total;
-    const uint64_t x0 = m.part[blockIdx.x], x1 = m.part[blockIdx.x + 1], y0 = d0 - x0, y1 = d1 - x1;
-    const uint32_t na = (uint32_t)(x1 - x0), nb = (uint32_t)(y1 - y0);
-    for (uint32_t t = threadIdx.x; t < na; t += MERGE_THREADS) s[t] = m.Dl[x0 + t];
-    for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) s[na + t] = m.S[y0 + t];
-    __syncthreads();
-    const u128* As = s;
-    const u128* Bs = s + na;
-    const uint32_t dl = threadIdx.x * MERGE_ITEMS;
-    if (dl >= na + nb) return;
-    uint32_t xa = (uint32_t)merge_path(As, na, Bs, nb, dl);
-    uint32_t yb = dl - xa;
-#pragma unroll
-    for (int it = 0; it < MERGE_ITEMS; ++it) {
-        if (xa + yb >= na + nb) break;
-        const uint64_t x = x0 + xa, y = y0 + yb;
-        if (xa < na && (yb >= nb || As[xa] < Bs[yb])) {
-            m.l_alias[x] = y < m.nH ? m.H[y] : kSelf;  // y < nH whenever the totals are exact
-            ++xa;
-        } else {
-            // own mass = S[y] + W - Dl[x]; exact totals make the last heavy
-            // full, the index guard only keeps a violated invariant from
-            // reading past H
-            const uint64_t own = (uint64_t)(Bs[yb] + (u128)m.W - (xa < na ? As[xa] : m.Dl[x]));
-            if (own >= m.W || y + 1 >= m.nH) {
-                m.h_thresh[y] = 0xFFFFFFFFu;
-                m.h_alias[y] = kSelf;
-            } else {
-                m.h_thresh[y] = frac32(own, m.D);
-                m.h_alias[y] = m.H[y + 1];
-            }
-            ++yb;
-        }
-    }
-}
-
 // Where the table goes: the node table as {thresh, alias} pairs, or the edge
 // table as packed 16-byte or wide 32-byte records with the endpoints of the
 // bucket's own entry and of its alias.
@@ -1686,57 +1652,91 @@ struct AliasOut {
     const uint32_t* col;     // kOutEdges*: column of each entry
 };
 
-// Each item's table entry, in item order: its place in the light or heavy
-// list comes from the split scan's tile prefix and a scan of the light flags
-// inside the tile.
+
+__device__ __forceinline__ void emit_entry(const AliasOut& o, int kind, uint32_t i, uint32_t th, uint32_t al) {
+    if (kind == kOutNodes) {
+        o.nodes[i] = make_uint2(th, al);
+    } else {
+        const uint32_t i0 = o.esrc[i], j0 = o.col[i], i1 = o.esrc[al], j1 = o.col[al];
+        if (kind == kOutEdges16) {
+            static_cast<uint4*>(o.edges)[i] = pack_edge16(th, i0, j0, i1, j1);
+        } else {
+            EdgeRec r;
+            r.thresh = th;
+            r.i0 = i0;
+            r.j0 = j0;
+            r.i1 = i1;
+            r.j1 = j1;
+            r.pad0 = r.pad1 = r.pad2 = 0;
+            static_cast<EdgeRec*>(o.edges)[i] = r;
+        }
+    }
+}
+
+struct EmitArgs {
+    SweepLists l;
+    const uint32_t* L;     // [nL] item of each light
+    const uint32_t* H;     // [nH] item of each heavy
+    InvDiv D;
+    const uint64_t* part;  // [tiles + 1] merge-path splits
+};
+
+// The merge, tile by tile, and each item's table entry from it.  Phase 1
+// merges the tile's Dl and S values in shared memory and records each
+// element's cross rank: light x placed after y heavies, heavy y after x
+// lights.  Phase 2 writes the entries, lights then heavies, each in list
+// (= item) order: light x has threshold a_x / W (a_x = W - (Dl(x + 1) -
+// Dl(x)) = q N) and alias H[y]; heavy y has own mass S(y) + W - Dl(x), which
+// fills the bucket (threshold all ones, alias itself) or leaves the rest to
+// the next heavy H[y + 1].
 template <int KIND>
-__global__ void __launch_bounds__(SPLIT_THREADS) k_alias_items(const uint32_t* __restrict__ q, uint64_t N,
-                                                               uint64_t W, InvDiv D,
-                                                               const SplitAcc* __restrict__ tile_pre,
-                                                               const uint32_t* __restrict__ l_alias,
-                                                               const uint32_t* __restrict__ h_thresh,
-                                                               const uint32_t* __restrict__ h_alias, AliasOut o) {
-    __shared__ uint32_t wt[SPLIT_THREADS / 32];
-    const uint64_t base = (uint64_t)blockIdx.x * SPLIT_TILE;
-    uint64_t lights = tile_pre[blockIdx.x].c;  // lights before the piece
-    for (uint64_t sb = base; sb < base + SPLIT_TILE && sb < N; sb += SPLIT_THREADS) {
-        const uint64_t i = sb + threadIdx.x;
-        const bool in = i < N;
-        const uint32_t qi = in ? q[i] : 0u;
-        const uint64_t a = (uint64_t)qi * N;
-        const bool light = in && a < W;
-        uint32_t tot;
-        const uint32_t before = block_exclusive_scan<uint32_t, SPLIT_THREADS>(light ? 1u : 0u, wt, tot);
-        if (in) {
-            uint32_t th, al;
-            if (light) {
-                th = frac32(a, D);
-                al = l_alias[lights + before];
+__global__ void __launch_bounds__(MERGE_THREADS) k_alias_emit(EmitArgs m, AliasOut o) {
+    __shared__ u128 s[MERGE_TILE + 1];
+    __shared__ uint16_t rank[MERGE_TILE];
+    const SweepLists& l = m.l;
+    const uint64_t total = l.nL + l.nH;
+    const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_TILE;
+    const uint64_t d1 = d0 + MERGE_TILE < total ? d0 + MERGE_TILE : total;
+    const uint64_t x0 = m.part[blockIdx.x], x1 = m.part[blockIdx.x + 1], y0 = d0 - x0, y1 = d1 - x1;
+    const uint32_t na = (uint32_t)(x1 - x0), nb = (uint32_t)(y1 - y0);
+    // Dl(x0 .. x1) inclusive (the value after the tile's last light closes
+    // it), then S(y0 .. y1 - 1)
+    for (uint32_t t = threadIdx.x; t <= na; t += MERGE_THREADS) s[t] = l.Dl(x0 + t);
+    u128* Bs = s + na + 1;
+    for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) Bs[t] = l.S(y0 + t);
+    __syncthreads();
+    const uint32_t dl = threadIdx.x * MERGE_ITEMS;
+    if (dl < na + nb) {
+        uint32_t xa = merge_path(s, na, Bs, nb, dl);
+        uint32_t yb = dl - xa;
+#pragma unroll
+        for (int it = 0; it < MERGE_ITEMS; ++it) {
+            if (xa + yb >= na + nb) break;
+            if (xa < na && (yb >= nb || s[xa] < Bs[yb])) {
+                rank[xa] = (uint16_t)yb;
+                ++xa;
             } else {
-                const uint64_t y = i - (lights + before);
-                th = h_thresh[y];
-                al = h_alias[y];
-            }
-            if (al == kSelf) al = (uint32_t)i;
-            if constexpr (KIND == kOutNodes) {
-                o.nodes[i] = make_uint2(th, al);
-            } else {
-                const uint32_t i0 = o.esrc[i], j0 = o.col[i], i1 = o.esrc[al], j1 = o.col[al];
-                if constexpr (KIND == kOutEdges16) {
-                    static_cast<uint4*>(o.edges)[i] = pack_edge16(th, i0, j0, i1, j1);
-                } else {
-                    EdgeRec r;
-                    r.thresh = th;
-                    r.i0 = i0;
-                    r.j0 = j0;
-                    r.i1 = i1;
-                    r.j1 = j1;
-                    r.pad0 = r.pad1 = r.pad2 = 0;
-                    static_cast<EdgeRec*>(o.edges)[i] = r;
-                }
+                rank[na + yb] = (uint16_t)xa;
+                ++yb;
             }
         }
-        lights += tot;
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < na; t += MERGE_THREADS) {
+        const uint32_t i = m.L[x0 + t];
+        const uint64_t y = y0 + rank[t];
+        const uint64_t a = l.W - (uint64_t)(s[t + 1] - s[t]);
+        const uint32_t al = y < l.nH ? m.H[y] : i;  // y < nH whenever the totals are exact
+        emit_entry(o, KIND, i, frac32(a, m.D), al);
+    }
+    for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) {
+        const uint64_t y = y0 + t;
+        const uint32_t i = m.H[y];
+        // own mass = S(y) + W - Dl(x); exact totals make the last heavy full,
+        // the index guard only keeps a violated invariant from reading past H
+        const uint64_t own = (uint64_t)(Bs[t] + (u128)l.W - s[rank[na + t]]);
+        if (own >= l.W || y + 1 >= l.nH) emit_entry(o, KIND, i, 0xFFFFFFFFu, i);
+        else emit_entry(o, KIND, i, frac32(own, m.D), m.H[y + 1]);
     }
 }
 
@@ -1773,28 +1773,21 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& ou
     d2h(ctx, &tot, tsum.p + stiles, 1);
     sync(ctx);
     const uint64_t nL = tot.c, nH = N - nL;
-    const InvDiv D = make_invdiv(W);
-    DBuf<uint32_t> l_alias(ctx, nL), h_thresh(ctx, nH), h_alias(ctx, nH);
-    {
-        DBuf<uint32_t> H(ctx, nH);
-        DBuf<u128> Dl(ctx, nL + 1), S(ctx, nH);
-        DRG_CUDA(cudaFuncSetAttribute(k_split_down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPLIT_DOWN_SMEM));
-        DRG_LAUNCH(ctx, k_split_down, (uint32_t)stiles, SPLIT_THREADS, SPLIT_DOWN_SMEM, q, N, W, tsum.p, Dl.p, H.p,
-                   S.p);
-        h2d(ctx, Dl.p + nL, &tot.D, 1);
-        // merge, recording each list element's result
-        const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
-        DBuf<uint64_t> part(ctx, tiles + 1);
-        DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, Dl.p, nL, S.p, nH, tiles,
-                   part.p);
-        MergeArgs m{Dl.p, S.p, H.p, nL, nH, W, D, part.p, l_alias.p, h_thresh.p, h_alias.p};
-        DRG_LAUNCH(ctx, k_merge_alias, (uint32_t)tiles, MERGE_THREADS, 0, m);
-    }
-    // the table in item order
-    auto kern = out.kind == kOutNodes ? k_alias_items<kOutNodes>
-                                      : (out.kind == kOutEdges16 ? k_alias_items<kOutEdges16> : k_alias_items<kOutEdges32>);
-    DRG_LAUNCH(ctx, kern, (uint32_t)stiles, SPLIT_THREADS, 0, q, N, W, D, tsum.p, l_alias.p, h_thresh.p, h_alias.p,
-               out);
+    DBuf<uint64_t> QL(ctx, nL + 1), QH(ctx, nH);
+    DBuf<uint32_t> L(ctx, nL), H(ctx, nH);
+    DRG_CUDA(cudaFuncSetAttribute(k_split_down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPLIT_DOWN_SMEM));
+    DRG_LAUNCH(ctx, k_split_down, (uint32_t)stiles, SPLIT_THREADS, SPLIT_DOWN_SMEM, q, N, W, tsum.p, QL.p, L.p, QH.p,
+               H.p);
+    h2d(ctx, QL.p + nL, &tot.QL, 1);
+    // merge-path splits, then the merge writing the table
+    const SweepLists lists{QL.p, QH.p, nL, nH, N, W};
+    const uint64_t tiles = (N + MERGE_TILE - 1) / MERGE_TILE;
+    DBuf<uint64_t> part(ctx, tiles + 1);
+    DRG_LAUNCH(ctx, k_merge_partition, grid_for(tiles + 1, 256, 65536), 256, 0, lists, tiles, part.p);
+    const EmitArgs m{lists, L.p, H.p, make_invdiv(W), part.p};
+    auto kern = out.kind == kOutNodes ? k_alias_emit<kOutNodes>
+                                      : (out.kind == kOutEdges16 ? k_alias_emit<kOutEdges16> : k_alias_emit<kOutEdges32>);
+    DRG_LAUNCH(ctx, kern, (uint32_t)tiles, MERGE_THREADS, 0, m, out);
     sync(ctx);  // `tot` is a host value read by an asynchronous copy above
     return true;
 }
