@@ -1443,8 +1443,8 @@ struct SplitLoad {
 };
 
 // Tiles of SPLIT_TILE items; the down pass walks a tile in SPLIT_SUB-item
-// pieces (8 consecutive items per thread).
-constexpr int SPLIT_THREADS = 256, SPLIT_SUB = 2048, SPLIT_TILE = 4 * SPLIT_SUB;
+// pieces (8 consecutive items per thread), one piece per tile.
+constexpr int SPLIT_THREADS = 256, SPLIT_SUB = 2048, SPLIT_TILE = SPLIT_SUB;
 
 __device__ __forceinline__ SplitAcc warp_sum(SplitAcc v) {
 #pragma unroll
@@ -1458,32 +1458,45 @@ __device__ __forceinline__ SplitAcc warp_sum(SplitAcc v) {
     return v;
 }
 
-// Per-tile sums (16-byte loads, 32 items per thread).
-__global__ void __launch_bounds__(SPLIT_THREADS) k_split_reduce(const uint32_t* __restrict__ q, uint64_t N,
-                                                                uint64_t W, SplitAcc* __restrict__ sums) {
-    __shared__ SplitAcc wt[SPLIT_THREADS / 32];
-    const uint64_t base = (uint64_t)blockIdx.x * SPLIT_TILE;
-    SplitAcc acc(0);
+// Per-tile sums: a block reads SPLIT_REDUCE_TILES tiles with 16-byte loads
+// (8 items per thread and tile) and writes each tile's sum.
+constexpr int SPLIT_REDUCE_TILES = 4;
+
+__global__ void __launch_bounds__(SPLIT_THREADS, 6) k_split_reduce(const uint32_t* __restrict__ q, uint64_t N,
+                                                                uint64_t W, uint64_t tiles,
+                                                                SplitAcc* __restrict__ sums) {
+    __shared__ SplitAcc wt[SPLIT_REDUCE_TILES][SPLIT_THREADS / 32];
+    constexpr int R = SPLIT_TILE / 4 / SPLIT_THREADS;  // 16-byte loads per thread and tile
+    SplitAcc acc[SPLIT_REDUCE_TILES];
 #pragma unroll
-    for (int r = 0; r < SPLIT_TILE / 4 / SPLIT_THREADS; ++r) {
-        const uint64_t i = base + 4 * ((uint64_t)r * SPLIT_THREADS + threadIdx.x);
-        if (i + 4 <= N) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(q + i));
-            acc += split_item(v.x, N, W);
-            acc += split_item(v.y, N, W);
-            acc += split_item(v.z, N, W);
-            acc += split_item(v.w, N, W);
-        } else {
-            for (uint64_t t = i; t < N && t < i + 4; ++t) acc += split_item(q[t], N, W);
+    for (int p = 0; p < SPLIT_REDUCE_TILES; ++p) {
+        acc[p] = SplitAcc(0);
+        const uint64_t base = ((uint64_t)blockIdx.x * SPLIT_REDUCE_TILES + p) * SPLIT_TILE;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t i = base + 4 * ((uint64_t)r * SPLIT_THREADS + threadIdx.x);
+            if (i + 4 <= N) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(q + i));
+                acc[p] += split_item(v.x, N, W);
+                acc[p] += split_item(v.y, N, W);
+                acc[p] += split_item(v.z, N, W);
+                acc[p] += split_item(v.w, N, W);
+            } else {
+                for (uint64_t t = i; t < N && t < i + 4; ++t) acc[p] += split_item(q[t], N, W);
+            }
         }
     }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = acc;
+#pragma unroll
+    for (int p = 0; p < SPLIT_REDUCE_TILES; ++p) {
+        const SplitAcc w = warp_sum(acc[p]);
+        if ((threadIdx.x & 31) == 0) wt[p][threadIdx.x >> 5] = w;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < SPLIT_REDUCE_TILES) {
+        const uint64_t tile = (uint64_t)blockIdx.x * SPLIT_REDUCE_TILES + threadIdx.x;
         SplitAcc t(0);
-        for (int w = 0; w < SPLIT_THREADS / 32; ++w) t += wt[w];
-        sums[blockIdx.x] = t;
+        for (int w = 0; w < SPLIT_THREADS / 32; ++w) t += wt[threadIdx.x][w];
+        if (tile < tiles) sums[tile] = t;
     }
 }
 
@@ -1491,7 +1504,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_reduce(const uint32_t* 
 // lights before it; heavy y is item H[y] with QH[y] = weight of the heavies
 // up to and including it.  Each piece's lights and heavies are gathered in
 // shared memory (lights first) and written out in order.
-constexpr size_t SPLIT_DOWN_SMEM = (size_t)SPLIT_SUB * (4 + 4 + 8);
+constexpr size_t SPLIT_DOWN_SMEM = (size_t)SPLIT_SUB * (4 + 8);
 
 __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __restrict__ q, uint64_t N, uint64_t W,
                                                               const SplitAcc* __restrict__ tile_pre,
@@ -1500,24 +1513,30 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __
     extern __shared__ __align__(16) unsigned char split_smem[];
     uint64_t* s_val = reinterpret_cast<uint64_t*>(split_smem);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(split_smem + (size_t)SPLIT_SUB * 8);
-    uint32_t* qs = s_idx + SPLIT_SUB;
     __shared__ SplitAcc wt[SPLIT_THREADS / 32];
     constexpr int IT = SPLIT_SUB / SPLIT_THREADS;
+    static_assert(IT == 8, "two 16-byte loads per thread");
     const uint64_t base = (uint64_t)blockIdx.x * SPLIT_TILE;
     SplitAcc run0 = tile_pre[blockIdx.x];  // everything before this piece
     for (uint64_t sb = base; sb < base + SPLIT_TILE && sb < N; sb += SPLIT_SUB) {
         const uint32_t cnt = N - sb < (uint64_t)SPLIT_SUB ? (uint32_t)(N - sb) : (uint32_t)SPLIT_SUB;
-#pragma unroll
-        for (int j = 0; j < IT; ++j) {
-            const uint32_t t = j * SPLIT_THREADS + threadIdx.x;
-            qs[t] = t < cnt ? q[sb + t] : 0u;
-        }
-        __syncthreads();
         const uint32_t t0 = threadIdx.x * IT;
+        // the thread's 8 consecutive items, in registers (q is 16-byte aligned
+        // and sb + t0 a multiple of 8)
+        uint32_t qv[IT];
+        if (t0 + IT <= cnt) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4*>(q + sb + t0));
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(q + sb + t0 + 4));
+            qv[0] = u.x; qv[1] = u.y; qv[2] = u.z; qv[3] = u.w;
+            qv[4] = v.x; qv[5] = v.y; qv[6] = v.z; qv[7] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < IT; ++j) qv[j] = t0 + j < cnt ? q[sb + t0 + j] : 0u;
+        }
         SplitAcc mine(0);
 #pragma unroll
         for (int j = 0; j < IT; ++j)
-            if (t0 + j < cnt) mine += split_item(qs[t0 + j], N, W);
+            if (t0 + j < cnt) mine += split_item(qv[j], N, W);
         SplitAcc bt;
         SplitAcc run = block_exclusive_scan<SplitAcc, SPLIT_THREADS>(mine, wt, bt);
         const uint32_t nl = (uint32_t)bt.c;  // lights of the piece
@@ -1525,7 +1544,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_split_down(const uint32_t* __
         for (int j = 0; j < IT; ++j) {
             const uint32_t t = t0 + j;
             if (t >= cnt) break;
-            const SplitAcc it = split_item(qs[t], N, W);
+            const SplitAcc it = split_item(qv[j], N, W);
             if (it.c) {
                 s_idx[run.c] = (uint32_t)(sb + t);
                 s_val[run.c] = run0.QL + run.QL;
@@ -1767,7 +1786,8 @@ bool build_alias(drg_ctx* ctx, const uint32_t* q, uint64_t N, const AliasOut& ou
     // split scan: tile sums, their exclusive prefix, then the lists
     const uint64_t stiles = (N + SPLIT_TILE - 1) / SPLIT_TILE;
     DBuf<SplitAcc> tsum(ctx, stiles + 1);
-    DRG_LAUNCH(ctx, k_split_reduce, (uint32_t)stiles, SPLIT_THREADS, 0, q, N, W, tsum.p);
+    DRG_LAUNCH(ctx, k_split_reduce, (uint32_t)((stiles + SPLIT_REDUCE_TILES - 1) / SPLIT_REDUCE_TILES),
+               SPLIT_THREADS, 0, q, N, W, stiles, tsum.p);
     scan<SplitAcc>(ctx, LoadArr<SplitAcc>{tsum.p}, stiles, tsum.p, false, tsum.p + stiles);
     SplitAcc tot(0);
     d2h(ctx, &tot, tsum.p + stiles, 1);
