@@ -460,6 +460,10 @@ drg_status drg_autotune_clear(void);
  *   DRG_PROBE_LOAD16_EVICT_FIRST  as LOAD16 with an L2 evict-first policy
  *   DRG_PROBE_COPY     streaming copy of the buffer's first half to its second
  *                      half (16-byte vectors; `accesses` is ignored)
+ *   DRG_PROBE_MIX_LOAD8_RED8  random 8-byte loads (as LOAD8) and 8-byte
+ *                      atomic adds (as RED8) interleaved two to one, the mix of
+ *                      a layout sample (12 or 14 loads, 7 atomic adds); both
+ *                      kinds count as accesses
  * Random places are uniform over the buffer (a 32-bit linear congruential
  * stream per thread, scaled to the element count).  `accesses` (1 .. 1e11) is
  * rounded up to whole iterations; *done receives the accesses made (COPY: the
@@ -470,6 +474,7 @@ drg_status drg_autotune_clear(void);
 #define DRG_PROBE_RED8 2
 #define DRG_PROBE_LOAD16_EVICT_FIRST 3
 #define DRG_PROBE_COPY 4
+#define DRG_PROBE_MIX_LOAD8_RED8 5
 drg_status drg_probe_memory(drg_ctx* ctx, int kind, uint64_t buffer_bytes, uint64_t accesses, uint32_t blocks_per_sm,
                             double* ms, uint64_t* done);
 

@@ -42,7 +42,7 @@ EXPORTS = [
     "drg_build_distance_matrix_capped", "drg_layout_step_explicit",
 ]
 
-PROBE_LOAD8, PROBE_LOAD16, PROBE_RED8, PROBE_LOAD16_EVICT_FIRST, PROBE_COPY = range(5)
+PROBE_LOAD8, PROBE_LOAD16, PROBE_RED8, PROBE_LOAD16_EVICT_FIRST, PROBE_COPY, PROBE_MIX_LOAD8_RED8 = range(6)
 
 PROF_EPOCH, PROF_APPLY, PROF_DMAT, PROF_HIER, PROF_GRAPH, PROF_BFS, PROF_SIM, PROF_ALIAS, PROF_ALLOC = range(9)
 

@@ -9,7 +9,8 @@
 // access kind alone, at random places spread uniformly over a buffer of a
 // chosen size (inside L2, or far larger than L2 for the HBM-resident table),
 // with enough independent accesses in flight on every SM to saturate the
-// memory system rather than the issuing threads.
+// memory system rather than the issuing threads; one more probe interleaves
+// loads and atomic adds two to one, the level kernels' own mix.
 #include "prims.cuh"
 
 namespace drg {
@@ -81,13 +82,24 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(void* __restrict__ buf,
             }
 #pragma unroll
             for (uint32_t u = 0; u < kProbeUnroll; ++u) acc += v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
-        } else {  // DRG_PROBE_RED8
+        } else if constexpr (KIND == DRG_PROBE_RED8) {
 #pragma unroll
             for (uint32_t u = 0; u < kProbeUnroll; ++u)
                 atomicAdd(static_cast<float2*>(buf) + probe_next(x, nelem), make_float2(1.f, -1.f));
+        } else {  // DRG_PROBE_MIX_LOAD8_RED8: two loads per atomic add, both at random places
+            float2 v[kProbeUnroll];
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u) v[u] = ld_cg_f2(static_cast<const float2*>(buf) + probe_next(x, nelem));
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll / 2; ++u)
+                atomicAdd(static_cast<float2*>(buf) + probe_next(x, nelem), make_float2(1.f, -1.f));
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll; ++u) acc += __float_as_uint(v[u].x) ^ __float_as_uint(v[u].y);
         }
     }
-    if (acc == 0x9E3779B9u) sink[0] = acc;  // keeps the loads; the buffer is zero, so never taken
+    // keeps the loads live; taken only if the bits happen to match (a harmless
+    // write of one word)
+    if (acc == 0x9E3779B9u) sink[0] = acc;
 }
 
 // Streaming copy of nvec 16-byte vectors from the first half of the buffer
@@ -102,7 +114,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_copy(const uint4* __res
 
 void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uint32_t blocks_per_sm, double* ms,
                   uint64_t* done) {
-    DRG_CHECK(kind >= DRG_PROBE_LOAD8 && kind <= DRG_PROBE_COPY, DRG_EINVAL, "unknown probe kind");
+    DRG_CHECK(kind >= DRG_PROBE_LOAD8 && kind <= DRG_PROBE_MIX_LOAD8_RED8, DRG_EINVAL, "unknown probe kind");
     DRG_CHECK(bytes >= (1ull << 20) && bytes <= (64ull << 30), DRG_EINVAL, "probe buffer must be 1 MiB .. 64 GiB");
     DRG_CHECK(accesses >= 1 && accesses <= 100000000000ull, DRG_EINVAL, "probe accesses must be 1 .. 1e11");
     DRG_CHECK(blocks_per_sm >= 1 && blocks_per_sm <= 8, DRG_EINVAL, "blocks per SM must be 1 .. 8");
@@ -131,8 +143,11 @@ void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uin
             *done = nvec;
         } else {
             const uint64_t per_thread = (accesses + threads - 1) / threads;
-            const uint32_t iters = (uint32_t)((per_thread + kProbeUnroll - 1) / kProbeUnroll);
-            const uint64_t elem = (kind == DRG_PROBE_LOAD8 || kind == DRG_PROBE_RED8) ? 8 : 16;
+            // accesses per thread and iteration
+            const uint32_t per_it = kind == DRG_PROBE_MIX_LOAD8_RED8 ? kProbeUnroll + kProbeUnroll / 2 : kProbeUnroll;
+            const uint32_t iters = (uint32_t)((per_thread + per_it - 1) / per_it);
+            const uint64_t elem =
+                (kind == DRG_PROBE_LOAD8 || kind == DRG_PROBE_RED8 || kind == DRG_PROBE_MIX_LOAD8_RED8) ? 8 : 16;
             const uint64_t nelem = bytes / elem;
             const uint32_t seed = (uint32_t)(accesses * 0x9E3779B97F4A7C15ull >> 32);
             DRG_CUDA(cudaEventRecord(e0, ctx->stream));
@@ -149,13 +164,17 @@ void probe_memory(drg_ctx* ctx, int kind, uint64_t bytes, uint64_t accesses, uin
                     DRG_LAUNCH(ctx, k_probe<DRG_PROBE_RED8>, grid, kProbeThreads, 0, (void*)buf.p, nelem, iters, seed,
                                sink.p);
                     break;
+                case DRG_PROBE_MIX_LOAD8_RED8:
+                    DRG_LAUNCH(ctx, k_probe<DRG_PROBE_MIX_LOAD8_RED8>, grid, kProbeThreads, 0, (void*)buf.p, nelem,
+                               iters, seed, sink.p);
+                    break;
                 default:
                     DRG_LAUNCH(ctx, k_probe<DRG_PROBE_LOAD16_EVICT_FIRST>, grid, kProbeThreads, 0, (void*)buf.p, nelem,
                                iters, seed, sink.p);
                     break;
             }
             DRG_CUDA(cudaEventRecord(e1, ctx->stream));
-            *done = threads * iters * kProbeUnroll;
+            *done = threads * iters * per_it;
         }
         DRG_CUDA(cudaEventSynchronize(e1));
         float t = 0.f;

@@ -1,8 +1,8 @@
 """The memory probes that give the level kernels' roofline its measured
 ceilings: every kind runs, counts what it did, and the ceilings order as the
 memory hierarchy says they must (random reads that stay in L2 beat random
-reads of HBM; a streaming copy moves far more bytes than random 16-byte
-reads).  Arguments outside the documented ranges are refused before any
+reads of HBM, also when loads and atomic adds are mixed; a streaming copy
+moves far more bytes than random 16-byte reads).  Arguments outside the documented ranges are refused before any
 device work."""
 import pytest
 
@@ -26,6 +26,7 @@ def test_probe_kinds_and_ordering(env):
     for name, kind, size, count in (("l2_load8", drg.PROBE_LOAD8, 32 << 20, 50_000_000),
                                     ("l2_load16", drg.PROBE_LOAD16, 32 << 20, 50_000_000),
                                     ("l2_red8", drg.PROBE_RED8, 32 << 20, 50_000_000),
+                                    ("l2_mix", drg.PROBE_MIX_LOAD8_RED8, 32 << 20, 48_000_000),
                                     ("hbm_load16", drg.PROBE_LOAD16, 2 << 30, 10_000_000),
                                     ("hbm_ef", drg.PROBE_LOAD16_EVICT_FIRST, 2 << 30, 10_000_000)):
         drg.probe_memory(ctx, kind, size, count)  # warm-up
@@ -36,6 +37,7 @@ def test_probe_kinds_and_ordering(env):
     assert vecs == (2 << 30) // 32
     copy_gbs = vecs * 32 / ms / 1e6
     assert rate["l2_load8"] > 2 * rate["hbm_load16"], rate
+    assert rate["l2_mix"] > 2 * rate["hbm_load16"], rate
     assert copy_gbs > rate["hbm_load16"] * 16 / 1e9, (copy_gbs, rate)
     assert copy_gbs > 1000, copy_gbs
 
