@@ -209,8 +209,13 @@ drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32
 /* drg_build_distance_matrix with a per-row neighbour cap, for graphs whose
  * k-order rows do not fit in memory (Sec. 3.2.1 notes that large k becomes
  * infeasible).  Row i keeps K_i, its row_cap nearest nodes of NNG(v_i, k) by
- * (hop distance, node id): all nodes of the levels whose cumulative count
- * stays below row_cap, then the smallest ids of the next level.  The matrix's
+ * (hop distance, tie order of the node id): all nodes of the levels whose
+ * cumulative count stays below row_cap, then the first nodes of the next level
+ * in tie order.  The tie order is a fixed bijection t of [0, 2^28), applied to
+ * a 28-bit id v as x = v ^ 0x2545F49; x = x * 0x9E3779B mod 2^28;
+ * x ^= x >> 14; x = x * 0x85EBCA7 mod 2^28; t = x ^ (x >> 13); it keeps the
+ * choice among equally near nodes unrelated to how ids were assigned (several
+ * graph generators give their hubs the smallest ids).  The matrix's
  * pattern is the union K u K^T (an entry (i, j) for j in K_i or i in K_j,
  * rows sorted by j, dist the hop distance); the similarity of Eq. 9 is taken
  * over each row's kept set, Z_i = sum over d = 1..k of count of K_i at
@@ -222,7 +227,9 @@ drg_status drg_build_distance_matrix_ex(drg_ctx* ctx, const drg_graph* g, uint32
  * row_cap at least the longest row it is that matrix bit for bit.  The
  * traversal stops at the level that fills the cap, so k = 3 stays feasible
  * where the full rows are not.  DRG_EINVAL for row_cap = 0;
- * DRG_EUNSUPPORTED when the kept entries reach 2^31.  Synchronises. */
+ * DRG_EUNSUPPORTED for graphs of more than 2^28 nodes, for row_cap above 2016
+ * unless it is at least n - 1 (then no row is cut: the uncapped matrix), and
+ * when the kept entries reach 2^31.  Synchronises. */
 drg_status drg_build_distance_matrix_capped(drg_ctx* ctx, const drg_graph* g, uint32_t k, float sigma,
                                             uint32_t row_cap, drg_dmat** out);
 /* Host copy of beta_i = 1/(2 sigma_i^2) of every node (n doubles; 0 for an

@@ -236,20 +236,41 @@ def korder(rp, col, k):
     return gd_rp, gd_col[:nnz], gd_dist[:nnz]
 
 
+TIE_BITS = 28
+_TIE_MASK = (1 << TIE_BITS) - 1
+
+
+def tie_order(v):
+    """The order that breaks hop-distance ties in a capped row: a fixed
+    bijection of [0, 2^28) (xor with a constant, multiplication by an odd
+    constant mod 2^28, xor-shift, again, again), so that which nodes of a cut
+    level are kept does not follow how the graph's ids were assigned (R-MAT
+    and preferential-attachment generators give their hubs the smallest
+    ids)."""
+    x = (np.asarray(v, np.int64) ^ 0x2545F49) & _TIE_MASK
+    x = (x * 0x9E3779B) & _TIE_MASK
+    x ^= x >> 14
+    x = (x * 0x85EBCA7) & _TIE_MASK
+    x ^= x >> 13
+    return x
+
+
 def korder_capped(rp, col, k, cap):
     """Sec. 3.2.1 with a per-row neighbour cap (a reading for graphs whose
     k-order rows are too large): row i keeps K_i, its `cap` nearest entries by
-    (hop distance, node id); the sampling pattern is the union of the kept
-    entries and their transposes, rows sorted by column.  Returns the union
-    CSR (rp, col, dist) and per entry (i, j) the flags own (j in K_i) and
-    back (i in K_j).  Index work only; small graphs (the full rows are built
-    first)."""
+    (hop distance, tie_order(node id)); the sampling pattern is the union of
+    the kept entries and their transposes, rows sorted by column.  Returns the
+    union CSR (rp, col, dist) and per entry (i, j) the flags own (j in K_i)
+    and back (i in K_j).  Index work only; small graphs (the full rows are
+    built first); node ids below 2^28."""
     n = len(rp) - 1
+    if n > (1 << TIE_BITS):
+        raise ValueError("capped rows need node ids below 2^28")
     g_rp, g_col, g_dist = korder(rp, col, k)
     rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g_rp).astype(np.int64))
     c64 = g_col.astype(np.int64)
-    # rank of every entry within its row by (distance, column)
-    order = np.lexsort((c64, g_dist.astype(np.int64), rows))
+    # rank of every entry within its row by (distance, tie order of the column)
+    order = np.lexsort((tie_order(c64), g_dist.astype(np.int64), rows))
     start = g_rp[:-1].astype(np.int64)
     rank = np.empty(len(order), np.int64)
     rank[order] = np.arange(len(order)) - start[rows[order]]

@@ -52,7 +52,8 @@ struct BfsArgs {
     uint64_t cap;             // staged: staging capacity
     uint64_t* row_off;        // staged: staging offset of each row
     uint32_t* overflow;       // staged: set when a row did not fit
-    uint32_t row_cap;         // > 0: each row keeps its row_cap nearest nodes by (hop distance, id) (k_bfs<false>)
+    uint32_t row_cap;         // > 0: each row keeps its row_cap nearest nodes (k_cap_rows only)
+    const uint32_t* tcol;     // k_cap_rows: each row's adjacency as tie values, ascending
     const uint64_t* gd_rp;    // direct: row offsets
     uint32_t* out_col;        // staging or final column array
     uint8_t* out_dist;        // staging or final distance array
@@ -158,8 +159,7 @@ __global__ void __launch_bounds__(BFS_THREADS, BFS_THREADS == 512 ? 3 : 1) k_bfs
         __syncthreads();
         uint32_t lo = 0, hi = s_len;
         __syncthreads();
-        // with a row cap: no further level once the levels so far hold cap nodes
-        for (uint32_t d = 2; d <= a.k && lo < hi && !(a.row_cap && hi >= a.row_cap); ++d) {
+        for (uint32_t d = 2; d <= a.k && lo < hi; ++d) {
             for (uint32_t c = lo; c < hi; c += BFS_THREADS) {
                 const uint32_t idx = c + threadIdx.x;
                 uint64_t deg = 0, start = 0;
@@ -251,53 +251,6 @@ __global__ void __launch_bounds__(BFS_THREADS, BFS_THREADS == 512 ? 3 : 1) k_bfs
         const uint64_t wper = (nw + NW - 1) / NW;
         const uint64_t w0 = (uint64_t)warp * wper < nw ? (uint64_t)warp * wper : nw;
         const uint64_t w1 = w0 + wper < nw ? w0 + wper : nw;
-        if (!K2 && a.row_cap && hi > a.row_cap) {
-            // row cap: the levels before the last ([0, lo) of the list, fewer
-            // than cap nodes) stay whole; of the last level only its cap - lo
-            // smallest ids.  Unmark the earlier levels, cut the bitmap after
-            // its (cap - lo)-th set bit in id order, mark them again.
-            const uint32_t keep = a.row_cap - lo;
-            for (uint32_t x = threadIdx.x; x < lo; x += BFS_THREADS) {
-                const uint32_t v = list[x];
-                atomicAnd(&bm[v >> 5], ~(1u << (v & 31)));
-            }
-            __syncthreads();
-            uint32_t cwc = 0;
-            for (uint64_t x = w0 + lane; x < w1; x += 32) cwc += __popc(bm[wlist[x]]);
-#pragma unroll
-            for (int off = 16; off; off >>= 1) cwc += __shfl_xor_sync(0xFFFFFFFFu, cwc, off);
-            if (lane == 0) s_wcnt[warp] = cwc;
-            __syncthreads();
-            uint32_t before = 0;  // last-level nodes in the words of earlier warps
-            for (uint32_t w = 0; w < warp; ++w) before += s_wcnt[w];
-            for (uint64_t x0 = w0; x0 < w1; x0 += 32) {
-                const uint64_t x = x0 + lane;
-                const uint32_t wi = x < w1 ? wlist[x] : 0u;
-                const uint32_t w = x < w1 ? bm[wi] : 0u;
-                const uint32_t c = __popc(w);
-                const uint32_t incl = warp_incl_scan(c, lane);
-                const uint32_t excl = before + incl - c;
-                if (x < w1 && excl + c > keep) {
-                    // keep only the first keep - excl bits of this word (none when excl >= keep)
-                    uint32_t m = w, left = excl < keep ? keep - excl : 0u;
-                    uint32_t kept = 0;
-                    while (m && left) {
-                        const uint32_t b = m & (0u - m);
-                        kept |= b;
-                        m ^= b;
-                        --left;
-                    }
-                    bm[wi] = kept;
-                }
-                before += __shfl_sync(0xFFFFFFFFu, incl, 31);
-            }
-            __syncthreads();
-            for (uint32_t x = threadIdx.x; x < lo; x += BFS_THREADS) {
-                const uint32_t v = list[x];
-                atomicOr(&bm[v >> 5], 1u << (v & 31));
-            }
-            __syncthreads();
-        }
         uint32_t cw = 0;
         for (uint64_t x = w0 + lane; x < w1; x += 32) cw += __popc(bm[wlist[x]]);
 #pragma unroll
@@ -522,26 +475,51 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
 }
 
 // ------------------------------------------------------------------ capped rows, one warp each
-// Rows of the capped matrix (R24), one warp each.  The warp keeps the row's
-// known nodes as sorted keys (v << 4 | d) in shared memory -- level 1 is the
-// source's sorted adjacency -- and grows them a level at a time while fewer
-// than row_cap nodes are known: the adjacencies of the last level's nodes
-// stream through the buffer as keys; whenever it fills, and at the end of the
-// level, the keys are sorted (bitonic), only the first key of each node is
-// kept (its smallest distance) and, once more than row_cap nodes are known,
-// the new level is cut to its row_cap - (nodes before it) smallest ids.  A
-// node cut that way never returns: at least that many smaller ids of the
-// level are kept.  From the first cut on, the largest kept id of the level
-// bounds what can still enter, so the candidates at or above it are dropped
-// as they are read, and each adjacency (sorted by id) is read only up to it.
-// The row is written in id order to the staging area.  A source of degree
-// >= row_cap keeps the first row_cap of its sorted adjacency directly.
-constexpr uint32_t CAPW_BUF = 1024, CAPW_FRONT = 512;
-constexpr uint32_t CAPW_MAX = CAPW_FRONT - 32;  // largest row_cap this kernel takes
-constexpr int CAPW_WARPS = 8;
+// Rows of the capped matrix (R24), one warp each: row i keeps K_i, its
+// row_cap nearest nodes by (hop distance, tie order of the id).  The tie
+// order is a fixed bijection of [0, 2^28): an xor with a constant, a
+// multiplication by an odd constant mod 2^28, an xor-shift, again, again; it
+// keeps the choice among equally near nodes independent of how the ids were
+// assigned.  The traversal reads a copy of the adjacency that holds each
+// row's neighbours as tie values in ascending order (tcol).  A source of
+// degree >= row_cap keeps the first row_cap of its list.  Otherwise the warp
+// holds the row's known nodes as keys (tie << 4 | d - 1, below the all-ones
+// padding key even at k = 15) in shared memory and grows them a level at a
+// time while fewer than row_cap nodes are known: the lists of the previous
+// level's nodes stream through the buffer; whenever it fills, and at the end
+// of the level, the keys are sorted (bitonic), only the first key of each
+// node is kept (its smallest distance) and, once more than row_cap nodes are
+// known, the level is cut to its row_cap - (nodes before it) first keys.  A
+// node cut that way never returns: at least that many keys of the level
+// before it are kept.  From the first cut on, the largest kept tie value of
+// the level bounds what can still enter: later candidates above it are
+// dropped, and each list is read only up to it.  The row is then re-keyed by
+// id, sorted and written to the staging area (staged) or at its final offset
+// (direct).
+constexpr uint32_t kTieMask = (1u << 28) - 1;
 
-// Ascending bitonic sort of buf[0, m) (m <= CAPW_BUF) by one warp; pads to a
-// power of two with all-ones keys.
+__device__ __forceinline__ uint32_t tie_of(uint32_t v) {
+    uint32_t x = (v ^ 0x2545F49u) & kTieMask;
+    x = (x * 0x9E3779Bu) & kTieMask;
+    x ^= x >> 14;
+    x = (x * 0x85EBCA7u) & kTieMask;
+    x ^= x >> 13;
+    return x;
+}
+
+// The inverse: each step undone in reverse order (the xor-shifts by their
+// repeated application within 28 bits, the multiplications by the inverses
+// of the odd constants mod 2^28).
+__device__ __forceinline__ uint32_t id_of_tie(uint32_t x) {
+    x ^= (x >> 13) ^ (x >> 26);
+    x = (x * 0x46B2B17u) & kTieMask;
+    x ^= x >> 14;
+    x = (x * 0x3811693u) & kTieMask;
+    return x ^ 0x2545F49u;
+}
+
+// Ascending bitonic sort of buf[0, m) by one warp; pads to a power of two with
+// all-ones keys (buf must hold that power of two).
 __device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t lane) {
     uint32_t P = 1, lp = 0;
     while (P < m) {
@@ -567,9 +545,10 @@ __device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t
 }
 
 // Sorts buf[0, m), keeps the first key of each node and, when more than cap
-// nodes remain, only the first cap - lower keys of level d (lower = nodes of
-// the levels before d, all kept); *tau becomes the largest id of level d
-// kept after such a cut.  Returns the new size (cap when cut).
+// nodes remain, only the first cap - lower keys of the level whose code (the
+// key's low 4 bits) is d (lower = nodes of the levels before it, all kept);
+// *tau becomes the largest tie value of that level kept after such a cut.
+// Returns the new size (cap when cut).
 __device__ __forceinline__ uint32_t capw_flush(uint32_t* buf, uint32_t m, uint32_t lower, uint32_t cap, uint32_t d,
                                                uint32_t lane, uint32_t* tau) {
     warp_bitonic(buf, m, lane);
@@ -611,126 +590,155 @@ __device__ __forceinline__ uint32_t capw_flush(uint32_t* buf, uint32_t m, uint32
     return kept;
 }
 
-// First index in [lo, hi) whose col entry is >= tau (hi if none); col is
-// ascending there.
-__device__ __forceinline__ uint64_t capw_clip(const uint32_t* __restrict__ col, uint64_t lo, uint64_t hi,
-                                              uint32_t tau) {
+// First index in [lo, hi) whose entry is >= tau (hi if none); the entries
+// are ascending there.
+__device__ __forceinline__ uint64_t capw_clip(const uint32_t* __restrict__ t, uint64_t lo, uint64_t hi, uint32_t tau) {
     while (lo < hi) {
         const uint64_t mid = (lo + hi) >> 1;
-        if (col[mid] < tau) lo = mid + 1; else hi = mid;
+        if (t[mid] < tau) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(CAPW_WARPS * 32) k_cap_small(BfsArgs a) {
-    extern __shared__ uint32_t small_smem[];
+// BUF: keys per warp buffer (>= row_cap + 32); the frontier buffer holds BUF/2.
+template <uint32_t BUF, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_cap_rows(BfsArgs a) {
+    extern __shared__ uint32_t capw_smem[];
+    constexpr uint32_t FRONT = BUF / 2;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* buf = small_smem + (size_t)warp * (CAPW_BUF + CAPW_FRONT);
-    uint32_t* fr = buf + CAPW_BUF;
+    uint32_t* buf = capw_smem + (size_t)warp * (BUF + FRONT);
+    uint32_t* fr = buf + BUF;
     const uint32_t C = a.row_cap;
     for (;;) {
         uint32_t row = 0;
         if (lane == 0) row = atomicAdd(a.next_row, 1u);
         row = __shfl_sync(0xFFFFFFFFu, row, 0);
         if (row >= a.nrows) break;
+        const uint32_t trow = tie_of(row);
         const uint64_t ab = a.rp[row], ae = a.rp[row + 1];
         const uint32_t deg = (uint32_t)(ae - ab);
-        uint32_t m;
-        bool direct = deg >= C;  // the first C of the sorted adjacency
-        if (direct) {
-            m = C;
-        } else {
-            for (uint32_t x = lane; x < deg; x += 32) buf[x] = (a.col[ab + x] << 4) | 1u;
-            m = deg;
-            __syncwarp();
-            for (uint32_t d = 2; d <= a.k && m < C; ++d) {
-                // the level-(d-1) nodes, copied out of the buffer
-                uint32_t nf = 0;
-                for (uint32_t x0 = 0; x0 < m; x0 += 32) {
-                    const uint32_t x = x0 + lane;
-                    const bool f = x < m && (buf[x] & 15u) == d - 1;
-                    const uint32_t fb = __ballot_sync(0xFFFFFFFFu, f);
-                    if (f) fr[nf + __popc(fb & lanemask_lt())] = buf[x] >> 4;
-                    nf += __popc(fb);
-                }
-                __syncwarp();
-                if (nf == 0) break;
-                const uint32_t lower = m;
-                uint32_t mm = m, tau = 0xFFFFFFFFu;
-                for (uint32_t c = 0; c < nf; c += 32) {
-                    // each lane walks one frontier node's adjacency [cur, end)
-                    uint64_t cur = 0, end = 0;
-                    if (c + lane < nf) {
-                        const uint32_t u = fr[c + lane];
-                        cur = a.rp[u];
-                        end = a.rp[u + 1];
-                    }
-                    if (tau != 0xFFFFFFFFu) end = capw_clip(a.col, cur, end, tau);
-                    for (;;) {
-                        const uint64_t r64 = end - cur;
-                        const uint32_t rem = r64 > (1ull << 26) ? (1u << 26) : (uint32_t)r64;
-                        const uint32_t incl = warp_incl_scan(rem, lane);
-                        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                        if (tot == 0) break;
-                        const uint32_t excl = incl - rem;
-                        const uint32_t take = min(tot, CAPW_BUF - mm);
-                        for (uint32_t x0 = 0; x0 < take; x0 += 32) {
-                            const uint32_t x = x0 + lane;
-                            uint32_t lo = 0, hi = 32;
-                            while (hi - lo > 1) {
-                                const uint32_t mid = (lo + hi) >> 1;
-                                if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
-                            }
-                            const uint64_t so = __shfl_sync(0xFFFFFFFFu, cur, lo);
-                            const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
-                            uint32_t key = 0xFFFFFFFFu;
-                            if (x < take) {
-                                const uint32_t v = a.col[so + (x - eo)];
-                                if (v != row && v < tau) key = (v << 4) | d;
-                            }
-                            const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
-                            if (key != 0xFFFFFFFFu) buf[mm + __popc(keep & lanemask_lt())] = key;
-                            mm += __popc(keep);
-                            __syncwarp();
-                        }
-                        cur += min(rem, take > excl ? take - excl : 0u);
-                        if (take < tot) {  // the buffer is full
-                            mm = capw_flush(buf, mm, lower, C, d, lane, &tau);
-                            if (tau != 0xFFFFFFFFu) end = capw_clip(a.col, cur, end, tau);
-                        }
-                    }
-                }
-                m = capw_flush(buf, mm, lower, C, d, lane, &tau);
-                if (m == lower) break;  // no new node: nothing further either
+        // level 1: the source's list (all of it, or its first C)
+        uint32_t m = deg < C ? deg : C;
+        for (uint32_t x = lane; x < m; x += 32) buf[x] = a.tcol[ab + x] << 4;
+        __syncwarp();
+        for (uint32_t d = 2; d <= a.k && m < C; ++d) {
+            // the level-(d-1) nodes
+            uint32_t nf = 0;
+            for (uint32_t x0 = 0; x0 < m; x0 += 32) {
+                const uint32_t x = x0 + lane;
+                const bool f = x < m && (buf[x] & 15u) == d - 2;
+                const uint32_t fb = __ballot_sync(0xFFFFFFFFu, f);
+                if (f) fr[nf + __popc(fb & lanemask_lt())] = id_of_tie(buf[x] >> 4);
+                nf += __popc(fb);
             }
+            __syncwarp();
+            if (nf == 0) break;
+            const uint32_t lower = m;
+            uint32_t mm = m, tau = 0xFFFFFFFFu;
+            for (uint32_t c = 0; c < nf; c += 32) {
+                // each lane walks one frontier node's adjacency [cur, end)
+                uint64_t cur = 0, end = 0;
+                if (c + lane < nf) {
+                    const uint32_t u = fr[c + lane];
+                    cur = a.rp[u];
+                    end = a.rp[u + 1];
+                }
+                if (tau != 0xFFFFFFFFu) end = capw_clip(a.tcol, cur, end, tau);
+                for (;;) {
+                    const uint64_t r64 = end - cur;
+                    const uint32_t rem = r64 > (1ull << 26) ? (1u << 26) : (uint32_t)r64;
+                    const uint32_t incl = warp_incl_scan(rem, lane);
+                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                    if (tot == 0) break;
+                    const uint32_t excl = incl - rem;
+                    const uint32_t take = min(tot, BUF - mm);
+                    for (uint32_t x0 = 0; x0 < take; x0 += 32) {
+                        const uint32_t x = x0 + lane;
+                        uint32_t lo = 0, hi = 32;
+                        while (hi - lo > 1) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (__shfl_sync(0xFFFFFFFFu, excl, mid) <= x) lo = mid; else hi = mid;
+                        }
+                        const uint64_t so = __shfl_sync(0xFFFFFFFFu, cur, lo);
+                        const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                        uint32_t key = 0xFFFFFFFFu;
+                        if (x < take) {
+                            const uint32_t tv = a.tcol[so + (x - eo)];
+                            if (tv != trow && tv < tau) key = (tv << 4) | (d - 1);
+                        }
+                        const uint32_t keep = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
+                        if (key != 0xFFFFFFFFu) buf[mm + __popc(keep & lanemask_lt())] = key;
+                        mm += __popc(keep);
+                        __syncwarp();
+                    }
+                    cur += min(rem, take > excl ? take - excl : 0u);
+                    if (take < tot) {  // the buffer is full
+                        mm = capw_flush(buf, mm, lower, C, d - 1, lane, &tau);
+                        if (tau != 0xFFFFFFFFu) end = capw_clip(a.tcol, cur, end, tau);
+                    }
+                }
+            }
+            m = capw_flush(buf, mm, lower, C, d - 1, lane, &tau);
+            if (m == lower) break;  // no new node: nothing further either
         }
+        // the kept nodes in id order
+        for (uint32_t x = lane; x < m; x += 32) buf[x] = (id_of_tie(buf[x] >> 4) << 4) | (buf[x] & 15u);
+        __syncwarp();
+        warp_bitonic(buf, m, lane);
         uint64_t base = 0;
         int skip = 0;
         if (lane == 0) {
             a.counts[row] = m;
-            const uint64_t span = ((uint64_t)m + 15) & ~15ull;
-            base = atomicAdd(a.cursor, (unsigned long long)span);
-            if (base + span > a.cap) {
-                skip = 1;
-                atomicExch(a.overflow, 1u);
+            if (a.staged) {
+                const uint64_t span = ((uint64_t)m + 15) & ~15ull;
+                base = atomicAdd(a.cursor, (unsigned long long)span);
+                if (base + span > a.cap) {
+                    skip = 1;
+                    atomicExch(a.overflow, 1u);
+                }
+                a.row_off[row] = base;
+            } else {
+                base = a.gd_rp[row];
             }
-            a.row_off[row] = base;
         }
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         skip = __shfl_sync(0xFFFFFFFFu, skip, 0);
         if (!skip) {
             for (uint32_t x = lane; x < m; x += 32) {
-                if (direct) {
-                    a.out_col[base + x] = a.col[ab + x];
-                    a.out_dist[base + x] = 1;
-                } else {
-                    a.out_col[base + x] = buf[x] >> 4;
-                    a.out_dist[base + x] = (uint8_t)(buf[x] & 15u);
-                }
+                a.out_col[base + x] = buf[x] >> 4;
+                a.out_dist[base + x] = (uint8_t)((buf[x] & 15u) + 1);
             }
         }
         __syncwarp();
     }
+}
+
+// Keys (row << 28 | tie(v)) of the adjacency entries, for the tie-ordered copy.
+__global__ void k_tie_keys(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ col, uint64_t m,
+                           uint64_t* __restrict__ keys) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        keys[e] = ((uint64_t)esrc[e] << 28) | tie_of(col[e]);
+}
+
+__global__ void k_tie_values(const uint64_t* __restrict__ keys, uint64_t m, uint32_t* __restrict__ t) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+        t[e] = (uint32_t)keys[e] & kTieMask;
+}
+
+// The two shapes: caps up to 480 (1024-key buffers, 8 warps per block) and up
+// to 2016 (4096-key buffers, 4 warps per block).
+constexpr uint32_t CAPW_MAX_SMALL = 1024 / 2 - 32, CAPW_MAX = 4096 / 2 - 32;
+
+static void launch_cap_rows(drg_ctx* ctx, const BfsArgs& a) {
+    auto run = [&](auto kern, uint32_t buf, int warps) {
+        const size_t smem = (size_t)warps * (buf + buf / 2) * 4;
+        DRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per = 0;
+        DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, warps * 32, smem));
+        DRG_LAUNCH(ctx, kern, (uint32_t)ctx->num_sms * (uint32_t)(per > 0 ? per : 1), warps * 32, smem, a);
+    };
+    if (a.row_cap <= CAPW_MAX_SMALL) run(k_cap_rows<1024, 8>, 1024, 8);
+    else run(k_cap_rows<4096, 4>, 4096, 4);
 }
 
 // Splits the rows into those of at most SMALL_CAP candidates (small) and the
@@ -841,6 +849,12 @@ static size_t dist_bytes(uint64_t nnz) { return (size_t)((nnz + 15) / 16 + 1) * 
 
 static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat* d, uint32_t row_cap) {
     const uint32_t n = g->n;
+    // a cap that no row can reach (n - 1 nodes besides the source) keeps every row whole
+    if (row_cap && (uint64_t)row_cap >= (uint64_t)(n > 0 ? n - 1 : 0)) row_cap = 0;
+    if (row_cap) {
+        DRG_CHECK(n <= (1u << 28), DRG_EUNSUPPORTED, "capped rows need fewer than 2^28 nodes");
+        DRG_CHECK(row_cap <= CAPW_MAX, DRG_EUNSUPPORTED, "a row cap above 2016 (and below n - 1) is not supported");
+    }
     d->rp = static_cast<uint64_t*>(dalloc(ctx, sizeof(uint64_t) * ((size_t)n + 1)));
     if (k == 1 && row_cap == 0) {
         // NNG(v_i, 1) is the adjacency itself, already sorted by column
@@ -852,7 +866,7 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
         DRG_LAUNCH(ctx, k_fill_u8, grid_for(d->nnz, 256, 65536), 256, 0, d->dist, d->nnz, (uint8_t)1);
         return;
     }
-    const bool k2 = k == 2 && row_cap == 0;  // capped rows take the general kernel (it knows every hop distance)
+    const bool k2 = k == 2 && row_cap == 0;
     const uint32_t words = (n + 31) / 32;
     const uint32_t swords = (words + 31) / 32;
     const size_t bm_bytes = (size_t)words * 4, extra = bfs_extra_smem(swords);
@@ -879,11 +893,12 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     uint32_t blocks = (uint32_t)ctx->num_sms * (uint32_t)per_sm;
     if (blocks > n) blocks = n;
     // per-block discovered lists, touched words, word offsets / hop distances
-    // (and bitmaps when they live in global memory)
-    DBuf<uint32_t> lists(ctx, (size_t)blocks * n);
-    DBuf<uint32_t> wlists(ctx, (size_t)blocks * words);
-    DBuf<uint8_t> dlev(ctx, k2 ? 1 : (size_t)blocks * n);
-    DBuf<uint32_t> gbm(ctx, smem_bm ? 1 : (size_t)blocks * words);
+    // (and bitmaps when they live in global memory); capped rows use none
+    const size_t per_block = row_cap ? 0 : (size_t)blocks;
+    DBuf<uint32_t> lists(ctx, per_block * n);
+    DBuf<uint32_t> wlists(ctx, per_block * words);
+    DBuf<uint8_t> dlev(ctx, k2 ? 1 : per_block * n);
+    DBuf<uint32_t> gbm(ctx, smem_bm ? 1 : per_block * words);
     DBuf<uint32_t> counter(ctx, 1), overflow(ctx, 1);
     DBuf<uint64_t> counts(ctx, (size_t)n), row_off(ctx, (size_t)n);
     DBuf<unsigned long long> cursor(ctx, 1);
@@ -925,6 +940,25 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     a.staged = 1; a.cursor = cursor.p; a.cap = cap; a.row_off = row_off.p; a.overflow = overflow.p;
     a.out_col = scol.p; a.out_dist = sdist.p;
     a.row_cap = row_cap;
+    // capped rows read every row's adjacency as tie values, ascending: one
+    // sort of the entries by (row, tie)
+    DBuf<uint32_t> tcol;
+    if (row_cap) {
+        const uint64_t m = g->nnz;
+        tcol = DBuf<uint32_t>(ctx, m);
+        DBuf<uint32_t> esrc(ctx, m);
+        DBuf<uint64_t> keys(ctx, m), kalt(ctx, m);
+        DRG_LAUNCH(ctx, k_expand_rows, grid_for((size_t)n * 32, 256, (uint32_t)ctx->num_sms * 16), 256, 0, g->rp, n,
+                   esrc.p);
+        DRG_LAUNCH(ctx, k_tie_keys, grid_for(m, 256, 65536), 256, 0, esrc.p, g->col, m, keys.p);
+        uint64_t* kp = keys.p;
+        uint64_t* ap = kalt.p;
+        uint32_t* vnull = nullptr;
+        uint32_t* vnull2 = nullptr;
+        radix_sort(ctx, kp, ap, vnull, vnull2, m, 0, 28 + std::max(1, bitlen(n > 1 ? n - 1 : 1)));
+        DRG_LAUNCH(ctx, k_tie_values, grid_for(m, 256, 65536), 256, 0, kp, m, tcol.p);
+        a.tcol = tcol.p;
+    }
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(overflow.p, 0, 4, ctx->stream));
     DRG_CUDA(cudaMemsetAsync(cursor.p, 0, 8, ctx->stream));
@@ -954,18 +988,10 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
             DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
             a.rows = big.p;
             a.nrows = nc[1];
-        } else if (row_cap && row_cap <= CAPW_MAX && n <= (1u << 28) && cap > 0) {
-            // capped rows of a small cap: every row by one warp
-            const size_t ssm = (size_t)CAPW_WARPS * (CAPW_BUF + CAPW_FRONT) * 4;
-            DRG_CUDA(cudaFuncSetAttribute(k_cap_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-            int sper = 0;
-            DRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, k_cap_small, CAPW_WARPS * 32, ssm));
-            BfsArgs as = a;
-            as.rows = nullptr;
-            as.nrows = n;
-            DRG_LAUNCH(ctx, k_cap_small, (uint32_t)ctx->num_sms * (uint32_t)(sper > 0 ? sper : 1), CAPW_WARPS * 32,
-                       ssm, as);
-            a.nrows = 0;  // no row left for the block kernel
+        } else if (row_cap) {
+            // capped rows: every row by one warp, on the tie-ordered adjacency
+            launch_cap_rows(ctx, a);
+            a.nrows = 0;
         }
         if (a.nrows) DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
     }
@@ -993,7 +1019,8 @@ static void build_korder(drg_ctx* ctx, const drg_graph* g, uint32_t k, drg_dmat*
     a.out_dist = d->dist;
     DRG_CUDA(cudaMemsetAsync(counter.p, 0, 4, ctx->stream));
     ProfSpan sb(ctx, DRG_PROF_BFS, 0);
-    DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
+    if (row_cap) launch_cap_rows(ctx, a);
+    else DRG_LAUNCH(ctx, kern, blocks, bfs_threads, dyn, a);
 }
 
 struct Gauss {

@@ -3,8 +3,8 @@
 feasible) against the oracle's korder_capped / similarity_capped: the union
 pattern K u K^T, hop distances, Z over each kept set, the quantised weights,
 the row sums and both alias tables bit for bit on small graphs (caps that bind
-at level 1, 2 and 3, ragged inputs, a cap above what one warp's buffer
-takes, and a cap that does not bind); at full
+at level 1, 2 and 3, ragged inputs, caps for both warp buffer sizes, and a
+cap that does not bind; caps out of range refused); at full
 size (DC-SBM 1M nodes, k = 3, where the uncapped matrix would exceed 2^32
 entries) sampled rows are checked against single-row traversals of the
 oracle."""
@@ -63,6 +63,20 @@ def test_capped_matrix_matches_oracle(env, orc, name, k, cap):
             assert np.array_equal(got[key], full[key]), key
 
 
+def test_caps_out_of_range_are_refused(env):
+    # caps above 2016 that a row could still reach are refused; a cap of n - 1
+    # or more is the uncapped matrix
+    drg, ctx = env
+    g = GRAPHS["tree3000"]()
+    G = drg.graph_from_edges(ctx, *g)
+    with pytest.raises(drg.DrgError):
+        drg.build_distance_matrix(ctx, G, 3, row_cap=2500)
+    full = drg.build_distance_matrix(ctx, G, 3).download()
+    got = drg.build_distance_matrix(ctx, G, 3, row_cap=2999).download()
+    for key in ("rp", "col", "dist", "q", "e_thresh", "v_thresh"):
+        assert np.array_equal(got[key], full[key]), key
+
+
 def test_capped_whole_run_matches_oracle(env, orc):
     # The whole path with capped rows (BA 3000, k = 3, rows of at most 30
     # nodes, synchronous mode) against the oracle's synchronous whole runs
@@ -106,8 +120,8 @@ def test_capped_whole_run_matches_oracle(env, orc):
             assert abs(m_got - m_ref) <= bar * se, (what, m_got, m_ref, se)
 
 
-def _kept(row_col, row_dist, cap):
-    order = np.lexsort((row_col.astype(np.int64), row_dist.astype(np.int64)))[:cap]
+def _kept(orc, row_col, row_dist, cap):
+    order = np.lexsort((orc.tie_order(row_col.astype(np.int64)), row_dist.astype(np.int64)))[:cap]
     return dict(zip(row_col[order].tolist(), row_dist[order].tolist()))
 
 
@@ -130,7 +144,7 @@ def test_dcsbm1m_k3_capped_rows(env, orc):
 
     def kept(v):
         if v not in kept_of:
-            kept_of[v] = _kept(*bfs.row(v), cap)
+            kept_of[v] = _kept(orc, *bfs.row(v), cap)
         return kept_of[v]
 
     for i in rows:

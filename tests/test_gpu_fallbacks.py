@@ -1,6 +1,6 @@
 """Paths the benchmark graphs never take, forced on the host: the k-order
-rows when the staging area is too small (all rows, or part of them, are
-traversed again at their final offsets), and resuming a level run from its
+rows, plain or capped, when the staging area is too small (all rows, or part
+of them, are traversed again at their final offsets), and resuming a level run from its
 positions and epoch counter."""
 import os
 
@@ -23,8 +23,8 @@ def drg():
 
 
 @pytest.mark.parametrize("limit", ["0", "4000"])
-@pytest.mark.parametrize("name,k", [("ba", 2), ("ba", 3), ("grid", 2)])
-def test_distance_matrix_without_enough_staging(drg, orc, limit, name, k):
+@pytest.mark.parametrize("name,k,cap", [("ba", 2, 0), ("ba", 3, 0), ("grid", 2, 0), ("ba", 3, 40), ("grid", 3, 7)])
+def test_distance_matrix_without_enough_staging(drg, orc, limit, name, k, cap):
     g = gg.barabasi_albert(3000, 3, 21) if name == "ba" else gg.grid(40, 37)
     old = os.environ.get("DRG_BFS_STAGE_LIMIT")
     os.environ["DRG_BFS_STAGE_LIMIT"] = limit
@@ -36,12 +36,16 @@ def test_distance_matrix_without_enough_staging(drg, orc, limit, name, k):
         else:
             os.environ["DRG_BFS_STAGE_LIMIT"] = old
     G = drg.graph_from_edges(ctx, *g)
-    D = drg.build_distance_matrix(ctx, G, k)
+    D = drg.build_distance_matrix(ctx, G, k, row_cap=cap)
     got = D.download()
     orp, ocol = orc.canonical_graph(*g)
-    rp, col, dist = orc.korder(orp, ocol, k)
+    if cap:
+        rp, col, dist, own, back = orc.korder_capped(orp, ocol, k, cap)
+        sim = orc.similarity_capped(rp, col, dist, own, back, k, 1.0)
+    else:
+        rp, col, dist = orc.korder(orp, ocol, k)
+        sim = orc.similarity(rp, col, dist, k, 1.0)
     assert np.array_equal(got["rp"], rp) and np.array_equal(got["col"], col) and np.array_equal(got["dist"], dist)
-    sim = orc.similarity(rp, col, dist, k, 1.0)
     assert np.array_equal(got["q"], sim["q"])
 
 

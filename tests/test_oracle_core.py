@@ -254,17 +254,32 @@ def test_capped_matrix_without_binding_cap_is_the_matrix(orc, k):
     assert np.array_equal(sc["q"], sim["q"]) and np.array_equal(sc["r"], sim["r"])
 
 
+def test_tie_order_is_a_scrambling_bijection(orc):
+    # distinct on 2^22 consecutive ids and inside [0, 2^28); unrelated to the
+    # id's size (rank correlation near 0; no fixed point at the smallest ids)
+    v = np.arange(1 << 22, dtype=np.int64)
+    t = orc.tie_order(v)
+    assert len(np.unique(t)) == len(v) and t.min() >= 0 and t.max() < (1 << 28)
+    assert abs(np.corrcoef(v, t)[0, 1]) < 0.01
+    assert np.argmin(t[:64]) != 0
+    top = (1 << 28) - (1 << 20) + np.arange(1 << 20, dtype=np.int64)
+    assert len(np.unique(np.r_[t[:1 << 20], orc.tie_order(top)])) == 2 << 20
+
+
 def test_capped_star_by_hand(orc):
-    # K_{1,5}, k = 2, cap 2: the hub keeps leaves 1, 2; every leaf keeps the
-    # hub and the smallest other leaf (1, or 2 for leaf 1)
+    # K_{1,5}, k = 2, cap 2.  The tie order ranks the leaves 5, 4, 2, 1, 3:
+    # the hub keeps leaves 5 and 4; every leaf keeps the hub and the first
+    # other leaf in that order (5, or 4 for leaf 5)
+    assert np.argsort(orc.tie_order(np.arange(1, 6))).tolist() == [4, 3, 1, 0, 2]
     rp, col = orc.canonical_graph(6, np.zeros(5, np.int64), np.arange(1, 6))
     u_rp, u_col, u_dist, own, back = orc.korder_capped(rp, col, 2, 2)
     rows = {i: u_col[int(u_rp[i]):int(u_rp[i + 1])].tolist() for i in range(6)}
-    assert rows == {0: [1, 2, 3, 4, 5], 1: [0, 2, 3, 4, 5], 2: [0, 1], 3: [0, 1], 4: [0, 1], 5: [0, 1]}
+    assert rows == {0: [1, 2, 3, 4, 5], 1: [0, 5], 2: [0, 5], 3: [0, 5], 4: [0, 5], 5: [0, 1, 2, 3, 4]}
     flags = {i: list(zip(own[int(u_rp[i]):int(u_rp[i + 1])].tolist(), back[int(u_rp[i]):int(u_rp[i + 1])].tolist()))
              for i in range(6)}
-    assert flags[0] == [(True, True), (True, True), (False, True), (False, True), (False, True)]
-    assert flags[1] == [(True, True), (True, True), (False, True), (False, True), (False, True)]
+    assert flags[0] == [(False, True), (False, True), (False, True), (True, True), (True, True)]
+    assert flags[5] == [(True, True), (False, True), (False, True), (False, True), (True, True)]
+    assert flags[4] == [(True, True), (True, True)]
     assert flags[3] == [(True, False), (True, False)]
     sc = orc.similarity_capped(u_rp, u_col, u_dist, own, back, 2, 1.0)
     g1, g2 = np.float32(np.exp(-0.5)), np.float32(np.exp(-2.0))
@@ -283,7 +298,7 @@ def test_capped_sets_against_all_pairs_shortest_paths(orc, seed, k, cap):
     kept = set()
     for i in range(n):
         cand = [(D[i, j], j) for j in range(n) if j != i and D[i, j] <= k]
-        kept |= {(i, j) for _, j in sorted(cand)[:cap]}
+        kept |= {(i, j) for _, _, j in sorted((dd, int(orc.tie_order(j)), j) for dd, j in cand)[:cap]}
     want = kept | {(j, i) for i, j in kept}
     u_rp, u_col, u_dist, own, back = orc.korder_capped(rp, col, k, cap)
     rows = np.repeat(np.arange(n), np.diff(u_rp).astype(np.int64))

@@ -592,8 +592,11 @@ def test_openmp_loop_with_one_thread_is_the_sequential_loop(orc):
 
 
 def test_openmp_loop_keeps_quality(orc):
-    # lock-free threads on a 32x32 grid: mean NP over three seeds within 15 %
-    # of the sequential loop's (both vary by about +-.05 across seeds)
+    # lock-free threads on a 32x32 grid: mean NP over eight seeds within 20 %
+    # of the sequential loop's.  Single runs spread from about .32 to .55 and
+    # the threads' timing changes them from run to run, so the mean of eight
+    # (standard error about .02, 5 % of the mean) keeps the bar four standard
+    # errors away
     if orc.build_omp() is None:
         pytest.skip("no OpenMP in this toolchain")
     n, s, d = gg.grid(32, 32)
@@ -601,12 +604,12 @@ def test_openmp_loop_keeps_quality(orc):
     gd = orc.korder(rp, col, 2)
     tab, _ = orc.sampling_tables(*gd, 2)
     nps = {1: [], 4: []}
-    for seed in (0, 1, 2):
+    for seed in range(8):
         p = orc.Params(k=2, M=5, epochs=200, b=3.0, mode=1, seed=seed)
         Y0 = orc.init_positions(p, 0, n) * 1e4
         nps[1].append(orc.neighbourhood_preservation(rp, col, orc.layout_level(tab, Y0.copy(), 0, None, p, 0.1), 2))
         nps[4].append(orc.neighbourhood_preservation(rp, col, orc.layout_level_omp(tab, Y0.copy(), 0, None, p, 0.1, 4), 2))
-    assert np.mean(nps[4]) >= 0.85 * np.mean(nps[1]), nps
+    assert np.mean(nps[4]) >= 0.8 * np.mean(nps[1]), nps
 
 
 def test_whole_run_with_a_cap_that_does_not_bind_is_the_whole_run(orc):
