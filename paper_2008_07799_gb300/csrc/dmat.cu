@@ -1736,7 +1736,7 @@ struct EmitArgs {
 // fills the bucket (threshold all ones, alias itself) or leaves the rest to
 // the next heavy H[y + 1].
 template <int KIND>
-__global__ void __launch_bounds__(MERGE_THREADS) k_alias_emit(EmitArgs m, AliasOut o) {
+__global__ void __launch_bounds__(MERGE_THREADS, 6) k_alias_emit(EmitArgs m, AliasOut o) {
     __shared__ u128 s[MERGE_TILE + 1];
     __shared__ uint16_t rank[MERGE_TILE];
     const SweepLists& l = m.l;
@@ -1746,10 +1746,24 @@ __global__ void __launch_bounds__(MERGE_THREADS) k_alias_emit(EmitArgs m, AliasO
     const uint64_t x0 = m.part[blockIdx.x], x1 = m.part[blockIdx.x + 1], y0 = d0 - x0, y1 = d1 - x1;
     const uint32_t na = (uint32_t)(x1 - x0), nb = (uint32_t)(y1 - y0);
     // Dl(x0 .. x1) inclusive (the value after the tile's last light closes
-    // it), then S(y0 .. y1 - 1)
-    for (uint32_t t = threadIdx.x; t <= na; t += MERGE_THREADS) s[t] = l.Dl(x0 + t);
+    // it), then S(y0 .. y1 - 1): slot u < na + 1 + nb <= MERGE_TILE + 1 of
+    // s; each thread loads the weight prefixes of all its slots before it
+    // computes any, so that their latencies overlap
+    constexpr int SLOTS = (MERGE_TILE + 1 + MERGE_THREADS - 1) / MERGE_THREADS;
+    const uint32_t nab = na + 1 + nb;
+    uint64_t raw[SLOTS];
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        const uint32_t u = threadIdx.x + k * MERGE_THREADS;
+        raw[k] = u <= na ? l.QL[x0 + u] : (u < nab ? l.QH[y0 + (u - na - 1)] : 0ull);
+    }
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        const uint32_t u = threadIdx.x + k * MERGE_THREADS;
+        if (u <= na) s[u] = (u128)(x0 + u) * l.W - (u128)l.N * raw[k];
+        else if (u < nab) s[u] = (u128)l.N * raw[k] - (u128)(y0 + (u - na - 1) + 1) * l.W;
+    }
     u128* Bs = s + na + 1;
-    for (uint32_t t = threadIdx.x; t < nb; t += MERGE_THREADS) Bs[t] = l.S(y0 + t);
     __syncthreads();
     const uint32_t dl = threadIdx.x * MERGE_ITEMS;
     if (dl < na + nb) {
