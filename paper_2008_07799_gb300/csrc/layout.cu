@@ -84,14 +84,27 @@ struct Words {
     }
 };
 
+// A 16-byte edge record, read with an L2 evict-first policy: the table is
+// far larger than L2 and each record is read once at a random place, so its
+// lines should leave L2 before the positions and node tables do.
+__device__ __forceinline__ uint4 ld_record(const uint4* p) {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
 // Edge record of bucket bkt: the first 16 bytes, and j1 of the wide form.
 __device__ __forceinline__ void load_edge(const EpochArgs& a, uint64_t bkt, uint4& e, uint32_t& j1) {
     if (a.packed) {
-        e = __ldg(static_cast<const uint4*>(a.etab) + bkt);
+        e = ld_record(static_cast<const uint4*>(a.etab) + bkt);
         j1 = 0;
     } else {
         const EdgeRec* r = static_cast<const EdgeRec*>(a.etab) + bkt;
-        e = __ldg(reinterpret_cast<const uint4*>(r));
+        e = ld_record(reinterpret_cast<const uint4*>(r));
         j1 = __ldg(&r->j1);
     }
 }
