@@ -359,6 +359,32 @@ __global__ void __launch_bounds__(BFS_THREADS, BFS_THREADS == 512 ? 3 : 1) k_bfs
     }
 }
 
+// Ascending bitonic sort of buf[0, m) by one warp; pads to a power of two with
+// all-ones keys (buf must hold that power of two).
+__device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t lane) {
+    uint32_t P = 1, lp = 0;
+    while (P < m) {
+        P <<= 1;
+        ++lp;
+    }
+    for (uint32_t x = m + lane; x < P; x += 32) buf[x] = 0xFFFFFFFFu;
+    __syncwarp();
+    for (uint32_t lk = 1; lk <= lp; ++lk) {
+        for (int lj = (int)lk - 1; lj >= 0; --lj) {
+            const uint32_t j = 1u << lj;
+            for (uint32_t t = lane; t < P / 2; t += 32) {
+                const uint32_t i = ((t >> lj) << (lj + 1)) | (t & (j - 1)), l = i + j;
+                const uint32_t u = buf[i], w = buf[l];
+                if ((u > w) == (((i >> lk) & 1u) == 0)) {
+                    buf[i] = w;
+                    buf[l] = u;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // ------------------------------------------------------------------ small rows, k = 2
 // Rows whose candidate count (the source's degree plus its neighbours'
 // degrees) is at most SMALL_CAP are built by one warp each, with no block
@@ -417,24 +443,9 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_bfs_small(BfsArgs a) {
                 m += __popc(keep);
             }
         }
-        // bitonic sort of buf[0, P), padded with the largest key
-        uint32_t P = 1;
-        while (P < m) P <<= 1;
-        for (uint32_t x = m + lane; x < P; x += 32) buf[x] = 0xFFFFFFFFu;
+        // keys v << 1 | 1 stay below the all-ones padding (ids < 2^31 - 1)
         __syncwarp();
-        for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t t = lane; t < P / 2; t += 32) {
-                    const uint32_t i = (t / j) * 2 * j + (t % j), l = i + j;
-                    const uint32_t u = buf[i], w = buf[l];
-                    if ((u > w) == ((i & k) == 0)) {
-                        buf[i] = w;
-                        buf[l] = u;
-                    }
-                }
-                __syncwarp();
-            }
-        }
+        warp_bitonic(buf, m, lane);
         // first key of each node, counted and written in order
         uint32_t total = 0;
         for (uint32_t x0 = 0; x0 < m; x0 += 32) {
@@ -516,32 +527,6 @@ __device__ __forceinline__ uint32_t id_of_tie(uint32_t x) {
     x ^= x >> 14;
     x = (x * 0x3811693u) & kTieMask;
     return x ^ 0x2545F49u;
-}
-
-// Ascending bitonic sort of buf[0, m) by one warp; pads to a power of two with
-// all-ones keys (buf must hold that power of two).
-__device__ __forceinline__ void warp_bitonic(uint32_t* buf, uint32_t m, uint32_t lane) {
-    uint32_t P = 1, lp = 0;
-    while (P < m) {
-        P <<= 1;
-        ++lp;
-    }
-    for (uint32_t x = m + lane; x < P; x += 32) buf[x] = 0xFFFFFFFFu;
-    __syncwarp();
-    for (uint32_t lk = 1; lk <= lp; ++lk) {
-        for (int lj = (int)lk - 1; lj >= 0; --lj) {
-            const uint32_t j = 1u << lj;
-            for (uint32_t t = lane; t < P / 2; t += 32) {
-                const uint32_t i = ((t >> lj) << (lj + 1)) | (t & (j - 1)), l = i + j;
-                const uint32_t u = buf[i], w = buf[l];
-                if ((u > w) == (((i >> lk) & 1u) == 0)) {
-                    buf[i] = w;
-                    buf[l] = u;
-                }
-            }
-            __syncwarp();
-        }
-    }
 }
 
 // Sorts buf[0, m), keeps the first key of each node and, when more than cap
