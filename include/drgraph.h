@@ -460,8 +460,9 @@ drg_status drg_autotune_clear(void);
  * stream:
  *   DRG_PROBE_LOAD8    random 8-byte loads through L2 (ld.global.cg.v2.f32),
  *                      the position gathers
- *   DRG_PROBE_LOAD16   random 16-byte loads (ld.global.nc.v4.u32), the table
- *                      records
+ *   DRG_PROBE_LOAD16   random 16-byte loads (ld.global.nc.L2::64B.v4.u32: a
+ *                      64-byte L2 prefetch size, as the edge records are read),
+ *                      the table records
  *   DRG_PROBE_RED8     random 8-byte vector atomic adds (red of a float2),
  *                      the position updates
  *   DRG_PROBE_LOAD16_EVICT_FIRST  as LOAD16 with an L2 evict-first policy

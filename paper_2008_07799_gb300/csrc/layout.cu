@@ -84,14 +84,16 @@ struct Words {
     }
 };
 
-// A 16-byte edge record, read with an L2 evict-first policy: the table is
-// far larger than L2 and each record is read once at a random place, so its
-// lines should leave L2 before the positions and node tables do.
+// A 16-byte edge record, read with an L2 evict-first policy and a 64-byte
+// L2 prefetch size: the table is far larger than L2 and each record is read
+// once at a random place, so its lines should leave L2 before the positions
+// and node tables do, and a miss should fetch 64 bytes rather than a
+// 128-byte line.
 __device__ __forceinline__ uint4 ld_record(const uint4* p) {
     uint64_t pol;
     asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     uint4 v;
-    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+    asm("ld.global.nc.L2::cache_hint.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(p), "l"(pol));
     return v;

@@ -42,15 +42,19 @@ __device__ __forceinline__ float2 ld_cg_f2(const float2* p) {
     return v;
 }
 
+// 16-byte loads as the level kernels read their table records: with a
+// 64-byte L2 prefetch size (a miss then fetches 64 bytes from DRAM, not a
+// 128-byte line)
 __device__ __forceinline__ uint4 ld_nc_u4(const uint4* p) {
     uint4 v;
-    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
     return v;
 }
 
 __device__ __forceinline__ uint4 ld_nc_u4_evict_first(const uint4* p, uint64_t pol) {
     uint4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+    asm volatile("ld.global.nc.L2::cache_hint.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p), "l"(pol));
     return v;
