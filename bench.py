@@ -150,7 +150,8 @@ PROBE_HBM_BYTES = 8 << 30     # far larger than L2, like the edge table
 def measure_probes(drg, ctx):
     """Random-access ceilings of this GPU (accesses/s), each the best of three
     launches after a warm-up: L2-resident 8-byte loads, 16-byte loads and
-    8-byte atomic adds, each alone and loads and atomic adds mixed two to one;
+    8-byte atomic adds, each alone, and a layout sample's mix (read-only table
+    loads, position loads and atomic adds, one to one to one);
     16-byte loads over a buffer far larger than L2 (plain
     and evict-first); and the streaming copy (GB/s, read + written)."""
     out = {}
@@ -178,7 +179,7 @@ def roofline_l2_hbm(kernel, M, precision, level_samples, kernel_ms, probes, hbm_
     """Both ceilings of a level-kernel run.  level_samples: [(samples, coarse)].
     L2: the time the run's L2 accesses take at the probes' rates, against the
     kernel's time -- at the rate of the probe that interleaves loads and
-    atomic adds two to one as the kernel does (the headline: mixing them costs
+    atomic adds as a layout sample does (the headline: mixing them costs
     throughput, so the kinds' separate rates overstate the ceiling), and at
     the kinds' separate rates; HBM: the edge records, one random 16-byte read
     per sample, against the random-read probe and against the copy peak."""
@@ -196,7 +197,8 @@ def roofline_l2_hbm(kernel, M, precision, level_samples, kernel_ms, probes, hbm_
     l2 = {"achieved": l2_bytes / sec / 1e9, "peak": l2_bytes / t_mix / 1e9, "unit": "GB/s", "frac": t_mix / sec,
           "algorithmic_bytes_per_sample": l2_bytes / max(samples, 1),
           "peak_kind": "measured: random-access probe (drg_probe_memory, PROBE_MIX_LOAD8_RED8) of this run, 8-byte "
-                       "loads and atomic adds interleaved two to one over a 32 MiB buffer, at the kernel's count of "
+                       "read-only table loads, position loads and position atomic adds interleaved one to one to one "
+                       "over a 32 MiB buffer, at the kernel's count of "
                        "L2 accesses per sample",
           "separate": {"peak": l2_bytes / t_sep / 1e9, "frac": t_sep / sec,
                        "peak_kind": "measured: the probes of each access kind alone (8-byte loads, 16-byte loads, "

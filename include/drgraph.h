@@ -468,10 +468,13 @@ drg_status drg_autotune_clear(void);
  *   DRG_PROBE_LOAD16_EVICT_FIRST  as LOAD16 with an L2 evict-first policy
  *   DRG_PROBE_COPY     streaming copy of the buffer's first half to its second
  *                      half (16-byte vectors; `accesses` is ignored)
- *   DRG_PROBE_MIX_LOAD8_RED8  random 8-byte loads (as LOAD8) and 8-byte
- *                      atomic adds (as RED8) interleaved two to one, the mix of
- *                      a layout sample (12 or 14 loads, 7 atomic adds); both
- *                      kinds count as accesses
+ *   DRG_PROBE_MIX_LOAD8_RED8  a layout sample's mix, interleaved one to one
+ *                      to one: random read-only 8-byte loads (ld.global.nc)
+ *                      from the buffer's first half (the tables), random
+ *                      8-byte loads through L2 (as LOAD8) and 8-byte atomic
+ *                      adds (as RED8) on its second half (the positions); a
+ *                      sample makes 5 to 7 table reads, 7 position reads and 7
+ *                      atomic adds; all count as accesses
  * Random places are uniform over the buffer (a 32-bit linear congruential
  * stream per thread, scaled to the element count).  `accesses` (1 .. 1e11) is
  * rounded up to whole iterations; *done receives the accesses made (COPY: the

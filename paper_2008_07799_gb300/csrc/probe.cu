@@ -10,7 +10,8 @@
 // chosen size (inside L2, or far larger than L2 for the HBM-resident table),
 // with enough independent accesses in flight on every SM to saturate the
 // memory system rather than the issuing threads; one more probe interleaves
-// loads and atomic adds two to one, the level kernels' own mix.
+// the three kinds of a layout sample one to one to one: read-only loads of
+// "tables" and loads and atomic adds of "positions".
 #include "prims.cuh"
 
 namespace drg {
@@ -90,13 +91,20 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(void* __restrict__ buf,
 #pragma unroll
             for (uint32_t u = 0; u < kProbeUnroll; ++u)
                 atomicAdd(static_cast<float2*>(buf) + probe_next(x, nelem), make_float2(1.f, -1.f));
-        } else {  // DRG_PROBE_MIX_LOAD8_RED8: two loads per atomic add, both at random places
+        } else {  // DRG_PROBE_MIX_LOAD8_RED8: a layout sample's mix, one to one to one
+            // read-only 8-byte loads from the first half of the buffer (the
+            // tables), 8-byte loads through L2 and atomic adds on the second
+            // half (the positions), all at random places
+            const uint64_t half = nelem / 2;
+            const float2* tab = static_cast<const float2*>(buf);
+            float2* pos = static_cast<float2*>(buf) + half;
             float2 v[kProbeUnroll];
 #pragma unroll
-            for (uint32_t u = 0; u < kProbeUnroll; ++u) v[u] = ld_cg_f2(static_cast<const float2*>(buf) + probe_next(x, nelem));
+            for (uint32_t u = 0; u < kProbeUnroll / 2; ++u) v[u] = __ldg(tab + probe_next(x, half));
 #pragma unroll
-            for (uint32_t u = 0; u < kProbeUnroll / 2; ++u)
-                atomicAdd(static_cast<float2*>(buf) + probe_next(x, nelem), make_float2(1.f, -1.f));
+            for (uint32_t u = kProbeUnroll / 2; u < kProbeUnroll; ++u) v[u] = ld_cg_f2(pos + probe_next(x, half));
+#pragma unroll
+            for (uint32_t u = 0; u < kProbeUnroll / 2; ++u) atomicAdd(pos + probe_next(x, half), make_float2(1.f, -1.f));
 #pragma unroll
             for (uint32_t u = 0; u < kProbeUnroll; ++u) acc += __float_as_uint(v[u].x) ^ __float_as_uint(v[u].y);
         }
