@@ -5,9 +5,9 @@ pattern K u K^T, hop distances, Z over each kept set, the quantised weights,
 the row sums and both alias tables bit for bit on small graphs (caps that bind
 at level 1, 2 and 3, ragged inputs, caps for both warp buffer sizes, and a
 cap that does not bind; caps out of range refused); at full
-size (DC-SBM 1M nodes, k = 3, where the uncapped matrix would exceed 2^32
-entries) sampled rows are checked against single-row traversals of the
-oracle."""
+size (DC-SBM 1M nodes and R-MAT scale 22, k = 3, where the uncapped matrices
+would exceed 2^32 entries) sampled rows are checked against single-row
+traversals of the oracle."""
 import numpy as np
 import pytest
 
@@ -125,10 +125,14 @@ def _kept(orc, row_col, row_dist, cap):
     return dict(zip(row_col[order].tolist(), row_dist[order].tolist()))
 
 
-def test_dcsbm1m_k3_capped_rows(env, orc):
+@pytest.mark.parametrize("wl,nrows,nback", [("dcsbm1m", 20, 4), ("rmat22", 6, 2)])
+def test_full_size_k3_capped_rows(env, orc, wl, nrows, nback):
+    # sampled rows of the 1M-node DC-SBM and of R-MAT scale 22 (whose hubs
+    # have the smallest ids, so the tie order decides most cut levels; its
+    # rows reach most of the 2M-node component, so fewer are traversed)
     drg, ctx = env
     cap, k = 128, 3
-    g = gg.workload("dcsbm1m")
+    g = gg.workload(wl)
     orp, ocol = orc.canonical_graph(*g)
     G = drg.graph_from_edges(ctx, *g)
     D = drg.build_distance_matrix(ctx, G, k, row_cap=cap)
@@ -139,7 +143,7 @@ def test_dcsbm1m_k3_capped_rows(env, orc):
     bfs = orc.RowBFS(orp, ocol, k)
     deg = np.diff(orp).astype(np.int64)
     rng = np.random.default_rng(7)
-    rows = np.r_[rng.choice(np.nonzero(deg > 0)[0], 20, replace=False), [int(np.argmax(deg))]]
+    rows = np.r_[rng.choice(np.nonzero(deg > 0)[0], nrows, replace=False), [int(np.argmax(deg))]]
     kept_of = {}
 
     def kept(v):
@@ -163,9 +167,9 @@ def test_dcsbm1m_k3_capped_rows(env, orc):
         assert np.float32(Z[i]).view(np.uint32) == z.view(np.uint32)
         # every other entry is there because i is kept by j; q exactly, for a few
         others = [j for j in entry if j not in Ki]
-        for j in others[:4]:
+        for j in others[:nback]:
             assert int(i) in kept(j)
-        for j in list(Ki)[:3] + others[:3]:
+        for j in list(Ki)[:3] + others[:min(3, nback)]:
             d = entry[j][0]
             gd = gz[d - 1]
             a = np.float32(gd / Z[i]) if j in Ki else np.float32(0.0)
