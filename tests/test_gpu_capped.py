@@ -4,10 +4,10 @@ feasible) against the oracle's korder_capped / similarity_capped: the union
 pattern K u K^T, hop distances, Z over each kept set, the quantised weights,
 the row sums and both alias tables bit for bit on small graphs (caps that bind
 at level 1, 2 and 3, ragged inputs, caps for both warp buffer sizes, and a
-cap that does not bind; caps out of range refused); at full
-size (DC-SBM 1M nodes and R-MAT scale 22, k = 3, where the uncapped matrices
-would exceed 2^32 entries) sampled rows are checked against single-row
-traversals of the oracle."""
+cap that does not bind; caps out of range refused); on large graphs (the
+1M-node DC-SBM at k = 3, where the uncapped matrix would exceed 2^32
+entries, and an R-MAT of scale 18) sampled rows are checked against
+single-row traversals of the oracle."""
 import numpy as np
 import pytest
 
@@ -125,14 +125,14 @@ def _kept(orc, row_col, row_dist, cap):
     return dict(zip(row_col[order].tolist(), row_dist[order].tolist()))
 
 
-@pytest.mark.parametrize("wl,nrows,nback", [("dcsbm1m", 20, 4), ("rmat22", 6, 2)])
-def test_full_size_k3_capped_rows(env, orc, wl, nrows, nback):
-    # sampled rows of the 1M-node DC-SBM and of R-MAT scale 22 (whose hubs
-    # have the smallest ids, so the tie order decides most cut levels; its
-    # rows reach most of the 2M-node component, so fewer are traversed)
+@pytest.mark.parametrize("wl", ["dcsbm1m", "rmat18"])
+def test_large_k3_capped_rows(env, orc, wl):
+    # sampled rows of the 1M-node DC-SBM (the bench graph) and of an R-MAT of
+    # scale 18 with the scale-22 workload's parameters (its hubs have the
+    # smallest ids, so the tie order decides most cut levels)
     drg, ctx = env
-    cap, k = 128, 3
-    g = gg.workload(wl)
+    cap, k, nrows, nback = 128, 3, 20, 4
+    g = gg.workload("dcsbm1m") if wl == "dcsbm1m" else gg.rmat(18, 8, 0.57, 0.19, 0.19, 4)
     orp, ocol = orc.canonical_graph(*g)
     G = drg.graph_from_edges(ctx, *g)
     D = drg.build_distance_matrix(ctx, G, k, row_cap=cap)
