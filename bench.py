@@ -377,9 +377,28 @@ def oracle_whole_path(wl, budget_s):
     orc.run(n, s, d, p, return_state=False)
     wall = time.perf_counter() - t0
     samples = sum(sizes) * E
+    # the run's steps before the level runs, timed one by one in a second
+    # pass (the phase boundaries of the GPU line's phases_ms); the level runs
+    # and refinement are the rest of the whole run's time
+    phases = {}
+    t = time.perf_counter()
+    rp, col = orc.canonical_graph(n, s, d)
+    phases["graph"] = time.perf_counter() - t
+    t = time.perf_counter()
+    gd = orc.korder(rp, col, wl["k"])
+    phases["distance_matrix"] = time.perf_counter() - t
+    t = time.perf_counter()
+    orc.sampling_tables(*gd, wl["k"], p.sigma)
+    phases["similarity_and_alias_tables"] = time.perf_counter() - t
+    t = time.perf_counter()
+    orc.hierarchy(rp, col, p)
+    phases["hierarchy"] = time.perf_counter() - t
+    phases["layout_levels_and_refinement"] = max(wall - sum(phases.values()), 0.0)
+    phases = {k: round(v * 1e3, 1) for k, v in phases.items()}
     return samples / wall, samples, (f"{desc}, k={wl['k']}, M={wl['M']}, b={wl['b']:g}; the FP64 oracle's whole path "
                                      f"(tables, hierarchy of {len(sizes)} levels, {E} epochs per level in "
-                                     f"sequential mode, refinement) on one core: {samples} samples in {wall:.1f} s")
+                                     f"sequential mode, refinement) on one core: {samples} samples in {wall:.1f} s"), \
+        phases
 
 
 def oracle_sample(wl, budget_s):
@@ -448,7 +467,7 @@ def run_reference(args):
     sample = ""
     total_samples = 0
     for _ in range(args.steps):
-        v, ns, sample = oracle_whole_path(wl, per_step)
+        v, ns, sample, _ = oracle_whole_path(wl, per_step)
         total_samples += ns
     wall = time.perf_counter() - t0
     value = total_samples / wall
@@ -667,9 +686,11 @@ def main():
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        v, ns, sample = oracle_whole_path(wl, args.cpu_budget)
+        v, ns, sample, ph = oracle_whole_path(wl, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample,
-                                "nproc": os.cpu_count()}
+                                "nproc": os.cpu_count(), "phases_ms": ph,
+                                "phases_note": "the steps before the level runs timed one by one in a second pass; "
+                                               "layout_levels_and_refinement is the rest of the whole run"}
         par = oracle_parallel_sample(wl, args.cpu_budget)
         if par is not None:
             line["cpu_parallel_baseline"] = {"value": par[0], "unit": "updates/s", "cores": par[1],
