@@ -10,6 +10,7 @@ layouts and a brute-force kNN; whole runs by a loose range around the paper's
 grid17 numbers.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -622,3 +623,30 @@ def test_whole_run_with_a_cap_that_does_not_bind_is_the_whole_run(orc):
     assert np.array_equal(a, b)
     c = orc.run(*g, orc.Params(**p, row_cap=6))
     assert np.all(np.isfinite(c)) and not np.array_equal(a, c)
+
+
+def test_stored_capped_runs_are_the_oracle_s(orc):
+    # tests/golden/capped_quality.json holds the oracle's capped whole runs
+    # (make_capped_quality.py); two of its seeds recomputed by the oracle as
+    # it stands give the stored NP and stress exactly
+    import json
+    gold = json.load(open(golden("capped_quality.json")))
+    n, s, d = getattr(gg, gold["graph"]["gen"])(*gold["graph"]["args"])
+    rp, col = orc.canonical_graph(n, s, d)
+    for seed in (0, 1):
+        Y = orc.run(n, s, d, orc.Params(**gold["params"], seed=seed))
+        assert [orc.neighbourhood_preservation(rp, col, Y, 2), orc.stress(rp, col, Y)] == gold["runs"][seed]
+
+
+def test_stored_whole_runs_are_the_oracle_s(orc):
+    # tests/golden/wholerun_quality.json holds the oracle's whole runs of the
+    # 20k-node graphs (make_wholerun_quality.py); one of them recomputed by the
+    # oracle as it stands (same graph, node and source samples) gives the
+    # stored NP and stress exactly
+    import json
+    import sys
+    sys.path.insert(0, os.path.dirname(golden("wholerun_quality.json")))
+    import make_wholerun_quality as m
+    gold = json.load(open(golden("wholerun_quality.json")))
+    _, _, _, npv, st = m.one(("ba20k", "sync", 0))
+    assert [npv, st] == gold["runs"]["ba20k"]["sync"][0]
