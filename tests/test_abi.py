@@ -94,3 +94,17 @@ def test_missing_library_fails_loudly():
             "    print('raised:', e)\n") % ROOT
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert "raised:" in out.stdout and "missing" in out.stdout, (out.stdout, out.stderr)
+
+
+def test_python_constants_match_the_header(drg):
+    # every DRG_PROBE_*, DRG_MODE_*, DRG_PREC_* and DRG_PROF_* value the
+    # binding names is the header's #define
+    src = open(os.path.join(ROOT, "include", "drgraph.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+DRG_([A-Z0-9_]+)\s+(\d+)\b", src)}
+    probes = {k: v for k, v in defines.items() if k.startswith("PROBE_")}
+    assert len(probes) == 6
+    for name, value in probes.items():
+        assert getattr(drg, name) == value, name
+    for name, value in defines.items():
+        if hasattr(drg, name) and isinstance(getattr(drg, name), int):
+            assert getattr(drg, name) == value, name
